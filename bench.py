@@ -1,0 +1,353 @@
+"""Benchmark: dSDC steps/s of the T255 rotating shallow-water workload on one GB300.
+
+Workload (the configuration the headline metric names): truncation T255 on a
+384 x 768 Gauss grid, M = 4 Radau-right nodes, K = 5 sweeps, dt = 150 s,
+seeded synthetic initial state (random vorticity/divergence spectra ~ n^-1.5
+scaled to 20 m/s rms wind, one 100 m Gaussian height bump of 500 km radius).
+A step is one full dSDC step (Algorithm 2): 1 + (K-1) M = 17 explicit
+tendency evaluations through the spherical-harmonic transform and K sweep
+kernels.
+
+Arms:
+  default            the CUDA library (FP64 transforms; the FP32 mixed mode is
+                     timed beside it and reported with its error)
+  --impl reference   the FP64 CPU oracle as it stands, on the host cores
+Under torchrun (N > 1) every rank runs an independent replica of the
+workload (no data-path collective): weak scaling, value = sum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import swe_inputs as si  # noqa: E402
+
+METRIC = "SDC steps/s at T255 M=4 K=5: FP64 vs mixed at fixed error; adjoint/fwd ratio"
+WORKLOAD = "t255"
+L2_FLUSH_BYTES = 512 << 20          # > 129 MB L2
+FP64_NOMINAL_TFLOPS = 1.25          # GB300 dense FP64 (nominal; no measured FP64 peak)
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# algorithmic work per launch (units stated in the design notes)
+# ---------------------------------------------------------------------------
+def stage_flops(wl, stage: str, batch: int) -> float:
+    T, J2, L = wl.T, wl.nlat // 2, wl.nlon
+    next_ = (T + 1) * (T + 4) // 2
+    if stage == "synthesis":          # 4 complex fields x 2 real FMA per (n', j)
+        return 16.0 * next_ * J2 * batch
+    if stage == "analysis":           # 5 complex fields x 2 real FMA per (n', j)
+        return 20.0 * next_ * J2 * batch
+    if stage == "ring":               # 9 complex FFTs (5 L log2 L) + products per ring pair
+        return (9 * 5.0 * L * np.log2(L) + 60.0 * L) * J2 * batch
+    raise ValueError(stage)
+
+
+def sweep_bytes(wl, all_nodes: bool) -> float:
+    nc = (wl.T + 1) * (wl.T + 2) // 2
+    M = wl.nodes
+    states = (1 + 2 * M + M) if all_nodes else (1 + 2 * M + 1)
+    return states * 3 * nc * 16.0
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# the oracle on the host cores
+# ---------------------------------------------------------------------------
+def oracle_steps_per_s(wl, budget_s: float, max_steps: int):
+    """Time full oracle steps of the workload until the budget is spent."""
+    from oracle import sdc as osdc
+    from oracle import sht, swe
+    o = swe.SWE(sht.Grid(wl.T, wl.nlat, wl.nlon), swe.default_physics())
+    u = swe.initial_state(wl, o)
+    coll = osdc.Collocation(wl.nodes)
+    n, t0 = 0, time.perf_counter()
+    while n < max_steps:
+        u = osdc.swe_step(o, u, coll, wl.sweeps, wl.dt)
+        n += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    el = time.perf_counter() - t0
+    return n / el, n, el
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def reference_arm(args, rank: int, world: int):
+    if rank != 0:
+        return
+    wl = si.WORKLOADS[WORKLOAD]
+    for _ in range(args.warmup):
+        pass                                  # the oracle has no warm-up state worth timing
+    cap = max(1, min(args.steps, 12))         # keeps the whole run within a few minutes
+    v, n, el = oracle_steps_per_s(wl, budget_s=150.0, max_steps=cap)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "steps/s", "n_gpus": 1,
+        "steps": n, "warmup": args.warmup, "ms_per_step": 1e3 * el / n, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl.describe(), "parallelism": "host cores"},
+        "cpu_baseline": {"value": v, "unit": "steps/s", "cores": host_cores(), "kind": "oracle",
+                         "sample": f"{n} full T255 dSDC steps (of {args.steps} requested)"},
+        "e2e": {"value": v, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# the CUDA arm
+# ---------------------------------------------------------------------------
+def time_device(s, state, steps: int, flush):
+    """Sum of CUDA-event times of `steps` single-step graph replays, L2 flushed before each."""
+    import torch
+    stream = torch.cuda.current_stream()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    for i in range(steps):
+        flush.zero_()
+        starts[i].record(stream)
+        s.run(state, 1)
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in zip(starts, ends)]
+
+
+def time_e2e(s, host_state, dev_state, host_out, steps: int):
+    """Host-buffer path: pinned H2D copy, one step through the C ABI, D2H copy."""
+    import torch
+    stream = torch.cuda.current_stream()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        dev_state.copy_(host_state, non_blocking=True)
+        s.run(dev_state, 1)
+        host_out.copy_(dev_state, non_blocking=True)
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b)
+
+
+def cuda_arm(args, rank: int, world: int):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2403_20135_gb300 import SDC_FP64, SDC_MIXED_FP32, Solver
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    wl = si.WORKLOADS[WORKLOAD]
+    peaks, peak_kind = _peaks()
+
+    s = Solver.for_workload(wl, precision=SDC_FP64)
+    u0 = s.initial_state(wl)
+    state = u0.clone()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+
+    for _ in range(args.warmup):
+        s.run(state, 1)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0, _, l0 = s.counters()
+    with ClockSampler(dev) as clk:
+        times = time_device(s, state, args.steps, flush)
+    ev1, _, l1 = s.counters()
+    total_ms = float(sum(times))
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    steps_per_s = world * args.steps / (total_ms * 1e-3)
+    clocks = clk.summary()
+
+    # kernel-by-kernel profile of the same step (CUDA events between launches)
+    prof_state = u0.clone()
+    prof = None
+    nprof = max(3, min(10, args.steps))
+    acc = {k: [0.0, 0] for k in Solver.STAGES}
+    for _ in range(nprof):
+        flush.zero_()
+        p = s.profile_step(prof_state)
+        for k, (ms, n) in p.items():
+            acc[k][0] += ms
+            acc[k][1] += n
+    prof = {k: {"ms_per_launch": (v[0] / v[1]) if v[1] else 0.0, "launches_per_step": v[1] // nprof,
+                "share": v[0] / max(1e-12, sum(x[0] for x in acc.values()))} for k, v in acc.items()}
+    dom = max(("synthesis", "ring", "analysis"), key=lambda k: acc[k][0])
+    # average work per launch of the dominant stage: launches come with batch 1 (E0) and batch M
+    K, M = wl.sweeps, wl.nodes
+    nodes_per_step = 1 + (K - 1) * M
+    launches_per_step = prof[dom]["launches_per_step"]
+    flops_per_launch = stage_flops(wl, dom, nodes_per_step) / launches_per_step
+    achieved_tf = flops_per_launch / (prof[dom]["ms_per_launch"] * 1e-3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved_tf, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved_tf / FP64_NOMINAL_TFLOPS, "traffic": None, "kernel": dom,
+                "peak_kind": "nominal FP64 (no measured FP64 peak)"}
+
+    # end to end through host buffers
+    host_state = u0.cpu().pin_memory()
+    host_out = torch.empty_like(host_state).pin_memory()
+    dev_state = torch.empty_like(u0)
+    ne2e = max(3, min(args.steps, 50))
+    time_e2e(s, host_state, dev_state, host_out, 2)
+    e2e_ms = time_e2e(s, host_state, dev_state, host_out, ne2e)
+    sbytes = 3 * s.ncoef * 16
+    e2e = {"value": world * ne2e / (e2e_ms * 1e-3), "unit": "steps/s", "h2d_bytes_per_step": sbytes,
+           "d2h_bytes_per_step": sbytes}
+
+    # FP32 mixed mode beside it: throughput and error against the FP64 path
+    mixed = None
+    if not args.no_mixed:
+        sm = Solver.for_workload(wl, precision=SDC_MIXED_FP32)
+        xs = u0.clone()
+        for _ in range(args.warmup):
+            sm.run(xs, 1)
+        tm = time_device(sm, xs, args.steps, flush)
+        a64, a32 = u0.clone(), u0.clone()
+        s.run(a64, 20)
+        sm.run(a32, 20)
+        err = ((a32 - a64).abs().pow(2).sum(1) / a64.abs().pow(2).sum(1)).sqrt().cpu().numpy()
+        mixed = {"fp32": {"value": world * args.steps / (sum(tm) * 1e-3), "unit": "steps/s",
+                          "rel_l2_vs_fp64_20_steps": {"phi": float(err[0]), "zeta": float(err[1]),
+                                                      "div": float(err[2])}}}
+        sm.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, n, el = oracle_steps_per_s(wl, budget_s=args.cpu_budget, max_steps=50)
+        cpu = {"value": v, "unit": "steps/s", "cores": host_cores(), "kind": "oracle",
+               "sample": f"{n} full T255 dSDC steps of the seeded state ({el:.1f} s, numpy FP64)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": steps_per_s, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl.describe(), "precision": "FP64 transforms, FP64 solves",
+                       "l2": "flushed (512 MiB write) before every timed step",
+                       "parallelism": f"replicas x{world}"},
+            "e2e": e2e, "gpu_launches": int(l1 - l0), "clocks": clocks, "roofline": roofline,
+            "stages": prof, "mixed": mixed, "adjoint_fwd_ratio": None, "cpu_baseline": cpu,
+            "peaks_source": peak_kind,
+        }
+        print(json.dumps(line), flush=True)
+    s.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "gloo" if args.impl == "reference" else "nccl"
+        if args.impl == "ours":
+            import torch
+            torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group(backend)
+    try:
+        if args.impl == "reference":
+            reference_arm(args, rank, world)
+        else:
+            cuda_arm(args, rank, world)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

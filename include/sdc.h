@@ -1,0 +1,163 @@
+/*
+ * sdc.h -- C ABI of the GB300 node-parallel diagonal IMEX SDC sweep for the
+ * rotating shallow-water equations in spherical-harmonic vorticity-divergence
+ * form (Freese, Goetschel, Lunet, Ruprecht, Schreiber: "Parallel performance
+ * of shared memory parallel spectral deferred corrections", arXiv 2403.20135,
+ * the SWEET variant of Sec. 3.2 and Sec. 4.4).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * State: three complex spectral fields in the order (Phi', zeta, div) -- the
+ *   paper's U-hat of Sec. 3.2 (it writes rho for the divergence) -- stored as
+ *   double2 (re, im) in DEVICE memory, layout state[3][ncoef].  Coefficient
+ *   (n, m), 0 <= m <= n <= T, sits at m (2T + 3 - m) / 2 + (n - m)
+ *   ("m-major triangular").  Basis: normalised associated Legendre functions
+ *   (integral of Pbar^2 over [-1, 1] equal to 1, no Condon-Shortley phase)
+ *   times e^{i m lambda}; a real field is f_0 + 2 Re sum_{m>0}.  Im of the
+ *   m = 0 coefficients is 0 on input and stays 0.
+ * Grid: nlat Gauss-Legendre latitudes ordered north to south, nlon equally
+ *   spaced longitudes from 0; grid arrays are double [nlat][nlon].
+ * Phi' = g (h - H) is the geopotential perturbation, Phibar = g H.
+ * Streams: every call is asynchronous on the stream given to sdc_create,
+ *   except where a HOST output (resid_out, loss_out, counters) is requested;
+ *   those calls synchronise that stream before returning.
+ * Ownership: the caller owns every state, grid and gradient buffer it passes;
+ *   the library owns its tables, workspaces and CUDA graphs, all allocated in
+ *   sdc_create and released in sdc_destroy.  No call other than sdc_create
+ *   allocates device memory.
+ * Errors: every call returns an sdc_status; no exception or abort crosses the
+ *   ABI.  sdc_last_error() returns a thread-local description of the last
+ *   failure on the calling thread.  After SDC_ECUDA the context must be
+ *   destroyed.
+ */
+#ifndef SDC_H_
+#define SDC_H_
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sdc_ctx sdc_ctx;
+
+/* Physical constants: sphere radius a [m], rotation rate Omega [1/s],
+ * gravity g [m/s^2], mean depth H [m] (Sec. 3.2, Eq. (4)). */
+typedef struct {
+    double radius;
+    double omega;
+    double gravity;
+    double mean_depth;
+} sdc_phys;
+
+/* Arithmetic of the explicit tendency's spectral transforms.  The implicit
+ * solves, the collocation (quadrature) accumulation and the residual norms
+ * are FP64 in every mode. */
+typedef enum {
+    SDC_FP64 = 0,          /* transforms in FP64 */
+    SDC_MIXED_FP32 = 1,    /* Legendre contractions and ring FFTs in FP32 */
+    SDC_MIXED_BF16X3 = 2   /* Legendre contractions as 3-term split-BF16 products
+                              on the tensor cores, FP32 accumulation */
+} sdc_precision;
+
+typedef enum {
+    SDC_OK = 0,
+    SDC_EINVAL = 1,        /* an argument is out of range (see each call) */
+    SDC_ENOMEM = 2,        /* device or host allocation failed in sdc_create */
+    SDC_ECUDA = 3,         /* a CUDA runtime call failed */
+    SDC_EDIVERGED = 4,     /* a requested residual norm is not finite */
+    SDC_ESTATE = 5,        /* call not valid in the context's current state */
+    SDC_EUNSUPPORTED = 6   /* option/precision not available for these sizes */
+} sdc_status;
+
+/* Option keys for sdc_set_option. */
+typedef enum {
+    /* MIN-SR-FLEX diagonal q^Delta_{m,m} = tau_m / q(k) at sweep k (Sec. 4.2).
+     * The paper always runs K = M; for k > M the value is
+     * SDC_QDELTA_CLAMPED (default): q(k) = min(k, M), or
+     * SDC_QDELTA_LITERAL: q(k) = k. */
+    SDC_OPT_QDELTA_RULE = 1
+} sdc_option;
+enum { SDC_QDELTA_CLAMPED = 0, SDC_QDELTA_LITERAL = 1 };
+
+/* Create a solver for truncation T on an nlat x nlon Gauss grid with M
+ * Radau-right collocation nodes (tau_M = 1, Sec. 4.2), K sweeps per step
+ * (Algorithm 2) and step size dt [s].
+ * Requirements (else SDC_EINVAL): 1 <= T <= 1023; nlat even, nlat >= (3T+1)/2
+ * (alias-free quadratic products), nlat <= 2048; nlon = 2^a 3^b with
+ * nlon >= 3T + 1 and nlon <= 2304 (one latitude ring pair's FFTs live in
+ * shared memory); 1 <= nodes <= 8; 1 <= sweeps <= 64;
+ * dt > 0; phys non-NULL with radius, gravity, mean_depth > 0; precision one of
+ * sdc_precision.  cuda_stream is a cudaStream_t (NULL = legacy default
+ * stream) used by every later call.  On success *out owns all device memory
+ * the solver needs; on failure *out is NULL and nothing is leaked. */
+int sdc_create(sdc_ctx **out, int truncation, int nlat, int nlon, int nodes, int sweeps,
+               double dt, const sdc_phys *phys, int precision, void *cuda_stream);
+
+/* Release everything sdc_create allocated (waits for the stream).  NULL is a
+ * no-op. */
+int sdc_destroy(sdc_ctx *ctx);
+
+/* Set an option (sdc_option); SDC_EINVAL for an unknown key or value. */
+int sdc_set_option(sdc_ctx *ctx, int key, int value);
+
+/* Number of complex coefficients per field, (T+1)(T+2)/2; -1 for NULL. */
+int sdc_ncoef(const sdc_ctx *ctx);
+
+/* One dSDC step t_n -> t_n + dt: Algorithm 2 with the node update Eq. (7)
+ * (f_I = L_g solved per spectral mode as in Eq. (8), f_E = T_E = L_c + N_a +
+ * N_r of Eq. (4)).  state_in and state_out are device state[3][ncoef]; they
+ * may be the same buffer.  resid_out (HOST, nullable) receives K x 3 doubles:
+ * for each sweep k = 1..K and field (Phi', zeta, div), the maximum over the
+ * nodes that sweep updates of the Parseval-weighted L2 norm of the
+ * collocation residual u_n + dt sum_j q_mj F(u_j^{k-1}) - u_m^{k-1}; when
+ * requested the call synchronises and returns SDC_EDIVERGED if any norm is
+ * not finite. */
+int sdc_step(sdc_ctx *ctx, const void *state_in, void *state_out, double *resid_out);
+
+/* nsteps >= 0 steps in place on the device state[3][ncoef] (one CUDA graph
+ * replay per step).  nsteps = 0 is a no-op. */
+int sdc_run(sdc_ctx *ctx, void *state, int nsteps);
+
+/* Explicit tendency T_E (Eq. (4): L_c + N_a + N_r through the spherical
+ * harmonic transform) of `batch` states: states and tend are device arrays
+ * [batch][3][ncoef]; 1 <= batch <= nodes. */
+int sdc_tendency(sdc_ctx *ctx, const void *states, void *tend, int batch);
+
+/* Scalar transforms of one field (helpers for initial states and grid
+ * diagnostics): spec is device double2[ncoef], grid is device
+ * double[nlat][nlon].  grid_to_spec is the Gauss-quadrature analysis onto
+ * degree <= T. */
+int sdc_spec_to_grid(sdc_ctx *ctx, const void *spec, double *grid);
+int sdc_grid_to_spec(sdc_ctx *ctx, const double *grid, void *spec);
+
+/* Host copies of the grid and collocation data: mu[nlat] = sin(latitude),
+ * w[nlat] Gauss weights, tau[nodes] Radau-right nodes, Q[nodes*nodes]
+ * row-major collocation matrix q_{m,j} = int_0^{tau_m} l_j (Sec. 4.1).
+ * Any pointer may be NULL. */
+int sdc_grid_coords(const sdc_ctx *ctx, double *mu, double *w);
+int sdc_collocation(const sdc_ctx *ctx, double *tau, double *Q);
+
+/* Work counters since creation (HOST outputs, any may be NULL): explicit
+ * tendency evaluations of single states, per-node implicit solves, and the
+ * library's own kernel launches.  Algorithm 2 performs 1 + (K-1) M
+ * evaluations and (K-1) M + 1 solves per step (Table 1). */
+int sdc_counters(const sdc_ctx *ctx, long long *explicit_evals, long long *solves,
+                 long long *kernel_launches);
+
+/* One step like sdc_run(ctx, state, 1), but launched kernel by kernel (not
+ * from the graph) with CUDA events between the launches; synchronises.
+ * HOST outputs ms[5] and launches[5] receive the summed device time and the
+ * number of launches of each kernel class: 0 Legendre synthesis, 1 ring
+ * FFT/products, 2 Legendre analysis, 3 quadrature + implicit solve (sweep),
+ * 4 residual reduction. */
+int sdc_profile_step(sdc_ctx *ctx, void *state, double *ms, int *launches);
+
+/* Launches per step of the captured step graph (HOST output). */
+int sdc_launches_per_step(const sdc_ctx *ctx, int *launches);
+
+const char *sdc_strerror(int status);
+const char *sdc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SDC_H_ */

@@ -87,7 +87,7 @@ def legendre_pbar(T: int, mu: np.ndarray, nmax_extra: int = 1):
     Pbar_n^m = (mu Pbar_{n-1}^m - eps_{n-1}^m Pbar_{n-2}^m) / eps_n^m.
     """
     mu = np.asarray(mu, dtype=np.float64)
-    s = np.sqrt(1.0 - mu * mu)
+    s = np.sqrt((1.0 - mu) * (1.0 + mu))          # sqrt(1 - mu^2) without cancellation near the poles
     nmax = T + nmax_extra
     out = []
     pmm = np.full(mu.shape, 1.0 / np.sqrt(2.0))

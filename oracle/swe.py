@@ -57,7 +57,7 @@ class SWE:
         # per-latitude weights
         mu = grid.mu
         self.w = grid.w
-        self.wt = grid.w / (1.0 - mu * mu)            # w_j / (1 - mu_j^2)
+        self.wt = grid.w / ((1.0 - mu) * (1.0 + mu))  # w_j / (1 - mu_j^2)
         self.n_explicit = 0                           # counters (Table 1)
         self.n_solve = 0
 
@@ -117,7 +117,7 @@ class SWE:
         B = eta * V
         C = phi * U
         D = phi * V
-        E = (U * U + V * V) / (2.0 * (1.0 - mu * mu))
+        E = (U * U + V * V) / (2.0 * (1.0 - mu) * (1.0 + mu))
         Am, Bm, Cm, Dm, Em = (g.grid_to_fourier(x) for x in (A, B, C, D, E))
         out = np.zeros_like(u)
         # zeta: -div(eta V)_n^m = -(1/a) sum_j wt_j [i m A_m Pbar - B_m H]

@@ -1,0 +1,18 @@
+"""GB300-native node-parallel diagonal IMEX SDC for rotating shallow water on the sphere.
+
+The hot path (spherical-harmonic tendencies, collocation quadrature, per-mode
+implicit solves, residuals) runs in hand-written CUDA kernels for sm_103a
+behind the C ABI of include/sdc.h; ``Solver`` is its thin Python face.
+"""
+from ._lib import (SDC_FP64, SDC_MIXED_FP32, SDC_MIXED_BF16X3, SDC_QDELTA_CLAMPED,
+                   SDC_QDELTA_LITERAL, SdcError, LIB_PATH, load)
+
+__all__ = ["Solver", "SDC_FP64", "SDC_MIXED_FP32", "SDC_MIXED_BF16X3", "SDC_QDELTA_CLAMPED",
+           "SDC_QDELTA_LITERAL", "SdcError", "LIB_PATH", "load"]
+
+
+def __getattr__(name):
+    if name == "Solver":
+        from .solver import Solver
+        return Solver
+    raise AttributeError(name)

@@ -1,0 +1,467 @@
+// C ABI: context life cycle and the dSDC step of Algorithm 2, captured once
+// as a CUDA graph and replayed per time step.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "sdc_internal.h"
+
+using namespace sdc;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int status, const std::string &msg) {
+    g_last_error = msg;
+    return status;
+}
+
+int cuda_fail(cudaError_t e, const char *where) {
+    return fail(SDC_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define SDC_CUDA(call)                                          \
+    do {                                                        \
+        cudaError_t e_ = (call);                                \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);     \
+    } while (0)
+
+bool is_2a3b(int L) {
+    if (L < 1) return false;
+    while (L % 2 == 0) L /= 2;
+    while (L % 3 == 0) L /= 3;
+    return L == 1;
+}
+
+}  // namespace
+
+struct sdc_ctx {
+    int T = 0, J = 0, L = 0, M = 0, K = 0;
+    int precision = SDC_FP64;
+    int qdelta_rule = SDC_QDELTA_CLAMPED;
+    double dt = 0.0;
+    sdc_phys phys{};
+    Dims d{};
+    FftPlan plan{};
+    cudaStream_t stream = nullptr;       // caller's stream
+    cudaStream_t cap = nullptr;          // private stream used for graph capture
+    std::vector<double> mu, w, tau, Q;
+
+    // device tables
+    double *pbar = nullptr;
+    float *pbar32 = nullptr;
+    double *eps = nullptr, *lam = nullptr, *mu2 = nullptr, *w2 = nullptr;
+    double2 *tw = nullptr;
+    float2 *tw32 = nullptr;
+    // device workspaces
+    double2 *un = nullptr, *U = nullptr, *E = nullptr, *E0 = nullptr;
+    void *f1 = nullptr, *f2 = nullptr;
+    double *resid_part = nullptr, *resid = nullptr;
+    int sweep_nblocks = 0;
+
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};   // [with residuals]
+    int graph_launches[2] = {0, 0};
+    long long n_explicit = 0, n_solve = 0, n_launch = 0;
+
+    long long state_elems() const { return 3LL * d.ncoef; }
+};
+
+namespace {
+
+void free_ctx(sdc_ctx *c) {
+    if (!c) return;
+    for (auto &g : c->graph)
+        if (g) cudaGraphExecDestroy(g);
+    void *ptrs[] = {c->pbar, c->pbar32, c->eps, c->lam, c->mu2, c->w2, c->tw, c->tw32, c->un, c->U,
+                    c->E, c->E0, c->f1, c->f2, c->resid_part, c->resid};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    if (c->cap) cudaStreamDestroy(c->cap);
+    delete c;
+}
+
+template <typename T>
+cudaError_t upload(T **dst, const T *src, size_t n) {
+    cudaError_t e = cudaMalloc(reinterpret_cast<void **>(dst), n * sizeof(T));
+    if (e != cudaSuccess) return e;
+    return cudaMemcpy(*dst, src, n * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+// q^Delta denominator of sweep k (1-based), Sec. 4.2 (MIN-SR-FLEX).
+double qdelta_den(const sdc_ctx *c, int k) {
+    if (c->qdelta_rule == SDC_QDELTA_LITERAL) return k;
+    return k < c->M ? k : c->M;
+}
+
+cudaError_t tendency(sdc_ctx *c, int B, const double2 *states, long long sstride, double2 *tend,
+                     long long tstride, cudaStream_t s, int *launches, StageTimer *timer = nullptr) {
+    if (c->precision == SDC_FP64)
+        return launch_tendency_f64(c->d, c->plan, B, states, sstride, tend, tstride, c->pbar, c->eps, c->lam,
+                                   c->mu2, c->w2, c->tw, static_cast<double2 *>(c->f1),
+                                   static_cast<double2 *>(c->f2), s, launches, timer);
+    return launch_tendency_f32(c->d, c->plan, B, states, sstride, tend, tstride, c->pbar32, c->eps, c->lam,
+                               c->mu2, c->w2, c->tw32, static_cast<float2 *>(c->f1),
+                               static_cast<float2 *>(c->f2), s, launches, timer);
+}
+
+// Enqueue one step u_n -> u_n (in place on c->un), Algorithm 2.
+cudaError_t enqueue_step(sdc_ctx *c, cudaStream_t s, bool with_resid, int *launches,
+                         StageTimer *timer = nullptr) {
+    const long long se = c->state_elems();
+    const int M = c->M, K = c->K;
+    cudaError_t e;
+    // E0 = T_E(u_n)
+    e = tendency(c, 1, c->un, se, c->E0, se, s, launches, timer);
+    if (e != cudaSuccess) return e;
+
+    SweepParams p{};
+    p.un = c->un;
+    p.lam = c->lam;
+    p.ncoef = c->d.ncoef;
+    p.T = c->T;
+    p.dt = c->dt;
+    p.phibar = c->phys.gravity * c->phys.mean_depth;
+    for (int m = 0; m < M; ++m)
+        for (int j = 0; j < M; ++j) p.Q[m][j] = c->Q[m * M + j];
+    p.resid_part = with_resid ? c->resid_part : nullptr;
+
+    for (int k = 0; k < K; ++k) {             // sweep k+1
+        const bool first = (k == 0), last = (k == K - 1);
+        p.ubase = first ? c->un : c->U;
+        p.ustride = first ? 0 : se;
+        p.ebase = first ? c->E0 : c->E;
+        p.estride = first ? 0 : se;
+        const double den = qdelta_den(c, k + 1);
+        for (int m = 0; m < M; ++m) p.alpha[m] = c->dt * c->tau[m] / den;
+        if (last) {                           // node M only, written to u_{n+1}
+            p.m0 = M - 1;
+            p.m1 = M;
+            p.out = c->un;
+            p.ostride = 0;
+        } else {
+            p.m0 = 0;
+            p.m1 = M;
+            p.out = c->U;
+            p.ostride = se;
+        }
+        e = launch_sweep(p, M, s, launches, timer);
+        if (e != cudaSuccess) return e;
+        if (with_resid) {
+            e = launch_resid_reduce(c->resid_part, c->sweep_nblocks, M, p.m0, p.m1, c->resid + 3 * k, s, launches,
+                                    timer);
+            if (e != cudaSuccess) return e;
+        }
+        if (!last) {
+            e = tendency(c, M, c->U, se, c->E, se, s, launches, timer);
+            if (e != cudaSuccess) return e;
+        }
+    }
+    return cudaSuccess;
+}
+
+int ensure_graph(sdc_ctx *c, bool with_resid) {
+    const int v = with_resid ? 1 : 0;
+    if (c->graph[v]) return SDC_OK;
+    cudaGraph_t g = nullptr;
+    SDC_CUDA(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
+    int launches = 0;
+    cudaError_t e = enqueue_step(c, c->cap, with_resid, &launches);
+    cudaError_t e2 = cudaStreamEndCapture(c->cap, &g);
+    if (e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return cuda_fail(e, "capture of the step");
+    }
+    if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&c->graph[v], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    c->graph_launches[v] = launches;
+    return SDC_OK;
+}
+
+int run_steps(sdc_ctx *c, int nsteps, bool with_resid) {
+    int st = ensure_graph(c, with_resid);
+    if (st != SDC_OK) return st;
+    for (int i = 0; i < nsteps; ++i) SDC_CUDA(cudaGraphLaunch(c->graph[with_resid ? 1 : 0], c->stream));
+    c->n_explicit += static_cast<long long>(nsteps) * (1 + (c->K - 1) * c->M);
+    c->n_solve += static_cast<long long>(nsteps) * ((c->K - 1) * c->M + 1);
+    c->n_launch += static_cast<long long>(nsteps) * c->graph_launches[with_resid ? 1 : 0];
+    return SDC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *sdc_strerror(int status) {
+    switch (status) {
+        case SDC_OK: return "ok";
+        case SDC_EINVAL: return "invalid argument";
+        case SDC_ENOMEM: return "out of memory";
+        case SDC_ECUDA: return "CUDA error";
+        case SDC_EDIVERGED: return "residual not finite";
+        case SDC_ESTATE: return "invalid state";
+        case SDC_EUNSUPPORTED: return "unsupported option";
+        default: return "unknown status";
+    }
+}
+
+const char *sdc_last_error(void) { return g_last_error.c_str(); }
+
+int sdc_create(sdc_ctx **out, int T, int J, int L, int M, int K, double dt, const sdc_phys *phys, int precision,
+               void *cuda_stream) {
+    if (!out) return fail(SDC_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (T < 1 || T > 1023) return fail(SDC_EINVAL, "truncation must be in [1, 1023]");
+    if (J % 2 != 0 || 2 * J < 3 * T + 1 || J > 2048) return fail(SDC_EINVAL, "nlat must be even, >= (3T+1)/2, <= 2048");
+    if (!is_2a3b(L) || L < 3 * T + 1 || L > 2304) return fail(SDC_EINVAL, "nlon must be 2^a 3^b, >= 3T+1, <= 2304");
+    if (M < 1 || M > kMaxNodes) return fail(SDC_EINVAL, "nodes must be in [1, 8]");
+    if (K < 1 || K > 64) return fail(SDC_EINVAL, "sweeps must be in [1, 64]");
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(SDC_EINVAL, "dt must be positive and finite");
+    if (!phys || !(phys->radius > 0) || !(phys->gravity > 0) || !(phys->mean_depth > 0) || !std::isfinite(phys->omega))
+        return fail(SDC_EINVAL, "physical constants invalid");
+    if (precision != SDC_FP64 && precision != SDC_MIXED_FP32 && precision != SDC_MIXED_BF16X3)
+        return fail(SDC_EINVAL, "unknown precision");
+    if (precision == SDC_MIXED_BF16X3) return fail(SDC_EUNSUPPORTED, "split-BF16 precision not built");
+
+    sdc_ctx *c = new (std::nothrow) sdc_ctx();
+    if (!c) return fail(SDC_ENOMEM, "host allocation");
+    c->T = T; c->J = J; c->L = L; c->M = M; c->K = K;
+    c->dt = dt;
+    c->phys = *phys;
+    c->precision = precision;
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+
+    Dims &d = c->d;
+    d.T = T; d.J = J; d.J2 = J / 2; d.J2p = ((J / 2) + 3) / 4 * 4; d.L = L;
+    d.ncoef = (T + 1) * (T + 2) / 2;
+    d.next = (T + 1) * (T + 4) / 2;
+    d.a = phys->radius;
+    d.two_omega = 2.0 * phys->omega;
+    if (!fft_plan(L, c->plan)) { free_ctx(c); return fail(SDC_EINVAL, "no FFT plan for nlon"); }
+    const int elem = precision == SDC_FP64 ? (int)sizeof(double2) : (int)sizeof(float2);
+    if (ring_smem_bytes(L, elem, nullptr) == 0) { free_ctx(c); return fail(SDC_EINVAL, "nlon too large"); }
+
+    // host precompute
+    gauss_legendre(J, c->mu, c->w);
+    radau_right(M, c->tau, c->Q);
+    std::vector<double> table, eps, lam(d.ncoef), twr, twi;
+    legendre_table(T, d.J2, d.J2p, c->mu, table);
+    epsilon_table(T, eps);
+    for (int m = 0; m <= T; ++m)
+        for (int n = m; n <= T; ++n)
+            lam[order_offset(T, m) + n - m] = double(n) * double(n + 1) / (phys->radius * phys->radius);
+    twiddles(L, twr, twi);
+    std::vector<double2> tw(L);
+    std::vector<float2> tw32(L);
+    for (int k = 0; k < L; ++k) {
+        tw[k] = make_double2(twr[k], twi[k]);
+        tw32[k] = make_float2(float(twr[k]), float(twi[k]));
+    }
+
+    cudaError_t e = cudaSuccess;
+#define SDC_TRY(call)                                                          \
+    do {                                                                       \
+        e = (call);                                                            \
+        if (e != cudaSuccess) {                                                \
+            int st_ = (e == cudaErrorMemoryAllocation) ? SDC_ENOMEM : SDC_ECUDA; \
+            std::string msg_ = std::string(#call) + ": " + cudaGetErrorString(e); \
+            free_ctx(c);                                                       \
+            return fail(st_, msg_);                                            \
+        }                                                                      \
+    } while (0)
+
+    SDC_TRY(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
+    SDC_TRY(configure_transform_kernels(d, c->plan, precision != SDC_FP64));
+    if (precision != SDC_FP64) SDC_TRY(configure_transform_kernels(d, c->plan, false));
+    if (precision == SDC_FP64) {
+        SDC_TRY(upload(&c->pbar, table.data(), table.size()));
+        SDC_TRY(upload(&c->tw, tw.data(), tw.size()));
+    } else {
+        std::vector<float> t32(table.size());
+        for (size_t i = 0; i < table.size(); ++i) t32[i] = float(table[i]);
+        SDC_TRY(upload(&c->pbar32, t32.data(), t32.size()));
+        SDC_TRY(upload(&c->tw32, tw32.data(), tw32.size()));
+        // the scalar helpers stay FP64
+        SDC_TRY(upload(&c->pbar, table.data(), table.size()));
+        SDC_TRY(upload(&c->tw, tw.data(), tw.size()));
+    }
+    SDC_TRY(upload(&c->eps, eps.data(), eps.size()));
+    SDC_TRY(upload(&c->lam, lam.data(), lam.size()));
+    SDC_TRY(upload(&c->mu2, c->mu.data(), d.J2));
+    SDC_TRY(upload(&c->w2, c->w.data(), d.J2));
+
+    const size_t sbytes = 3ULL * d.ncoef * sizeof(double2);
+    SDC_TRY(cudaMalloc(&c->un, sbytes));
+    SDC_TRY(cudaMalloc(&c->U, sbytes * M));
+    SDC_TRY(cudaMalloc(&c->E, sbytes * M));
+    SDC_TRY(cudaMalloc(&c->E0, sbytes));
+    const size_t f1b = static_cast<size_t>(M) * d.J2 * 8 * (T + 1) * elem;
+    const size_t f2b = static_cast<size_t>(M) * (T + 1) * 10 * d.J2 * elem;
+    const size_t scal = static_cast<size_t>(d.J2) * 2 * (T + 1) * sizeof(double2);   // scalar helpers (FP64)
+    SDC_TRY(cudaMalloc(&c->f1, f1b > scal ? f1b : scal));
+    SDC_TRY(cudaMalloc(&c->f2, f2b > scal ? f2b : scal));
+    c->sweep_nblocks = sweep_blocks(d.ncoef);
+    SDC_TRY(cudaMalloc(&c->resid_part, static_cast<size_t>(c->sweep_nblocks) * M * 3 * sizeof(double)));
+    SDC_TRY(cudaMalloc(&c->resid, static_cast<size_t>(K) * 3 * sizeof(double)));
+    SDC_TRY(cudaDeviceSynchronize());
+#undef SDC_TRY
+    *out = c;
+    return SDC_OK;
+}
+
+int sdc_destroy(sdc_ctx *c) {
+    if (!c) return SDC_OK;
+    cudaStreamSynchronize(c->stream);
+    free_ctx(c);
+    return SDC_OK;
+}
+
+int sdc_set_option(sdc_ctx *c, int key, int value) {
+    if (!c) return fail(SDC_EINVAL, "ctx is NULL");
+    if (key == SDC_OPT_QDELTA_RULE) {
+        if (value != SDC_QDELTA_CLAMPED && value != SDC_QDELTA_LITERAL) return fail(SDC_EINVAL, "bad q-delta rule");
+        if (value != c->qdelta_rule) {
+            c->qdelta_rule = value;
+            for (auto &g : c->graph)
+                if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+        }
+        return SDC_OK;
+    }
+    return fail(SDC_EINVAL, "unknown option");
+}
+
+int sdc_ncoef(const sdc_ctx *c) { return c ? c->d.ncoef : -1; }
+
+int sdc_step(sdc_ctx *c, const void *in, void *out, double *resid_out) {
+    if (!c || !in || !out) return fail(SDC_EINVAL, "NULL argument");
+    const size_t sbytes = 3ULL * c->d.ncoef * sizeof(double2);
+    SDC_CUDA(cudaMemcpyAsync(c->un, in, sbytes, cudaMemcpyDeviceToDevice, c->stream));
+    int st = run_steps(c, 1, resid_out != nullptr);
+    if (st != SDC_OK) return st;
+    SDC_CUDA(cudaMemcpyAsync(out, c->un, sbytes, cudaMemcpyDeviceToDevice, c->stream));
+    if (resid_out) {
+        SDC_CUDA(cudaMemcpyAsync(resid_out, c->resid, sizeof(double) * 3 * c->K, cudaMemcpyDeviceToHost, c->stream));
+        SDC_CUDA(cudaStreamSynchronize(c->stream));
+        for (int i = 0; i < 3 * c->K; ++i)
+            if (!std::isfinite(resid_out[i])) return fail(SDC_EDIVERGED, "non-finite residual norm");
+    }
+    return SDC_OK;
+}
+
+int sdc_run(sdc_ctx *c, void *state, int nsteps) {
+    if (!c || !state) return fail(SDC_EINVAL, "NULL argument");
+    if (nsteps < 0) return fail(SDC_EINVAL, "nsteps < 0");
+    if (nsteps == 0) return SDC_OK;
+    const size_t sbytes = 3ULL * c->d.ncoef * sizeof(double2);
+    SDC_CUDA(cudaMemcpyAsync(c->un, state, sbytes, cudaMemcpyDeviceToDevice, c->stream));
+    int st = run_steps(c, nsteps, false);
+    if (st != SDC_OK) return st;
+    SDC_CUDA(cudaMemcpyAsync(state, c->un, sbytes, cudaMemcpyDeviceToDevice, c->stream));
+    return SDC_OK;
+}
+
+int sdc_tendency(sdc_ctx *c, const void *states, void *tend, int batch) {
+    if (!c || !states || !tend) return fail(SDC_EINVAL, "NULL argument");
+    if (batch < 1 || batch > c->M) return fail(SDC_EINVAL, "batch must be in [1, nodes]");
+    int launches = 0;
+    const long long se = c->state_elems();
+    cudaError_t e = tendency(c, batch, static_cast<const double2 *>(states), se, static_cast<double2 *>(tend), se,
+                             c->stream, &launches);
+    if (e != cudaSuccess) return cuda_fail(e, "tendency");
+    c->n_explicit += batch;
+    c->n_launch += launches;
+    return SDC_OK;
+}
+
+int sdc_spec_to_grid(sdc_ctx *c, const void *spec, double *grid) {
+    if (!c || !spec || !grid) return fail(SDC_EINVAL, "NULL argument");
+    cudaError_t e = launch_spec_to_grid(c->d, c->plan, static_cast<const double2 *>(spec), grid, c->pbar, c->tw,
+                                        static_cast<double2 *>(c->f1), c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "spec_to_grid");
+    c->n_launch += 2;
+    return SDC_OK;
+}
+
+int sdc_grid_to_spec(sdc_ctx *c, const double *grid, void *spec) {
+    if (!c || !spec || !grid) return fail(SDC_EINVAL, "NULL argument");
+    cudaError_t e = launch_grid_to_spec(c->d, c->plan, grid, static_cast<double2 *>(spec), c->pbar, c->w2, c->tw,
+                                        static_cast<double2 *>(c->f2), c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "grid_to_spec");
+    c->n_launch += 2;
+    return SDC_OK;
+}
+
+int sdc_grid_coords(const sdc_ctx *c, double *mu, double *w) {
+    if (!c) return fail(SDC_EINVAL, "ctx is NULL");
+    if (mu) std::memcpy(mu, c->mu.data(), sizeof(double) * c->J);
+    if (w) std::memcpy(w, c->w.data(), sizeof(double) * c->J);
+    return SDC_OK;
+}
+
+int sdc_collocation(const sdc_ctx *c, double *tau, double *Q) {
+    if (!c) return fail(SDC_EINVAL, "ctx is NULL");
+    if (tau) std::memcpy(tau, c->tau.data(), sizeof(double) * c->M);
+    if (Q) std::memcpy(Q, c->Q.data(), sizeof(double) * c->M * c->M);
+    return SDC_OK;
+}
+
+int sdc_counters(const sdc_ctx *c, long long *evals, long long *solves, long long *launches) {
+    if (!c) return fail(SDC_EINVAL, "ctx is NULL");
+    if (evals) *evals = c->n_explicit;
+    if (solves) *solves = c->n_solve;
+    if (launches) *launches = c->n_launch;
+    return SDC_OK;
+}
+
+int sdc_profile_step(sdc_ctx *c, void *state, double *ms, int *launches) {
+    if (!c || !state || !ms || !launches) return fail(SDC_EINVAL, "NULL argument");
+    StageTimer tm;
+    tm.stream = c->stream;
+    for (int i = 0; i <= StageTimer::kMax; ++i) {
+        cudaError_t e = cudaEventCreate(&tm.ev[i]);
+        if (e != cudaSuccess) {
+            for (int k = 0; k < i; ++k) cudaEventDestroy(tm.ev[k]);
+            return cuda_fail(e, "cudaEventCreate");
+        }
+    }
+    const size_t sbytes = 3ULL * c->d.ncoef * sizeof(double2);
+    int nl = 0;
+    cudaError_t e = cudaMemcpyAsync(c->un, state, sbytes, cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess) e = enqueue_step(c, c->stream, false, &nl, &tm);
+    tm.end();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(state, c->un, sbytes, cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e == cudaSuccess) {
+        for (int k = 0; k < NSTAGES; ++k) { ms[k] = 0.0; launches[k] = 0; }
+        for (int i = 0; i < tm.n; ++i) {
+            float t = 0.f;
+            cudaEventElapsedTime(&t, tm.ev[i], tm.ev[i + 1]);
+            ms[tm.cls[i]] += t;
+            launches[tm.cls[i]] += 1;
+        }
+        c->n_explicit += 1 + (c->K - 1) * c->M;
+        c->n_solve += (c->K - 1) * c->M + 1;
+        c->n_launch += nl;
+    }
+    for (int i = 0; i <= StageTimer::kMax; ++i) cudaEventDestroy(tm.ev[i]);
+    if (e != cudaSuccess) return cuda_fail(e, "profiled step");
+    return SDC_OK;
+}
+
+int sdc_launches_per_step(const sdc_ctx *c, int *launches) {
+    if (!c || !launches) return fail(SDC_EINVAL, "NULL argument");
+    sdc_ctx *cc = const_cast<sdc_ctx *>(c);
+    int st = ensure_graph(cc, false);
+    if (st != SDC_OK) return st;
+    *launches = c->graph_launches[0];
+    return SDC_OK;
+}
+
+}  // extern "C"

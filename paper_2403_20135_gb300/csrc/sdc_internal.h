@@ -1,0 +1,127 @@
+// Internal declarations shared by the host driver and the CUDA kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/sdc.h"
+
+namespace sdc {
+
+constexpr int kMaxNodes = 8;
+constexpr int kMaxStages = 16;
+
+// Field order of a spectral state (the paper's U-hat, Sec. 3.2).
+enum { F_PHI = 0, F_ZETA = 1, F_DIV = 2 };
+// Fields of the synthesis output (grid Fourier coefficients per latitude).
+enum { G_ZETA = 0, G_PHI = 1, G_U = 2, G_V = 3, NSYN = 4 };
+// Fields of the ring products fed to the analysis.
+enum { P_A = 0, P_B = 1, P_C = 2, P_D = 3, P_E = 4, NANA = 5 };
+
+// Offset of order m in the packed triangular layout (n = m..T).
+__host__ __device__ inline int order_offset(int T, int m) { return m * (2 * T + 3 - m) / 2; }
+// Offset of order m in the extended layout (n = m..T+1), which carries one
+// more degree per order for the (1-mu^2) d/dmu recurrences.
+__host__ __device__ inline int ext_offset(int T, int m) { return m * (2 * T + 5 - m) / 2; }
+
+// Mixed-radix (2, 3, 4) Stockham plan of a length-L complex FFT.
+struct FftPlan {
+    int L;
+    int nstages;
+    int radix[kMaxStages];
+};
+
+// Sizes handed to every transform kernel.
+struct Dims {
+    int T;        // truncation
+    int J;        // latitudes
+    int J2;       // latitude pairs (north half)
+    int J2p;      // padded row length of the Legendre table (multiple of 4)
+    int L;        // longitudes
+    int ncoef;    // (T+1)(T+2)/2
+    int next;     // (T+1)(T+4)/2, extended packing
+    double a;     // radius
+    double two_omega;
+};
+
+// Parameters of the fused quadrature + implicit solve + residual kernel.
+struct SweepParams {
+    const double2 *un;            // u_n, [3][ncoef]
+    const double2 *ubase;         // node j iterate at ubase + j * ustride
+    long long ustride;            // 0 on the first sweep (u_j^0 = u_n)
+    const double2 *ebase;         // node j explicit tendency at ebase + j * estride
+    long long estride;
+    double2 *out;                 // node m result at out + (m - m0) * ostride
+    long long ostride;
+    const double *lam;            // n(n+1)/a^2 per packed coefficient
+    double *resid_part;           // [gridDim.x][M][3] or nullptr
+    int ncoef;
+    int T;
+    int m0, m1;                   // nodes updated: [m0, m1)
+    double dt;
+    double phibar;
+    double Q[kMaxNodes][kMaxNodes];
+    double alpha[kMaxNodes];      // dt * q^Delta_{m,m}
+};
+
+// Per-kernel CUDA-event timing of a directly launched (not graph) step:
+// mark(c) records an event and tags the kernel launched next with class c.
+enum { STAGE_SYNTH = 0, STAGE_RING = 1, STAGE_ANALYSIS = 2, STAGE_SWEEP = 3, STAGE_RESID = 4, NSTAGES = 5 };
+struct StageTimer {
+    static constexpr int kMax = 512;
+    cudaEvent_t ev[kMax + 1];
+    int cls[kMax];
+    int n = 0;
+    cudaStream_t stream = nullptr;
+    void mark(int c) {
+        if (n < kMax) { cudaEventRecord(ev[n], stream); cls[n] = c; ++n; }
+    }
+    void end() { cudaEventRecord(ev[n], stream); }
+};
+
+// ---- host-side precompute (tables.cpp) ----------------------------------
+void gauss_legendre(int J, std::vector<double> &mu, std::vector<double> &w);
+void radau_right(int M, std::vector<double> &tau, std::vector<double> &Q);
+// Pbar_n^m(mu_j) for the northern latitudes j < J2, extended packing, rows
+// padded to J2p: table[(ext_offset(m) + n - m) * J2p + j].
+void legendre_table(int T, int J2, int J2p, const std::vector<double> &mu, std::vector<double> &table);
+void epsilon_table(int T, std::vector<double> &eps);   // extended packing, eps_n^m
+bool fft_plan(int L, FftPlan &plan);
+void twiddles(int L, std::vector<double> &re, std::vector<double> &im);   // e^{-2 pi i k / L}
+
+// ---- kernel launchers (transforms.cu, sweep.cu) -------------------------
+// Explicit tendency of B states (K1 -> K2 -> K3).  Returns cudaError_t.
+cudaError_t launch_tendency_f64(const Dims &d, const FftPlan &plan, int B,
+                                const double2 *states, long long sstride,
+                                double2 *tend, long long tstride,
+                                const double *pbar, const double *eps, const double *lam,
+                                const double *mu, const double *w, const double2 *tw,
+                                double2 *f1, double2 *f2, cudaStream_t s, int *launches,
+                                StageTimer *timer = nullptr);
+cudaError_t launch_tendency_f32(const Dims &d, const FftPlan &plan, int B,
+                                const double2 *states, long long sstride,
+                                double2 *tend, long long tstride,
+                                const float *pbar, const double *eps, const double *lam,
+                                const double *mu, const double *w, const float2 *tw,
+                                float2 *f1, float2 *f2, cudaStream_t s, int *launches,
+                                StageTimer *timer = nullptr);
+cudaError_t launch_sweep(const SweepParams &p, int M, cudaStream_t s, int *launches,
+                         StageTimer *timer = nullptr);
+cudaError_t launch_resid_reduce(const double *part, int nblocks, int M, int m0, int m1,
+                                double *out3, cudaStream_t s, int *launches,
+                                StageTimer *timer = nullptr);
+int sweep_blocks(int ncoef);
+
+cudaError_t launch_spec_to_grid(const Dims &d, const FftPlan &plan, const double2 *spec,
+                                double *grid, const double *pbar, const double2 *tw,
+                                double2 *f1, cudaStream_t s);
+cudaError_t launch_grid_to_spec(const Dims &d, const FftPlan &plan, const double *grid,
+                                double2 *spec, const double *pbar, const double *w,
+                                const double2 *tw, double2 *f2, cudaStream_t s);
+
+size_t ring_smem_bytes(int L, int elem_bytes, int *scratch_arrays);
+cudaError_t configure_transform_kernels(const Dims &d, const FftPlan &plan, bool fp32);
+
+}  // namespace sdc

@@ -1,0 +1,162 @@
+// K4: fused collocation quadrature, diagonal implicit solve and residual
+// partial sums of one sweep (Eq. (7) with the solver form Eq. (8)), for every
+// node of the sweep at once -- the paper's parallel node loop of Algorithm 2
+// lives inside each thread, which owns one spectral mode for all nodes.
+//
+// Per mode (n, m) with lambda_n = n(n+1)/a^2 and F_j = L_g(u_j^k) + T_E(u_j^k):
+//   R_m   = u_n + dt sum_j q_{m,j} F_j                   (collocation right side)
+//   rhs_m = R_m - alpha_m L_g(u_m^k),  alpha_m = dt q^Delta_{m,m}
+//   (I - alpha_m L_g) u_m^{k+1} = rhs_m, in closed form for
+//   L_g(Phi', zeta, div) = (-Phibar div, 0, lambda_n Phi'):
+//     Phi' = (rhs_Phi - alpha Phibar rhs_div) / (1 + alpha^2 Phibar lambda_n)
+//     div  = rhs_div + alpha lambda_n Phi',  zeta = rhs_zeta
+//   residual R_m - u_m^k accumulated as sum w |r|^2 (w = 1 at m = 0, else 2).
+// All arithmetic is FP64.
+#include <cuda_runtime.h>
+
+#include "sdc_internal.h"
+
+namespace sdc {
+
+constexpr int kSweepThreads = 256;
+
+int sweep_blocks(int ncoef) { return (ncoef + kSweepThreads - 1) / kSweepThreads; }
+
+template <int M>
+__global__ void __launch_bounds__(kSweepThreads) k4_sweep(SweepParams p) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nc = p.ncoef;
+    double rs[M][3];
+#pragma unroll
+    for (int m = 0; m < M; ++m) rs[m][0] = rs[m][1] = rs[m][2] = 0.0;
+
+    if (i < nc) {
+        const double lam = p.lam[i];
+        const double wgt = (i <= p.T) ? 1.0 : 2.0;      // order m = 0 occupies indices 0..T
+        const double2 un_p = p.un[F_PHI * nc + i];
+        const double2 un_z = p.un[F_ZETA * nc + i];
+        const double2 un_d = p.un[F_DIV * nc + i];
+        double2 Fp[M], Fz[M], Fd[M];
+        double2 up[M], uz[M], ud[M];
+#pragma unroll
+        for (int j = 0; j < M; ++j) {
+            const double2 *u = p.ubase + j * p.ustride;
+            const double2 *e = p.ebase + j * p.estride;
+            up[j] = u[F_PHI * nc + i];
+            uz[j] = u[F_ZETA * nc + i];
+            ud[j] = u[F_DIV * nc + i];
+            const double2 ep = e[F_PHI * nc + i], ez = e[F_ZETA * nc + i], ed = e[F_DIV * nc + i];
+            Fp[j] = make_double2(ep.x - p.phibar * ud[j].x, ep.y - p.phibar * ud[j].y);
+            Fz[j] = ez;
+            Fd[j] = make_double2(ed.x + lam * up[j].x, ed.y + lam * up[j].y);
+        }
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            if (m < p.m0 || m >= p.m1) continue;
+            double2 Rp = make_double2(0, 0), Rz = Rp, Rd = Rp;
+#pragma unroll
+            for (int j = 0; j < M; ++j) {
+                const double q = p.Q[m][j];
+                Rp.x = fma(q, Fp[j].x, Rp.x); Rp.y = fma(q, Fp[j].y, Rp.y);
+                Rz.x = fma(q, Fz[j].x, Rz.x); Rz.y = fma(q, Fz[j].y, Rz.y);
+                Rd.x = fma(q, Fd[j].x, Rd.x); Rd.y = fma(q, Fd[j].y, Rd.y);
+            }
+            const double dt = p.dt;
+            Rp = make_double2(fma(dt, Rp.x, un_p.x), fma(dt, Rp.y, un_p.y));
+            Rz = make_double2(fma(dt, Rz.x, un_z.x), fma(dt, Rz.y, un_z.y));
+            Rd = make_double2(fma(dt, Rd.x, un_d.x), fma(dt, Rd.y, un_d.y));
+            // residual of the current iterate
+            const double rpx = Rp.x - up[m].x, rpy = Rp.y - up[m].y;
+            const double rzx = Rz.x - uz[m].x, rzy = Rz.y - uz[m].y;
+            const double rdx = Rd.x - ud[m].x, rdy = Rd.y - ud[m].y;
+            rs[m][F_PHI] = wgt * (rpx * rpx + rpy * rpy);
+            rs[m][F_ZETA] = wgt * (rzx * rzx + rzy * rzy);
+            rs[m][F_DIV] = wgt * (rdx * rdx + rdy * rdy);
+            // rhs = R - alpha L_g(u_m^k)
+            const double al = p.alpha[m];
+            const double2 bp = make_double2(Rp.x + al * p.phibar * ud[m].x, Rp.y + al * p.phibar * ud[m].y);
+            const double2 bd = make_double2(Rd.x - al * lam * up[m].x, Rd.y - al * lam * up[m].y);
+            const double den = 1.0 / (1.0 + al * al * p.phibar * lam);
+            const double2 np = make_double2((bp.x - al * p.phibar * bd.x) * den, (bp.y - al * p.phibar * bd.y) * den);
+            const double2 nd = make_double2(bd.x + al * lam * np.x, bd.y + al * lam * np.y);
+            double2 *o = p.out + (m - p.m0) * p.ostride;
+            o[F_PHI * nc + i] = np;
+            o[F_ZETA * nc + i] = Rz;
+            o[F_DIV * nc + i] = nd;
+        }
+    }
+
+    if (p.resid_part == nullptr) return;
+    // block reduction of the residual partial sums (warp shuffle, then smem)
+    __shared__ double red[kSweepThreads / 32][M * 3];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int m = 0; m < M; ++m)
+#pragma unroll
+        for (int f = 0; f < 3; ++f) {
+            double v = rs[m][f];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            if (lane == 0) red[warp][m * 3 + f] = v;
+        }
+    __syncthreads();
+    if (threadIdx.x < M * 3) {
+        double v = 0.0;
+        for (int w = 0; w < kSweepThreads / 32; ++w) v += red[w][threadIdx.x];
+        p.resid_part[static_cast<size_t>(blockIdx.x) * M * 3 + threadIdx.x] = v;
+    }
+}
+
+// K5: fixed-order (deterministic) sum of the block partials, square root,
+// maximum over the updated nodes -> 3 doubles (Phi', zeta, div).
+__global__ void k5_resid_reduce(const double *__restrict__ part, int nblocks, int M, int m0, int m1,
+                                double *__restrict__ out3) {
+    __shared__ double acc[kMaxNodes * 3][33];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;   // one warp per (m, f)
+    for (int mf = warp; mf < M * 3; mf += blockDim.x / 32) {
+        double v = 0.0;
+        for (int b = lane; b < nblocks; b += 32) v += part[static_cast<size_t>(b) * M * 3 + mf];
+        acc[mf][lane] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        const int f = threadIdx.x;
+        double best = 0.0;
+        for (int m = m0; m < m1; ++m) {
+            double s = 0.0;
+            for (int l = 0; l < 32; ++l) s += acc[m * 3 + f][l];
+            const double r = sqrt(s);
+            best = (r > best || r != r) ? r : best;
+        }
+        out3[f] = best;
+    }
+}
+
+cudaError_t launch_sweep(const SweepParams &p, int M, cudaStream_t s, int *launches, StageTimer *timer) {
+    const int nb = sweep_blocks(p.ncoef);
+    if (timer) timer->mark(STAGE_SWEEP);
+    switch (M) {
+        case 1: k4_sweep<1><<<nb, kSweepThreads, 0, s>>>(p); break;
+        case 2: k4_sweep<2><<<nb, kSweepThreads, 0, s>>>(p); break;
+        case 3: k4_sweep<3><<<nb, kSweepThreads, 0, s>>>(p); break;
+        case 4: k4_sweep<4><<<nb, kSweepThreads, 0, s>>>(p); break;
+        case 5: k4_sweep<5><<<nb, kSweepThreads, 0, s>>>(p); break;
+        case 6: k4_sweep<6><<<nb, kSweepThreads, 0, s>>>(p); break;
+        case 7: k4_sweep<7><<<nb, kSweepThreads, 0, s>>>(p); break;
+        case 8: k4_sweep<8><<<nb, kSweepThreads, 0, s>>>(p); break;
+        default: return cudaErrorInvalidValue;
+    }
+    if (launches) *launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_resid_reduce(const double *part, int nblocks, int M, int m0, int m1, double *out3,
+                                cudaStream_t s, int *launches, StageTimer *timer) {
+    if (timer) timer->mark(STAGE_RESID);
+    k5_resid_reduce<<<1, 32 * kMaxNodes * 3 > 1024 ? 1024 : 32 * kMaxNodes * 3, 0, s>>>(part, nblocks, M, m0, m1,
+                                                                                         out3);
+    if (launches) *launches += 1;
+    return cudaGetLastError();
+}
+
+}  // namespace sdc

@@ -1,0 +1,200 @@
+// Host-side FP64 precompute: Gauss grid, normalised associated Legendre
+// table, recurrence coefficients, Radau-right collocation data, FFT plans and
+// twiddles.  Runs once in sdc_create; everything here is uploaded to the
+// device and never recomputed on the hot path.
+#include <cmath>
+#include <vector>
+
+#include "sdc_internal.h"
+
+namespace sdc {
+
+namespace {
+
+// P_n(x) and P_n'(x) by the Bonnet recurrence (n >= 1).
+void legendre_value_and_slope(int n, double x, double &p, double &dp) {
+    double pm1 = 1.0, pn = x;
+    for (int k = 2; k <= n; ++k) {
+        double pk = ((2.0 * k - 1.0) * x * pn - (k - 1.0) * pm1) / k;
+        pm1 = pn;
+        pn = pk;
+    }
+    p = pn;
+    // (1 - x^2) P_n'(x) = n (P_{n-1}(x) - x P_n(x))
+    dp = n * (pm1 - x * pn) / ((1.0 - x) * (1.0 + x));
+}
+
+}  // namespace
+
+// Gauss-Legendre rule on [-1, 1], nodes ordered north to south (mu
+// descending).  Newton's method runs in the colatitude theta = acos(mu) so
+// that the polar nodes and weights keep full relative precision; the weight
+// is 2 / ((1 - mu^2) P_J'(mu)^2) with 1 - mu^2 = sin^2(theta).
+void gauss_legendre(int J, std::vector<double> &mu, std::vector<double> &w) {
+    mu.assign(J, 0.0);
+    w.assign(J, 0.0);
+    const int half = (J + 1) / 2;
+    for (int i = 0; i < half; ++i) {
+        double th = M_PI * (i + 0.75) / (J + 0.5);
+        for (int it = 0; it < 40; ++it) {
+            const double x = std::cos(th);
+            double p, dp;
+            legendre_value_and_slope(J, x, p, dp);
+            // d/dtheta P_J(cos theta) = -sin(theta) P_J'(x)
+            const double delta = p / (-std::sin(th) * dp);
+            th -= delta;
+            if (std::fabs(delta) <= 1e-17) break;
+        }
+        const double x = std::cos(th);
+        const double s = std::sin(th);
+        double p, dp;
+        legendre_value_and_slope(J, x, p, dp);
+        // keep the (1 - x^2) P' product intact: n (P_{n-1} - x P_n) / sin(theta)
+        const double slope_times_s = dp * ((1.0 - x) * (1.0 + x)) / s;
+        const double wi = 2.0 / (slope_times_s * slope_times_s);
+        mu[i] = x;
+        w[i] = wi;
+        mu[J - 1 - i] = -x;
+        w[J - 1 - i] = wi;
+    }
+    if (J % 2 == 1) mu[J / 2] = 0.0;
+}
+
+// Radau IIA (right) nodes on [0, 1]: tau_M = 1 and the M - 1 roots of
+// P_M(x) - P_{M-1}(x) in (-1, 1), mapped by tau = (x + 1) / 2.  The roots are
+// bracketed on a fine grid and refined by bisection.  Q[m][j] integrates the
+// Lagrange basis l_j over [0, tau_m] with an M-point Gauss rule (exact for
+// polynomials of degree <= 2M - 1).
+void radau_right(int M, std::vector<double> &tau, std::vector<double> &Q) {
+    tau.assign(M, 0.0);
+    Q.assign(M * M, 0.0);
+    auto f = [M](double x) {
+        double p0 = 1.0, p1 = x;
+        if (M == 1) return p1 - p0;
+        for (int k = 2; k <= M; ++k) {
+            double pk = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+            p0 = p1;
+            p1 = pk;
+        }
+        return p1 - p0;
+    };
+    int found = 0;
+    const int ngrid = 20000;
+    double xa = -1.0, fa = f(xa);
+    for (int g = 1; g <= ngrid && found < M - 1; ++g) {
+        double xb = -1.0 + 2.0 * g / ngrid * (1.0 - 1e-9);
+        double fb = f(xb);
+        if (fa == 0.0 || (fa < 0) != (fb < 0)) {
+            double lo = xa, hi = xb, flo = fa;
+            for (int it = 0; it < 200; ++it) {
+                double mid = 0.5 * (lo + hi);
+                if (mid <= lo || mid >= hi) break;
+                double fm = f(mid);
+                if ((fm < 0) == (flo < 0)) { lo = mid; flo = fm; } else { hi = mid; }
+            }
+            tau[found++] = 0.5 * (0.5 * (lo + hi) + 1.0);
+        }
+        xa = xb;
+        fa = fb;
+    }
+    tau[M - 1] = 1.0;
+    std::vector<double> gx, gw;
+    gauss_legendre(M, gx, gw);
+    for (int m = 0; m < M; ++m) {
+        for (int j = 0; j < M; ++j) {
+            double acc = 0.0;
+            for (int q = 0; q < M; ++q) {
+                double s = 0.5 * tau[m] * (gx[q] + 1.0);
+                double l = 1.0;
+                for (int k = 0; k < M; ++k)
+                    if (k != j) l *= (s - tau[k]) / (tau[j] - tau[k]);
+                acc += gw[q] * l;
+            }
+            Q[m * M + j] = 0.5 * tau[m] * acc;
+        }
+    }
+}
+
+// Normalised associated Legendre functions (unit L2 norm on [-1, 1], no
+// Condon-Shortley phase) at the northern Gauss latitudes, degrees m..T+1.
+// Pbar_0^0 = 1/sqrt(2), Pbar_m^m = sqrt((2m+1)/(2m)) sqrt(1-mu^2) Pbar_{m-1}^{m-1},
+// Pbar_n^m = (mu Pbar_{n-1}^m - eps_{n-1}^m Pbar_{n-2}^m) / eps_n^m.
+void legendre_table(int T, int J2, int J2p, const std::vector<double> &mu, std::vector<double> &table) {
+    const int next = (T + 1) * (T + 4) / 2;
+    table.assign(static_cast<size_t>(next) * J2p, 0.0);
+    std::vector<double> eps;
+    epsilon_table(T, eps);
+    for (int j = 0; j < J2; ++j) {
+        const double x = mu[j];
+        const double s = std::sqrt((1.0 - x) * (1.0 + x));
+        double pmm = 1.0 / std::sqrt(2.0);
+        for (int m = 0; m <= T; ++m) {
+            if (m > 0) pmm *= std::sqrt((2.0 * m + 1.0) / (2.0 * m)) * s;
+            const int base = ext_offset(T, m);
+            double p2 = 0.0, p1 = pmm;
+            table[static_cast<size_t>(base) * J2p + j] = pmm;
+            for (int n = m + 1; n <= T + 1; ++n) {
+                const double e_n = eps[base + n - m];
+                const double e_n1 = eps[base + n - 1 - m];
+                const double p = (x * p1 - e_n1 * p2) / e_n;
+                table[static_cast<size_t>(base + n - m) * J2p + j] = p;
+                p2 = p1;
+                p1 = p;
+            }
+        }
+    }
+}
+
+void epsilon_table(int T, std::vector<double> &eps) {
+    const int next = (T + 1) * (T + 4) / 2;
+    eps.assign(next, 0.0);
+    for (int m = 0; m <= T; ++m)
+        for (int n = m; n <= T + 1; ++n) {
+            const double nn = n, mm = m;
+            eps[ext_offset(T, m) + n - m] = n == 0 ? 0.0 : std::sqrt((nn * nn - mm * mm) / (4.0 * nn * nn - 1.0));
+        }
+}
+
+bool fft_plan(int L, FftPlan &plan) {
+    plan.L = L;
+    plan.nstages = 0;
+    int rest = L;
+    while (rest % 4 == 0) { plan.radix[plan.nstages++] = 4; rest /= 4; }
+    if (rest % 2 == 0) { plan.radix[plan.nstages++] = 2; rest /= 2; }
+    while (rest % 3 == 0) {
+        if (plan.nstages >= kMaxStages) return false;
+        plan.radix[plan.nstages++] = 3;
+        rest /= 3;
+    }
+    return rest == 1 && plan.nstages <= kMaxStages;
+}
+
+// e^{-2 pi i k / L}: the angle is folded into [0, pi/4] with exact integer
+// arithmetic before calling sin/cos.
+void twiddles(int L, std::vector<double> &re, std::vector<double> &im) {
+    re.assign(L, 0.0);
+    im.assign(L, 0.0);
+    const double unit = 2.0 * M_PI / (8.0 * L);   // angle of 1/(8L) of a turn
+    for (int k = 0; k < L; ++k) {
+        // angle = 2 pi k / L = unit * 8k; work with a = 8k in [0, 8L)
+        long long a = 8LL * k;
+        double sgn_s = 1.0;
+        if (a > 4LL * L) { a = 8LL * L - a; sgn_s = -1.0; }         // theta -> 2pi - theta
+        double sgn_c = 1.0;
+        if (a > 2LL * L) { a = 4LL * L - a; sgn_c = -1.0; }         // theta -> pi - theta
+        double c, s;
+        if (a > L) {                                                 // theta -> pi/2 - theta
+            const double t = unit * static_cast<double>(2LL * L - a);
+            c = std::sin(t);
+            s = std::cos(t);
+        } else {
+            const double t = unit * static_cast<double>(a);
+            c = std::cos(t);
+            s = std::sin(t);
+        }
+        re[k] = sgn_c * c;
+        im[k] = -sgn_s * s;    // forward kernel e^{-i theta}
+    }
+}
+
+}  // namespace sdc

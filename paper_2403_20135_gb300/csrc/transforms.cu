@@ -1,0 +1,564 @@
+// Explicit tendency T_E = L_c + N_a + N_r (Eq. (4)) through the spherical
+// harmonic transform, for a batch of B node states (the paper's parallel
+// node loop of Algorithm 2 becomes the batch dimension of each launch).
+//
+//   K1 synthesis  (per order m):   spectral -> Fourier coefficients on the
+//                                  northern latitudes, split by the parity of
+//                                  n - m (even/odd symmetry about the equator)
+//   K2 ring       (per ring pair): inverse FFT -> grid products -> forward FFT
+//   K3 analysis   (per order m):   Fourier -> spectral, with the vector
+//                                  (div/curl) epilogue written out per mode
+//
+// The (1 - mu^2) d/dmu terms of the vector transforms are moved onto the
+// coefficients with the recurrence
+//   H_n^m = (1-mu^2) dPbar_n^m/dmu = -n eps_{n+1} Pbar_{n+1} + (n+1) eps_n Pbar_{n-1},
+// so both contractions use the one table Pbar_n^m, n = m..T+1.  This is the
+// same discrete operator as the direct H sums, up to rounding.
+//
+// Templated on the arithmetic type R (double for SDC_FP64, float for the
+// FP32 mixed mode); spectral inputs and outputs are always FP64.
+#include <cuda_runtime.h>
+
+#include "sdc_internal.h"
+
+namespace sdc {
+
+template <typename R> struct V2t;
+template <> struct V2t<double> { using type = double2; };
+template <> struct V2t<float> { using type = float2; };
+template <typename R> using V2 = typename V2t<R>::type;
+
+template <typename R> __device__ __forceinline__ V2<R> mk(R x, R y) { V2<R> v; v.x = x; v.y = y; return v; }
+template <typename R> __device__ __forceinline__ V2<R> cadd(V2<R> a, V2<R> b) { return mk<R>(a.x + b.x, a.y + b.y); }
+template <typename R> __device__ __forceinline__ V2<R> csub(V2<R> a, V2<R> b) { return mk<R>(a.x - b.x, a.y - b.y); }
+template <typename R> __device__ __forceinline__ V2<R> cmul(V2<R> a, V2<R> b) {
+    return mk<R>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <typename R> __device__ __forceinline__ V2<R> cscale(V2<R> a, R s) { return mk<R>(a.x * s, a.y * s); }
+// multiply by +i or -i
+template <typename R> __device__ __forceinline__ V2<R> mul_i(V2<R> a) { return mk<R>(-a.y, a.x); }
+template <typename R> __device__ __forceinline__ V2<R> mul_mi(V2<R> a) { return mk<R>(a.y, -a.x); }
+
+// ---------------------------------------------------------------------------
+// K1: synthesis.  grid (T+1 orders, B states, ceil(J2/blockDim) latitude
+// chunks).  Output F1[b][j][field][parity][m], fields (zeta, Phi', U, V).
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void k1_synthesis(const double2 *__restrict__ states, long long sstride, Dims d,
+                             const R *__restrict__ pbar, const double *__restrict__ eps,
+                             V2<R> *__restrict__ f1) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    V2<R> *cf = reinterpret_cast<V2<R> *>(smem_raw);   // [nn][4]
+    const int m = blockIdx.x;
+    const int b = blockIdx.y;
+    const int T = d.T;
+    const int nn = T + 2 - m;                            // n' = m..T+1
+    const double2 *st = states + b * sstride;
+    const int off = order_offset(T, m);
+    const int eoff = ext_offset(T, m);
+    const double a = d.a, inv_a = 1.0 / d.a;
+
+    // psi_n = -a^2 zeta_n / (n(n+1)) (zero outside m..T and at n = 0); the
+    // same map takes div to chi.
+    auto pot = [&](int field, int n) -> double2 {
+        if (n < m || n > T || n == 0) return make_double2(0.0, 0.0);
+        const double2 v = st[field * d.ncoef + off + n - m];
+        const double s = -a * a / (double(n) * double(n + 1));
+        return make_double2(s * v.x, s * v.y);
+    };
+    for (int t = threadIdx.x; t < nn; t += blockDim.x) {
+        const int n = m + t;
+        double2 z = make_double2(0.0, 0.0), p = z;
+        if (n <= T) {
+            z = st[F_ZETA * d.ncoef + off + t];
+            p = st[F_PHI * d.ncoef + off + t];
+        }
+        // tilde-coefficients: sum_n c_n H_n = sum_n' Pbar_n' ctilde_n'
+        const double elo = (n - 1 >= m) ? -(n - 1.0) * eps[eoff + t] : 0.0;     // -(n'-1) eps_{n'}
+        const double ehi = (n + 1 <= T) ? (n + 2.0) * eps[eoff + t + 1] : 0.0;   // (n'+2) eps_{n'+1}
+        const double2 psm = pot(F_ZETA, n - 1), psp = pot(F_ZETA, n + 1), ps0 = pot(F_ZETA, n);
+        const double2 chm = pot(F_DIV, n - 1), chp = pot(F_DIV, n + 1), ch0 = pot(F_DIV, n);
+        const double2 pst = make_double2(elo * psm.x + ehi * psp.x, elo * psm.y + ehi * psp.y);
+        const double2 cht = make_double2(elo * chm.x + ehi * chp.x, elo * chm.y + ehi * chp.y);
+        const double mm = m;
+        // a U-coef = i m chi - psi~ ;  a V-coef = i m psi + chi~
+        const double2 uc = make_double2((-mm * ch0.y - pst.x) * inv_a, (mm * ch0.x - pst.y) * inv_a);
+        const double2 vc = make_double2((-mm * ps0.y + cht.x) * inv_a, (mm * ps0.x + cht.y) * inv_a);
+        cf[t * 4 + G_ZETA] = mk<R>(R(z.x), R(z.y));
+        cf[t * 4 + G_PHI] = mk<R>(R(p.x), R(p.y));
+        cf[t * 4 + G_U] = mk<R>(R(uc.x), R(uc.y));
+        cf[t * 4 + G_V] = mk<R>(R(vc.x), R(vc.y));
+    }
+    __syncthreads();
+
+    const int j = blockIdx.z * blockDim.x + threadIdx.x;
+    if (j >= d.J2) return;
+    V2<R> ae[4], ao[4];
+#pragma unroll
+    for (int f = 0; f < 4; ++f) { ae[f] = mk<R>(0, 0); ao[f] = mk<R>(0, 0); }
+    const R *prow = pbar + static_cast<size_t>(eoff) * d.J2p + j;
+    int t = 0;
+    for (; t + 1 < nn; t += 2) {
+        const R pe = prow[static_cast<size_t>(t) * d.J2p];
+        const R po = prow[static_cast<size_t>(t + 1) * d.J2p];
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+            const V2<R> ce = cf[t * 4 + f], co = cf[(t + 1) * 4 + f];
+            ae[f].x = fma(pe, ce.x, ae[f].x);
+            ae[f].y = fma(pe, ce.y, ae[f].y);
+            ao[f].x = fma(po, co.x, ao[f].x);
+            ao[f].y = fma(po, co.y, ao[f].y);
+        }
+    }
+    if (t < nn) {
+        const R pe = prow[static_cast<size_t>(t) * d.J2p];
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+            const V2<R> ce = cf[t * 4 + f];
+            ae[f].x = fma(pe, ce.x, ae[f].x);
+            ae[f].y = fma(pe, ce.y, ae[f].y);
+        }
+    }
+    V2<R> *o = f1 + (static_cast<size_t>(b) * d.J2 + j) * (4 * 2 * (T + 1));
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+        o[(f * 2 + 0) * (T + 1) + m] = ae[f];
+        o[(f * 2 + 1) * (T + 1) + m] = ao[f];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Mixed radix (4, 2, 3) Stockham FFT of nb length-L sequences in shared
+// memory, all threads of the block cooperating.  Forward: e^{-i...};
+// inverse: e^{+i...}, unscaled.  Returns the buffer that holds the result.
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ void butterfly(V2<R> *v, int radix, bool inv) {
+    if (radix == 4) {
+        const V2<R> a0 = cadd<R>(v[0], v[2]), a1 = csub<R>(v[0], v[2]);
+        const V2<R> b0 = cadd<R>(v[1], v[3]), b1 = csub<R>(v[1], v[3]);
+        v[0] = cadd<R>(a0, b0);
+        v[2] = csub<R>(a0, b0);
+        const V2<R> ib1 = inv ? mul_i<R>(b1) : mul_mi<R>(b1);
+        v[1] = cadd<R>(a1, ib1);
+        v[3] = csub<R>(a1, ib1);
+    } else if (radix == 2) {
+        const V2<R> a = v[0];
+        v[0] = cadd<R>(a, v[1]);
+        v[1] = csub<R>(a, v[1]);
+    } else {   // 3
+        const R h = R(0.86602540378443864676);   // sqrt(3)/2
+        const V2<R> t1 = cadd<R>(v[1], v[2]);
+        const V2<R> t2 = csub<R>(v[0], cscale<R>(t1, R(0.5)));
+        V2<R> t3 = cscale<R>(csub<R>(v[1], v[2]), inv ? h : -h);
+        const V2<R> it3 = mul_i<R>(t3);
+        v[0] = cadd<R>(v[0], t1);
+        v[1] = cadd<R>(t2, it3);
+        v[2] = csub<R>(t2, it3);
+    }
+}
+
+template <typename R>
+__device__ V2<R> *fft_batch(V2<R> *x, V2<R> *y, int nb, const FftPlan &plan,
+                            const V2<R> *__restrict__ tw, bool inv) {
+    const int L = plan.L;
+    V2<R> *src = x, *dst = y;
+    int Ns = 1;
+    for (int s = 0; s < plan.nstages; ++s) {
+        const int radix = plan.radix[s];
+        const int Lr = L / radix;
+        const int tws = L / (Ns * radix);
+        for (int idx = threadIdx.x; idx < nb * Lr; idx += blockDim.x) {
+            const int bb = idx / Lr;
+            const int j = idx - bb * Lr;
+            const V2<R> *in = src + bb * L;
+            V2<R> *out = dst + bb * L;
+            const int k = j % Ns;
+            V2<R> v[4];
+            v[0] = in[j];
+            for (int r = 1; r < radix; ++r) {
+                V2<R> w = tw[r * k * tws];
+                if (inv) w.y = -w.y;
+                v[r] = cmul<R>(in[j + r * Lr], w);
+            }
+            butterfly<R>(v, radix, inv);
+            const int base = (j - k) * radix + k;
+            for (int r = 0; r < radix; ++r) out[base + r * Ns] = v[r];
+        }
+        __syncthreads();
+        V2<R> *t = src; src = dst; dst = t;
+        Ns *= radix;
+    }
+    return src;
+}
+
+// FFT of nb arrays starting at data (stride L) using `scratch` arrays of
+// scratch space, in batches; results land back in data.
+template <typename R>
+__device__ void fft_inplace(V2<R> *data, V2<R> *scratch, int nscratch, int nb, const FftPlan &plan,
+                            const V2<R> *__restrict__ tw, bool inv) {
+    for (int b0 = 0; b0 < nb; b0 += nscratch) {
+        const int cnt = min(nscratch, nb - b0);
+        V2<R> *x = data + b0 * plan.L;
+        V2<R> *res = fft_batch<R>(x, scratch, cnt, plan, tw, inv);
+        if (res != x) {
+            for (int i = threadIdx.x; i < cnt * plan.L; i += blockDim.x) x[i] = res[i];
+            __syncthreads();
+        }
+    }
+}
+
+size_t ring_smem_bytes(int L, int elem_bytes, int *scratch_arrays) {
+    const size_t cap = 227 * 1024;
+    for (int s = 5; s >= 1; --s) {
+        const size_t bytes = static_cast<size_t>(5 + s) * L * elem_bytes;
+        if (bytes <= cap) {
+            if (scratch_arrays) *scratch_arrays = s;
+            return bytes;
+        }
+    }
+    if (scratch_arrays) *scratch_arrays = 0;
+    return 0;
+}
+
+// ---------------------------------------------------------------------------
+// K2: one block per (latitude pair j2, state b).  The north ring (mu_j > 0)
+// and its mirror (mu = -mu_j) travel together as the real and imaginary
+// parts of one complex sequence.
+// Input  F1[b][j2][4][2][T+1]; output F2[b][m][5][2][J2] =
+//   w~_j (G_north + G_south) (parity 0), w~_j (G_north - G_south) (parity 1)
+// for G in (A, B, C, D) = (eta U, eta V, Phi' U, Phi' V), weight w~ = w/(1-mu^2);
+// G = E = (U^2 + V^2) / (2 (1 - mu^2)) uses the plain Gauss weight w.
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void k2_ring(const V2<R> *__restrict__ f1, V2<R> *__restrict__ f2, Dims d, FftPlan plan,
+                        const V2<R> *__restrict__ tw, const double *__restrict__ mu,
+                        const double *__restrict__ w, int nscratch) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    V2<R> *X = reinterpret_cast<V2<R> *>(smem_raw);   // [5][L]
+    V2<R> *S = X + 5 * plan.L;                          // [nscratch][L]
+    const int j2 = blockIdx.x;
+    const int b = blockIdx.y;
+    const int T = d.T, L = plan.L;
+    const V2<R> *in = f1 + (static_cast<size_t>(b) * d.J2 + j2) * (4 * 2 * (T + 1));
+
+    // Hermitian packing of north (real part) and south (imaginary part).
+    for (int i = threadIdx.x; i < 4 * L; i += blockDim.x) {
+        const int f = i / L, k = i - f * L;
+        V2<R> z = mk<R>(0, 0);
+        int m = -1;
+        bool conj = false;
+        if (k <= T) m = k;
+        else if (k >= L - T) { m = L - k; conj = true; }
+        if (m >= 0) {
+            V2<R> e = in[(f * 2 + 0) * (T + 1) + m];
+            V2<R> o = in[(f * 2 + 1) * (T + 1) + m];
+            if (m == 0) { e.y = 0; o.y = 0; }
+            V2<R> n = cadd<R>(e, o), s = csub<R>(e, o);
+            if (conj) { n.y = -n.y; s.y = -s.y; }
+            z = mk<R>(n.x - s.y, n.y + s.x);       // n + i s
+        }
+        X[f * L + k] = z;
+    }
+    __syncthreads();
+    fft_inplace<R>(X, S, nscratch, 4, plan, tw, true);
+
+    const double mun = mu[j2];
+    const R cosl2 = R((1.0 - mun) * (1.0 + mun));
+    const R fN = R(d.two_omega * mun);
+    const R inv2c = R(0.5) / cosl2;
+    for (int k = threadIdx.x; k < L; k += blockDim.x) {
+        const V2<R> zz = X[G_ZETA * L + k], pp = X[G_PHI * L + k];
+        const V2<R> uu = X[G_U * L + k], vv = X[G_V * L + k];
+        // .x = north ring, .y = south ring (where f = -fN)
+        const R etaN = zz.x + fN, etaS = zz.y - fN;
+        X[P_A * L + k] = mk<R>(etaN * uu.x, etaS * uu.y);
+        X[P_B * L + k] = mk<R>(etaN * vv.x, etaS * vv.y);
+        X[P_C * L + k] = mk<R>(pp.x * uu.x, pp.y * uu.y);
+        X[P_D * L + k] = mk<R>(pp.x * vv.x, pp.y * vv.y);
+        X[P_E * L + k] = mk<R>((uu.x * uu.x + vv.x * vv.x) * inv2c, (uu.y * uu.y + vv.y * vv.y) * inv2c);
+    }
+    __syncthreads();
+    fft_inplace<R>(X, S, nscratch, 5, plan, tw, false);
+
+    const double wj = w[j2];
+    const R wt = R(wj / ((1.0 - mun) * (1.0 + mun)));
+    const R wp = R(wj);
+    const R invL = R(1.0) / R(L);
+    for (int i = threadIdx.x; i < 5 * (T + 1); i += blockDim.x) {
+        const int g = i / (T + 1), m = i - g * (T + 1);
+        const V2<R> y = X[g * L + m];
+        V2<R> yc = X[g * L + (m == 0 ? 0 : L - m)];
+        yc.y = -yc.y;
+        // north = (y + conj y_{L-m}) / 2, south = -i (y - conj y_{L-m}) / 2
+        const V2<R> gn = cscale<R>(cadd<R>(y, yc), R(0.5) * invL);
+        const V2<R> gs = cscale<R>(mul_mi<R>(csub<R>(y, yc)), R(0.5) * invL);
+        const R wg = (g == P_E) ? wp : wt;
+        V2<R> *o = f2 + ((static_cast<size_t>(b) * (T + 1) + m) * 5 + g) * 2 * d.J2 + j2;
+        o[0] = cscale<R>(cadd<R>(gn, gs), wg);
+        o[d.J2] = cscale<R>(csub<R>(gn, gs), wg);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// K3: one block per (order m, state b).  Projections
+//   G^_n' = sum_j2 Pbar_n'(mu_j) W_g[parity(n'-m)][j2],  n' = m..T+1,
+// then per mode n = m..T (1/a folded in here):
+//   T_E(zeta)_n = -(1/a) [i m A^_n + n eps_{n+1} B^_{n+1} - (n+1) eps_n B^_{n-1}]
+//   T_E(div)_n  =  (1/a) [i m B^_n - n eps_{n+1} A^_{n+1} + (n+1) eps_n A^_{n-1}] + lambda_n E^_n
+//   T_E(Phi')_n = -(1/a) [i m C^_n + n eps_{n+1} D^_{n+1} - (n+1) eps_n D^_{n-1}]
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void k3_analysis(const V2<R> *__restrict__ f2, Dims d, const R *__restrict__ pbar,
+                            const double *__restrict__ eps, double2 *__restrict__ tend,
+                            long long tstride) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int m = blockIdx.x;
+    const int b = blockIdx.y;
+    const int T = d.T;
+    const int J2 = d.J2;
+    const int nn = T + 2 - m;
+    V2<R> *W = reinterpret_cast<V2<R> *>(smem_raw);                  // [5][2][J2]
+    double2 *Y = reinterpret_cast<double2 *>(smem_raw + ((10 * J2 * sizeof(V2<R>) + 15) / 16) * 16);  // [nn][5]
+    const V2<R> *src = f2 + (static_cast<size_t>(b) * (T + 1) + m) * 10 * J2;
+    for (int i = threadIdx.x; i < 10 * J2; i += blockDim.x) W[i] = src[i];
+    __syncthreads();
+
+    const int eoff = ext_offset(T, m);
+    for (int t = threadIdx.x; t < nn; t += blockDim.x) {
+        const int par = t & 1;
+        V2<R> acc[5];
+#pragma unroll
+        for (int g = 0; g < 5; ++g) acc[g] = mk<R>(0, 0);
+        const R *prow = pbar + static_cast<size_t>(eoff + t) * d.J2p;
+        for (int j = 0; j < J2; ++j) {
+            const R p = prow[j];
+#pragma unroll
+            for (int g = 0; g < 5; ++g) {
+                const V2<R> wv = W[(g * 2 + par) * J2 + j];
+                acc[g].x = fma(p, wv.x, acc[g].x);
+                acc[g].y = fma(p, wv.y, acc[g].y);
+            }
+        }
+#pragma unroll
+        for (int g = 0; g < 5; ++g) Y[t * 5 + g] = make_double2(double(acc[g].x), double(acc[g].y));
+    }
+    __syncthreads();
+
+    const double inv_a = 1.0 / d.a;
+    const int off = order_offset(T, m);
+    const double mm = m;
+    double2 *out = tend + b * tstride;
+    for (int t = threadIdx.x; t < nn - 1; t += blockDim.x) {
+        const int n = m + t;
+        const double cu = n * eps[eoff + t + 1];                        // n eps_{n+1}
+        const double cl = (t > 0) ? (n + 1.0) * eps[eoff + t] : 0.0;    // (n+1) eps_n
+        const double2 z0 = make_double2(0.0, 0.0);
+        const double2 Ah = Y[t * 5 + P_A], Bh = Y[t * 5 + P_B], Ch = Y[t * 5 + P_C];
+        const double2 Eh = Y[t * 5 + P_E];
+        const double2 Au = Y[(t + 1) * 5 + P_A], Bu = Y[(t + 1) * 5 + P_B], Du = Y[(t + 1) * 5 + P_D];
+        const double2 Al = t > 0 ? Y[(t - 1) * 5 + P_A] : z0;
+        const double2 Bl = t > 0 ? Y[(t - 1) * 5 + P_B] : z0;
+        const double2 Dl = t > 0 ? Y[(t - 1) * 5 + P_D] : z0;
+        const double lam = double(n) * double(n + 1) * inv_a * inv_a;
+        double2 tz, td, tp;
+        // i m X = (-m X.y, m X.x)
+        tz.x = -inv_a * (-mm * Ah.y + cu * Bu.x - cl * Bl.x);
+        tz.y = -inv_a * (mm * Ah.x + cu * Bu.y - cl * Bl.y);
+        td.x = inv_a * (-mm * Bh.y - cu * Au.x + cl * Al.x) + lam * Eh.x;
+        td.y = inv_a * (mm * Bh.x - cu * Au.y + cl * Al.y) + lam * Eh.y;
+        tp.x = -inv_a * (-mm * Ch.y + cu * Du.x - cl * Dl.x);
+        tp.y = -inv_a * (mm * Ch.x + cu * Du.y - cl * Dl.y);
+        out[F_PHI * d.ncoef + off + t] = tp;
+        out[F_ZETA * d.ncoef + off + t] = tz;
+        out[F_DIV * d.ncoef + off + t] = td;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+__global__ void k_scalar_ring_inverse(const double2 *__restrict__ f1, double *__restrict__ grid, Dims d,
+                                      FftPlan plan, const double2 *__restrict__ tw);
+__global__ void k_scalar_ring_forward(const double *__restrict__ grid, double2 *__restrict__ f2, Dims d,
+                                      FftPlan plan, const double2 *__restrict__ tw,
+                                      const double *__restrict__ w);
+constexpr int kK1Threads = 64;
+constexpr int kK2Threads = 256;
+constexpr int kK3Threads = 128;
+
+template <typename R>
+static size_t k3_smem(const Dims &d) {
+    return ((10 * d.J2 * sizeof(V2<R>) + 15) / 16) * 16 + static_cast<size_t>(d.T + 2) * 5 * sizeof(double2);
+}
+
+template <typename R>
+static cudaError_t configure(const Dims &d, const FftPlan &plan) {
+    const size_t sm2 = ring_smem_bytes(plan.L, sizeof(V2<R>), nullptr);
+    if (sm2 == 0) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(k2_ring<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k3_analysis<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k3_smem<R>(d));
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k1_synthesis<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(static_cast<size_t>(d.T + 2) * 4 * sizeof(V2<R>)));
+}
+
+template <typename R>
+static cudaError_t launch_tendency(const Dims &d, const FftPlan &plan, int B, const double2 *states,
+                                   long long sstride, double2 *tend, long long tstride, const R *pbar,
+                                   const double *eps, const double *mu, const double *w,
+                                   const V2<R> *tw, V2<R> *f1, V2<R> *f2, cudaStream_t s,
+                                   int *launches, StageTimer *timer) {
+    const size_t sm1 = static_cast<size_t>(d.T + 2) * 4 * sizeof(V2<R>);
+    dim3 g1(d.T + 1, B, (d.J2 + kK1Threads - 1) / kK1Threads);
+    int nscratch = 0;
+    const size_t sm2 = ring_smem_bytes(d.L, sizeof(V2<R>), &nscratch);
+    if (sm2 == 0) return cudaErrorInvalidValue;
+    if (timer) timer->mark(STAGE_SYNTH);
+    k1_synthesis<R><<<g1, kK1Threads, sm1, s>>>(states, sstride, d, pbar, eps, f1);
+    if (timer) timer->mark(STAGE_RING);
+    k2_ring<R><<<dim3(d.J2, B), kK2Threads, sm2, s>>>(f1, f2, d, plan, tw, mu, w, nscratch);
+    if (timer) timer->mark(STAGE_ANALYSIS);
+    k3_analysis<R><<<dim3(d.T + 1, B), kK3Threads, k3_smem<R>(d), s>>>(f2, d, pbar, eps, tend, tstride);
+    if (launches) *launches += 3;
+    return cudaGetLastError();
+}
+
+cudaError_t configure_transform_kernels(const Dims &d, const FftPlan &plan, bool fp32) {
+    cudaError_t e = fp32 ? configure<float>(d, plan) : configure<double>(d, plan);
+    if (e != cudaSuccess) return e;
+    const size_t sm = 2 * static_cast<size_t>(plan.L) * sizeof(double2);
+    e = cudaFuncSetAttribute(k_scalar_ring_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_scalar_ring_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+}
+
+cudaError_t launch_tendency_f64(const Dims &d, const FftPlan &plan, int B, const double2 *states,
+                                long long sstride, double2 *tend, long long tstride, const double *pbar,
+                                const double *eps, const double *lam, const double *mu, const double *w,
+                                const double2 *tw, double2 *f1, double2 *f2, cudaStream_t s, int *launches,
+                                StageTimer *timer) {
+    (void)lam;
+    return launch_tendency<double>(d, plan, B, states, sstride, tend, tstride, pbar, eps, mu, w, tw, f1, f2, s,
+                                   launches, timer);
+}
+
+cudaError_t launch_tendency_f32(const Dims &d, const FftPlan &plan, int B, const double2 *states,
+                                long long sstride, double2 *tend, long long tstride, const float *pbar,
+                                const double *eps, const double *lam, const double *mu, const double *w,
+                                const float2 *tw, float2 *f1, float2 *f2, cudaStream_t s, int *launches,
+                                StageTimer *timer) {
+    (void)lam;
+    return launch_tendency<float>(d, plan, B, states, sstride, tend, tstride, pbar, eps, mu, w, tw, f1, f2, s,
+                                  launches, timer);
+}
+
+// ---------------------------------------------------------------------------
+// Scalar transforms (FP64), for initial states and grid diagnostics.
+// ---------------------------------------------------------------------------
+__global__ void k_scalar_synthesis(const double2 *__restrict__ spec, Dims d, const double *__restrict__ pbar,
+                                   double2 *__restrict__ f1) {
+    const int m = blockIdx.x;
+    const int j = blockIdx.y * blockDim.x + threadIdx.x;
+    if (j >= d.J2) return;
+    const int T = d.T, nn = T + 1 - m;
+    const int off = order_offset(T, m), eoff = ext_offset(T, m);
+    double2 se = make_double2(0, 0), so = se;
+    for (int t = 0; t < nn; ++t) {
+        const double p = pbar[static_cast<size_t>(eoff + t) * d.J2p + j];
+        const double2 c = spec[off + t];
+        if (t & 1) { so.x = fma(p, c.x, so.x); so.y = fma(p, c.y, so.y); }
+        else { se.x = fma(p, c.x, se.x); se.y = fma(p, c.y, se.y); }
+    }
+    f1[(static_cast<size_t>(j) * 2 + 0) * (T + 1) + m] = se;
+    f1[(static_cast<size_t>(j) * 2 + 1) * (T + 1) + m] = so;
+}
+
+__global__ void k_scalar_ring_inverse(const double2 *__restrict__ f1, double *__restrict__ grid, Dims d,
+                                      FftPlan plan, const double2 *__restrict__ tw) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double2 *X = reinterpret_cast<double2 *>(smem_raw);
+    double2 *S = X + plan.L;
+    const int j2 = blockIdx.x, T = d.T, L = plan.L;
+    const double2 *in = f1 + static_cast<size_t>(j2) * 2 * (T + 1);
+    for (int k = threadIdx.x; k < L; k += blockDim.x) {
+        double2 z = make_double2(0, 0);
+        int m = -1;
+        bool conj = false;
+        if (k <= T) m = k;
+        else if (k >= L - T) { m = L - k; conj = true; }
+        if (m >= 0) {
+            double2 e = in[m], o = in[(T + 1) + m];
+            if (m == 0) { e.y = 0; o.y = 0; }
+            double2 n = make_double2(e.x + o.x, e.y + o.y), s = make_double2(e.x - o.x, e.y - o.y);
+            if (conj) { n.y = -n.y; s.y = -s.y; }
+            z = make_double2(n.x - s.y, n.y + s.x);
+        }
+        X[k] = z;
+    }
+    __syncthreads();
+    fft_inplace<double>(X, S, 1, 1, plan, tw, true);
+    for (int k = threadIdx.x; k < L; k += blockDim.x) {
+        grid[static_cast<size_t>(j2) * L + k] = X[k].x;
+        grid[static_cast<size_t>(d.J - 1 - j2) * L + k] = X[k].y;
+    }
+}
+
+__global__ void k_scalar_ring_forward(const double *__restrict__ grid, double2 *__restrict__ f2, Dims d,
+                                      FftPlan plan, const double2 *__restrict__ tw,
+                                      const double *__restrict__ w) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double2 *X = reinterpret_cast<double2 *>(smem_raw);
+    double2 *S = X + plan.L;
+    const int j2 = blockIdx.x, T = d.T, L = plan.L;
+    for (int k = threadIdx.x; k < L; k += blockDim.x)
+        X[k] = make_double2(grid[static_cast<size_t>(j2) * L + k], grid[static_cast<size_t>(d.J - 1 - j2) * L + k]);
+    __syncthreads();
+    fft_inplace<double>(X, S, 1, 1, plan, tw, false);
+    const double wj = w[j2], invL = 1.0 / L;
+    for (int m = threadIdx.x; m <= T; m += blockDim.x) {
+        const double2 y = X[m];
+        double2 yc = X[m == 0 ? 0 : L - m];
+        yc.y = -yc.y;
+        const double2 gn = make_double2(0.5 * invL * (y.x + yc.x), 0.5 * invL * (y.y + yc.y));
+        const double2 gs = make_double2(0.5 * invL * (y.y - yc.y), -0.5 * invL * (y.x - yc.x));
+        f2[(static_cast<size_t>(m) * 2 + 0) * d.J2 + j2] = make_double2(wj * (gn.x + gs.x), wj * (gn.y + gs.y));
+        f2[(static_cast<size_t>(m) * 2 + 1) * d.J2 + j2] = make_double2(wj * (gn.x - gs.x), wj * (gn.y - gs.y));
+    }
+}
+
+__global__ void k_scalar_analysis(const double2 *__restrict__ f2, Dims d, const double *__restrict__ pbar,
+                                  double2 *__restrict__ spec) {
+    const int m = blockIdx.x, T = d.T;
+    const int off = order_offset(T, m), eoff = ext_offset(T, m);
+    for (int t = threadIdx.x; t <= T - m; t += blockDim.x) {
+        const double2 *W = f2 + (static_cast<size_t>(m) * 2 + (t & 1)) * d.J2;
+        const double *prow = pbar + static_cast<size_t>(eoff + t) * d.J2p;
+        double2 acc = make_double2(0, 0);
+        for (int j = 0; j < d.J2; ++j) {
+            acc.x = fma(prow[j], W[j].x, acc.x);
+            acc.y = fma(prow[j], W[j].y, acc.y);
+        }
+        spec[off + t] = acc;
+    }
+}
+
+cudaError_t launch_spec_to_grid(const Dims &d, const FftPlan &plan, const double2 *spec, double *grid,
+                                const double *pbar, const double2 *tw, double2 *f1, cudaStream_t s) {
+    k_scalar_synthesis<<<dim3(d.T + 1, (d.J2 + 63) / 64), 64, 0, s>>>(spec, d, pbar, f1);
+    const size_t sm = 2 * static_cast<size_t>(plan.L) * sizeof(double2);
+    k_scalar_ring_inverse<<<d.J2, 256, sm, s>>>(f1, grid, d, plan, tw);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_grid_to_spec(const Dims &d, const FftPlan &plan, const double *grid, double2 *spec,
+                                const double *pbar, const double *w, const double2 *tw, double2 *f2,
+                                cudaStream_t s) {
+    const size_t sm = 2 * static_cast<size_t>(plan.L) * sizeof(double2);
+    k_scalar_ring_forward<<<d.J2, 256, sm, s>>>(grid, f2, d, plan, tw, w);
+    k_scalar_analysis<<<d.T + 1, 128, 0, s>>>(f2, d, pbar, spec);
+    return cudaGetLastError();
+}
+
+}  // namespace sdc
