@@ -154,6 +154,30 @@ int sdc_profile_step(sdc_ctx *ctx, void *state, double *ms, int *launches);
 /* Launches per step of the captured step graph (HOST output). */
 int sdc_launches_per_step(const sdc_ctx *ctx, int *launches);
 
+/* Spectral-to-grid transform of one field that allocates nothing and needs no
+ * context.  The paper has no counterpart: this serves callers that cannot call
+ * cudaMalloc -- host applications that own all device memory through their
+ * own allocator and forbid other code from allocating, latency-critical loops
+ * that cannot afford cudaMalloc/cudaFree (which may synchronise the device),
+ * and processes under a fixed device-memory budget -- and therefore cannot
+ * create an sdc_ctx.  It computes what sdc_spec_to_grid computes (same sizes
+ * rules as sdc_create; spec is device double2[(T+1)(T+2)/2], grid is device
+ * double[nlat][nlon], both owned by the caller) with the Gauss nodes, Legendre
+ * functions and FFT twiddles generated on the fly.  Its only intermediate data
+ * live in a static 2 MiB device array that every GPU loading the library holds
+ * until exit: the call is rejected with SDC_EUNSUPPORTED unless
+ * (nlat/2)*2*(T+1) + ceil(nlat/4) <= 131072 complex doubles (T255 on 384
+ * latitudes fits; T511 on 768 does not).  SDC_EINVAL for NULL pointers or
+ * invalid sizes, SDC_ECUDA if a CUDA call fails; sdc_last_error() is not
+ * updated.  The first call on each device does a one-time set-up on the
+ * current device (looks up the array's device address, raises a kernel's
+ * shared-memory limit); make that first call before any stream capture.
+ * Every call shares the array: calls whose work overlaps on the GPU (several
+ * streams or host threads) race and must be serialised by the caller.
+ * Asynchronous on cuda_stream (a cudaStream_t, NULL = legacy default). */
+int sdc_spec_to_grid_static(int truncation, int nlat, int nlon, const void *spec, double *grid,
+                            void *cuda_stream);
+
 const char *sdc_strerror(int status);
 const char *sdc_last_error(void);
 

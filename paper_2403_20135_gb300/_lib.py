@@ -48,6 +48,7 @@ SIGNATURES = {
     "sdc_counters": (_I, [_P, ctypes.POINTER(_LL), ctypes.POINTER(_LL), ctypes.POINTER(_LL)]),
     "sdc_launches_per_step": (_I, [_P, ctypes.POINTER(_I)]),
     "sdc_profile_step": (_I, [_P, _P, ctypes.POINTER(_D), ctypes.POINTER(_I)]),
+    "sdc_spec_to_grid_static": (_I, [_I, _I, _I, _P, _P, _P]),
     "sdc_strerror": (ctypes.c_char_p, [_I]),
     "sdc_last_error": (ctypes.c_char_p, []),
 }

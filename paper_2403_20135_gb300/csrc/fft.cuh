@@ -1,0 +1,108 @@
+// Complex helpers and the shared-memory mixed-radix Stockham FFT used by the
+// ring kernels (device code only).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "sdc_internal.h"
+
+namespace sdc {
+
+template <typename R> struct V2t;
+template <> struct V2t<double> { using type = double2; };
+template <> struct V2t<float> { using type = float2; };
+template <typename R> using V2 = typename V2t<R>::type;
+
+template <typename R> __device__ __forceinline__ V2<R> mk(R x, R y) { V2<R> v; v.x = x; v.y = y; return v; }
+template <typename R> __device__ __forceinline__ V2<R> cadd(V2<R> a, V2<R> b) { return mk<R>(a.x + b.x, a.y + b.y); }
+template <typename R> __device__ __forceinline__ V2<R> csub(V2<R> a, V2<R> b) { return mk<R>(a.x - b.x, a.y - b.y); }
+template <typename R> __device__ __forceinline__ V2<R> cmul(V2<R> a, V2<R> b) {
+    return mk<R>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <typename R> __device__ __forceinline__ V2<R> cscale(V2<R> a, R s) { return mk<R>(a.x * s, a.y * s); }
+// multiply by +i or -i
+template <typename R> __device__ __forceinline__ V2<R> mul_i(V2<R> a) { return mk<R>(-a.y, a.x); }
+template <typename R> __device__ __forceinline__ V2<R> mul_mi(V2<R> a) { return mk<R>(a.y, -a.x); }
+
+// ---------------------------------------------------------------------------
+// Mixed radix (4, 2, 3) Stockham FFT of nb length-L sequences in shared
+// memory, all threads of the block cooperating.  Forward: e^{-i...};
+// inverse: e^{+i...}, unscaled.  Returns the buffer that holds the result.
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ void butterfly(V2<R> *v, int radix, bool inv) {
+    if (radix == 4) {
+        const V2<R> a0 = cadd<R>(v[0], v[2]), a1 = csub<R>(v[0], v[2]);
+        const V2<R> b0 = cadd<R>(v[1], v[3]), b1 = csub<R>(v[1], v[3]);
+        v[0] = cadd<R>(a0, b0);
+        v[2] = csub<R>(a0, b0);
+        const V2<R> ib1 = inv ? mul_i<R>(b1) : mul_mi<R>(b1);
+        v[1] = cadd<R>(a1, ib1);
+        v[3] = csub<R>(a1, ib1);
+    } else if (radix == 2) {
+        const V2<R> a = v[0];
+        v[0] = cadd<R>(a, v[1]);
+        v[1] = csub<R>(a, v[1]);
+    } else {   // 3
+        const R h = R(0.86602540378443864676);   // sqrt(3)/2
+        const V2<R> t1 = cadd<R>(v[1], v[2]);
+        const V2<R> t2 = csub<R>(v[0], cscale<R>(t1, R(0.5)));
+        V2<R> t3 = cscale<R>(csub<R>(v[1], v[2]), inv ? h : -h);
+        const V2<R> it3 = mul_i<R>(t3);
+        v[0] = cadd<R>(v[0], t1);
+        v[1] = cadd<R>(t2, it3);
+        v[2] = csub<R>(t2, it3);
+    }
+}
+
+template <typename R>
+__device__ V2<R> *fft_batch(V2<R> *x, V2<R> *y, int nb, const FftPlan &plan,
+                            const V2<R> *__restrict__ tw, bool inv) {
+    const int L = plan.L;
+    V2<R> *src = x, *dst = y;
+    int Ns = 1;
+    for (int s = 0; s < plan.nstages; ++s) {
+        const int radix = plan.radix[s];
+        const int Lr = L / radix;
+        const int tws = L / (Ns * radix);
+        for (int idx = threadIdx.x; idx < nb * Lr; idx += blockDim.x) {
+            const int bb = idx / Lr;
+            const int j = idx - bb * Lr;
+            const V2<R> *in = src + bb * L;
+            V2<R> *out = dst + bb * L;
+            const int k = j % Ns;
+            V2<R> v[4];
+            v[0] = in[j];
+            for (int r = 1; r < radix; ++r) {
+                V2<R> w = tw[r * k * tws];
+                if (inv) w.y = -w.y;
+                v[r] = cmul<R>(in[j + r * Lr], w);
+            }
+            butterfly<R>(v, radix, inv);
+            const int base = (j - k) * radix + k;
+            for (int r = 0; r < radix; ++r) out[base + r * Ns] = v[r];
+        }
+        __syncthreads();
+        V2<R> *t = src; src = dst; dst = t;
+        Ns *= radix;
+    }
+    return src;
+}
+
+// FFT of nb arrays starting at data (stride L) using `scratch` arrays of
+// scratch space, in batches; results land back in data.
+template <typename R>
+__device__ void fft_inplace(V2<R> *data, V2<R> *scratch, int nscratch, int nb, const FftPlan &plan,
+                            const V2<R> *__restrict__ tw, bool inv) {
+    for (int b0 = 0; b0 < nb; b0 += nscratch) {
+        const int cnt = min(nscratch, nb - b0);
+        V2<R> *x = data + b0 * plan.L;
+        V2<R> *res = fft_batch<R>(x, scratch, cnt, plan, tw, inv);
+        if (res != x) {
+            for (int i = threadIdx.x; i < cnt * plan.L; i += blockDim.x) x[i] = res[i];
+            __syncthreads();
+        }
+    }
+}
+
+}  // namespace sdc
