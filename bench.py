@@ -193,6 +193,21 @@ def time_device(s, state, steps: int, flush):
     return [a.elapsed_time(b) for a, b in zip(starts, ends)]
 
 
+def profile_stages(s, u0, flush, nprof: int):
+    """Per-kernel-class device time of nprof steps launched kernel by kernel."""
+    st = u0.clone()
+    acc = {k: [0.0, 0] for k in s.STAGES}
+    for _ in range(nprof):
+        flush.zero_()
+        for k, (ms, n) in s.profile_step(st).items():
+            acc[k][0] += ms
+            acc[k][1] += n
+    tot = max(1e-12, sum(x[0] for x in acc.values()))
+    prof = {k: {"ms_per_launch": (v[0] / v[1]) if v[1] else 0.0, "launches_per_step": v[1] // nprof,
+                "share": v[0] / tot} for k, v in acc.items()}
+    return prof, acc
+
+
 def time_e2e(s, host_state, dev_state, host_out, steps: int):
     """Host-buffer path: pinned H2D copy, one step through the C ABI, D2H copy."""
     import torch
@@ -244,18 +259,7 @@ def cuda_arm(args, rank: int, world: int):
     clocks = clk.summary()
 
     # kernel-by-kernel profile of the same step (CUDA events between launches)
-    prof_state = u0.clone()
-    prof = None
-    nprof = max(3, min(10, args.steps))
-    acc = {k: [0.0, 0] for k in Solver.STAGES}
-    for _ in range(nprof):
-        flush.zero_()
-        p = s.profile_step(prof_state)
-        for k, (ms, n) in p.items():
-            acc[k][0] += ms
-            acc[k][1] += n
-    prof = {k: {"ms_per_launch": (v[0] / v[1]) if v[1] else 0.0, "launches_per_step": v[1] // nprof,
-                "share": v[0] / max(1e-12, sum(x[0] for x in acc.values()))} for k, v in acc.items()}
+    prof, acc = profile_stages(s, u0, flush, max(3, min(10, args.steps)))
     dom = max(("synthesis", "ring", "analysis"), key=lambda k: acc[k][0])
     # average work per launch of the dominant stage: launches come with batch 1 (E0) and batch M
     K, M = wl.sweeps, wl.nodes
@@ -286,11 +290,13 @@ def cuda_arm(args, rank: int, world: int):
         for _ in range(args.warmup):
             sm.run(xs, 1)
         tm = time_device(sm, xs, args.steps, flush)
+        mprof, _ = profile_stages(sm, u0, flush, max(3, min(10, args.steps)))
         a64, a32 = u0.clone(), u0.clone()
         s.run(a64, 20)
         sm.run(a32, 20)
         err = ((a32 - a64).abs().pow(2).sum(1) / a64.abs().pow(2).sum(1)).sqrt().cpu().numpy()
         mixed = {"fp32": {"value": world * args.steps / (sum(tm) * 1e-3), "unit": "steps/s",
+                          "ms_per_step": sum(tm) / args.steps, "stages": mprof,
                           "rel_l2_vs_fp64_20_steps": {"phi": float(err[0]), "zeta": float(err[1]),
                                                       "div": float(err[2])}}}
         sm.close()

@@ -145,13 +145,15 @@ int sdc_counters(const sdc_ctx *ctx, long long *explicit_evals, long long *solve
 
 /* One step like sdc_run(ctx, state, 1), but launched kernel by kernel (not
  * from the graph) with CUDA events between the launches; synchronises.
- * HOST outputs ms[5] and launches[5] receive the summed device time and the
+ * HOST outputs ms[6] and launches[6] receive the summed device time and the
  * number of launches of each kernel class: 0 Legendre synthesis, 1 ring
- * FFT/products, 2 Legendre analysis, 3 quadrature + implicit solve (sweep),
- * 4 residual reduction. */
+ * FFT/products, 2 Legendre analysis (projections), 3 analysis epilogue
+ * (div/curl recombination per mode), 4 quadrature + implicit solve (sweep),
+ * 5 residual reduction. */
 int sdc_profile_step(sdc_ctx *ctx, void *state, double *ms, int *launches);
 
-/* Launches per step of the captured step graph (HOST output). */
+/* Launches per step of the captured step graph (HOST output): 4 per tendency
+ * batch (K per step) plus one sweep kernel per sweep. */
 int sdc_launches_per_step(const sdc_ctx *ctx, int *launches);
 
 /* Spectral-to-grid transform of one field that allocates nothing and needs no

@@ -56,12 +56,13 @@ struct sdc_ctx {
     // device tables
     double *pbar = nullptr;
     float *pbar32 = nullptr;
-    double *eps = nullptr, *lam = nullptr, *mu2 = nullptr, *w2 = nullptr;
+    double *eps = nullptr, *lam = nullptr, *mu2 = nullptr, *w2 = nullptr, *syn = nullptr;
+    int *row_m = nullptr, *coef_m = nullptr;
     double2 *tw = nullptr;
     float2 *tw32 = nullptr;
     // device workspaces
     double2 *un = nullptr, *U = nullptr, *E = nullptr, *E0 = nullptr;
-    void *f1 = nullptr, *f2 = nullptr;
+    void *f1 = nullptr, *f2 = nullptr, *f3 = nullptr;
     double *resid_part = nullptr, *resid = nullptr;
     int sweep_nblocks = 0;
 
@@ -78,8 +79,8 @@ void free_ctx(sdc_ctx *c) {
     if (!c) return;
     for (auto &g : c->graph)
         if (g) cudaGraphExecDestroy(g);
-    void *ptrs[] = {c->pbar, c->pbar32, c->eps, c->lam, c->mu2, c->w2, c->tw, c->tw32, c->un, c->U,
-                    c->E, c->E0, c->f1, c->f2, c->resid_part, c->resid};
+    void *ptrs[] = {c->pbar, c->pbar32, c->eps, c->lam, c->mu2, c->w2, c->syn, c->row_m, c->coef_m, c->tw,
+                    c->tw32, c->un, c->U, c->E, c->E0, c->f1, c->f2, c->f3, c->resid_part, c->resid};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->cap) cudaStreamDestroy(c->cap);
@@ -101,13 +102,19 @@ double qdelta_den(const sdc_ctx *c, int k) {
 
 cudaError_t tendency(sdc_ctx *c, int B, const double2 *states, long long sstride, double2 *tend,
                      long long tstride, cudaStream_t s, int *launches, StageTimer *timer = nullptr) {
-    if (c->precision == SDC_FP64)
-        return launch_tendency_f64(c->d, c->plan, B, states, sstride, tend, tstride, c->pbar, c->eps, c->lam,
-                                   c->mu2, c->w2, c->tw, static_cast<double2 *>(c->f1),
-                                   static_cast<double2 *>(c->f2), s, launches, timer);
-    return launch_tendency_f32(c->d, c->plan, B, states, sstride, tend, tstride, c->pbar32, c->eps, c->lam,
-                               c->mu2, c->w2, c->tw32, static_cast<float2 *>(c->f1),
-                               static_cast<float2 *>(c->f2), s, launches, timer);
+    const bool fp32 = c->precision != SDC_FP64;
+    DeviceTables tb{};
+    tb.pbar = fp32 ? static_cast<const void *>(c->pbar32) : static_cast<const void *>(c->pbar);
+    tb.tw = fp32 ? static_cast<const void *>(c->tw32) : static_cast<const void *>(c->tw);
+    tb.eps = c->eps;
+    tb.lam = c->lam;
+    tb.mu = c->mu2;
+    tb.w = c->w2;
+    tb.syn = c->syn;
+    tb.row_m = c->row_m;
+    tb.coef_m = c->coef_m;
+    Workspace ws{c->f1, c->f2, c->f3};
+    return launch_tendency(c->d, c->plan, fp32, B, states, sstride, tend, tstride, tb, ws, s, launches, timer);
 }
 
 // Enqueue one step u_n -> u_n (in place on c->un), Algorithm 2.
@@ -251,9 +258,12 @@ int sdc_create(sdc_ctx **out, int T, int J, int L, int M, int K, double dt, cons
     // host precompute
     gauss_legendre(J, c->mu, c->w);
     radau_right(M, c->tau, c->Q);
-    std::vector<double> table, eps, lam(d.ncoef), twr, twi;
+    std::vector<double> table, eps, lam(d.ncoef), twr, twi, syn;
+    std::vector<int> row_m, coef_m;
     legendre_table(T, d.J2, d.J2p, c->mu, table);
     epsilon_table(T, eps);
+    synthesis_factors(T, phys->radius, syn);
+    order_maps(T, row_m, coef_m);
     for (int m = 0; m <= T; ++m)
         for (int n = m; n <= T; ++n)
             lam[order_offset(T, m) + n - m] = double(n) * double(n + 1) / (phys->radius * phys->radius);
@@ -293,6 +303,9 @@ int sdc_create(sdc_ctx **out, int T, int J, int L, int M, int K, double dt, cons
         SDC_TRY(upload(&c->tw, tw.data(), tw.size()));
     }
     SDC_TRY(upload(&c->eps, eps.data(), eps.size()));
+    SDC_TRY(upload(&c->syn, syn.data(), syn.size()));
+    SDC_TRY(upload(&c->row_m, row_m.data(), row_m.size()));
+    SDC_TRY(upload(&c->coef_m, coef_m.data(), coef_m.size()));
     SDC_TRY(upload(&c->lam, lam.data(), lam.size()));
     SDC_TRY(upload(&c->mu2, c->mu.data(), d.J2));
     SDC_TRY(upload(&c->w2, c->w.data(), d.J2));
@@ -307,6 +320,7 @@ int sdc_create(sdc_ctx **out, int T, int J, int L, int M, int K, double dt, cons
     const size_t scal = static_cast<size_t>(d.J2) * 2 * (T + 1) * sizeof(double2);   // scalar helpers (FP64)
     SDC_TRY(cudaMalloc(&c->f1, f1b > scal ? f1b : scal));
     SDC_TRY(cudaMalloc(&c->f2, f2b > scal ? f2b : scal));
+    SDC_TRY(cudaMalloc(&c->f3, static_cast<size_t>(M) * d.next * 5 * elem));
     c->sweep_nblocks = sweep_blocks(d.ncoef);
     SDC_TRY(cudaMalloc(&c->resid_part, static_cast<size_t>(c->sweep_nblocks) * M * 3 * sizeof(double)));
     SDC_TRY(cudaMalloc(&c->resid, static_cast<size_t>(K) * 3 * sizeof(double)));

@@ -68,7 +68,10 @@ struct SweepParams {
 
 // Per-kernel CUDA-event timing of a directly launched (not graph) step:
 // mark(c) records an event and tags the kernel launched next with class c.
-enum { STAGE_SYNTH = 0, STAGE_RING = 1, STAGE_ANALYSIS = 2, STAGE_SWEEP = 3, STAGE_RESID = 4, NSTAGES = 5 };
+enum {
+    STAGE_SYNTH = 0, STAGE_RING = 1, STAGE_ANALYSIS = 2, STAGE_EPILOGUE = 3, STAGE_SWEEP = 4, STAGE_RESID = 5,
+    NSTAGES = 6
+};
 struct StageTimer {
     static constexpr int kMax = 512;
     cudaEvent_t ev[kMax + 1];
@@ -81,6 +84,26 @@ struct StageTimer {
     void end() { cudaEventRecord(ev[n], stream); }
 };
 
+// Device-resident tables of one context (pbar and tw in the transform
+// precision: double / double2 or float / float2).
+struct DeviceTables {
+    const void *pbar;      // Pbar [next][J2p]
+    const void *tw;        // twiddles [L]
+    const double *eps;     // eps_n^m [next]
+    const double *lam;     // n(n+1)/a^2 [ncoef]
+    const double *mu;      // northern Gauss nodes [J2]
+    const double *w;       // northern Gauss weights [J2]
+    const double *syn;     // wind synthesis factors (c0, c1, c2) [next][3]
+    const int *row_m;      // order m of each extended row [next]
+    const int *coef_m;     // order m of each packed coefficient [ncoef]
+};
+
+// Transform workspaces (elements of the transform precision):
+// f1 [B][J2][4][2][T+1], f2 [B][T+1][5][2][J2], f3 [B][next][5] complex.
+struct Workspace {
+    void *f1, *f2, *f3;
+};
+
 // ---- host-side precompute (tables.cpp) ----------------------------------
 void gauss_legendre(int J, std::vector<double> &mu, std::vector<double> &w);
 void radau_right(int M, std::vector<double> &tau, std::vector<double> &Q);
@@ -88,25 +111,16 @@ void radau_right(int M, std::vector<double> &tau, std::vector<double> &Q);
 // padded to J2p: table[(ext_offset(m) + n - m) * J2p + j].
 void legendre_table(int T, int J2, int J2p, const std::vector<double> &mu, std::vector<double> &table);
 void epsilon_table(int T, std::vector<double> &eps);   // extended packing, eps_n^m
+void synthesis_factors(int T, double radius, std::vector<double> &syn);   // [next][3]
+void order_maps(int T, std::vector<int> &row_m, std::vector<int> &coef_m);
 bool fft_plan(int L, FftPlan &plan);
 void twiddles(int L, std::vector<double> &re, std::vector<double> &im);   // e^{-2 pi i k / L}
 
 // ---- kernel launchers (transforms.cu, sweep.cu) -------------------------
-// Explicit tendency of B states (K1 -> K2 -> K3).  Returns cudaError_t.
-cudaError_t launch_tendency_f64(const Dims &d, const FftPlan &plan, int B,
-                                const double2 *states, long long sstride,
-                                double2 *tend, long long tstride,
-                                const double *pbar, const double *eps, const double *lam,
-                                const double *mu, const double *w, const double2 *tw,
-                                double2 *f1, double2 *f2, cudaStream_t s, int *launches,
-                                StageTimer *timer = nullptr);
-cudaError_t launch_tendency_f32(const Dims &d, const FftPlan &plan, int B,
-                                const double2 *states, long long sstride,
-                                double2 *tend, long long tstride,
-                                const float *pbar, const double *eps, const double *lam,
-                                const double *mu, const double *w, const float2 *tw,
-                                float2 *f1, float2 *f2, cudaStream_t s, int *launches,
-                                StageTimer *timer = nullptr);
+// Explicit tendency of B states (K1 -> K2 -> K3a -> K3b).
+cudaError_t launch_tendency(const Dims &d, const FftPlan &plan, bool fp32, int B, const double2 *states,
+                            long long sstride, double2 *tend, long long tstride, const DeviceTables &tb,
+                            const Workspace &ws, cudaStream_t s, int *launches, StageTimer *timer = nullptr);
 cudaError_t launch_sweep(const SweepParams &p, int M, cudaStream_t s, int *launches,
                          StageTimer *timer = nullptr);
 cudaError_t launch_resid_reduce(const double *part, int nblocks, int M, int m0, int m1,

@@ -155,6 +155,40 @@ void epsilon_table(int T, std::vector<double> &eps) {
         }
 }
 
+// Factors that map (zeta, div) on degrees m..T to the coefficients of the
+// wind components U = u cos(lat), V = v cos(lat) on degrees n' = m..T+1:
+//   U_n' = i c0 div_n' - c1 zeta_{n'-1} - c2 zeta_{n'+1}
+//   V_n' = i c0 zeta_n' + c1 div_{n'-1} + c2 div_{n'+1}
+// with s_n = -a^2 / (n(n+1)) (the inverse Laplacian, 0 at n = 0 and outside
+// m..T), c0 = (m/a) s_n', c1 = -(n'-1) eps_n' s_{n'-1} / a,
+// c2 = (n'+2) eps_{n'+1} s_{n'+1} / a.  This is U = (1/a) sum_n [i m chi_n Pbar_n
+// - psi_n H_n] (and V alike) after H_n = -n eps_{n+1} Pbar_{n+1} + (n+1) eps_n Pbar_{n-1}.
+void synthesis_factors(int T, double a, std::vector<double> &syn) {
+    const int next = (T + 1) * (T + 4) / 2;
+    syn.assign(3 * static_cast<size_t>(next), 0.0);
+    std::vector<double> eps;
+    epsilon_table(T, eps);
+    for (int m = 0; m <= T; ++m) {
+        const int base = ext_offset(T, m);
+        auto s = [&](int n) { return (n < m || n > T || n == 0) ? 0.0 : -a * a / (double(n) * double(n + 1)); };
+        for (int n = m; n <= T + 1; ++n) {
+            const int e = base + n - m;
+            syn[3 * e] = double(m) / a * s(n);
+            syn[3 * e + 1] = (n - 1 >= m) ? -(n - 1.0) * eps[e] * s(n - 1) / a : 0.0;
+            syn[3 * e + 2] = (n + 1 <= T) ? (n + 2.0) * eps[e + 1] * s(n + 1) / a : 0.0;
+        }
+    }
+}
+
+void order_maps(int T, std::vector<int> &row_m, std::vector<int> &coef_m) {
+    row_m.clear();
+    coef_m.clear();
+    for (int m = 0; m <= T; ++m) {
+        for (int n = m; n <= T + 1; ++n) row_m.push_back(m);
+        for (int n = m; n <= T; ++n) coef_m.push_back(m);
+    }
+}
+
 bool fft_plan(int L, FftPlan &plan) {
     plan.L = L;
     plan.nstages = 0;

@@ -25,100 +25,109 @@
 namespace sdc {
 
 // ---------------------------------------------------------------------------
-// K1: synthesis.  grid (T+1 orders, B states, ceil(J2/blockDim) latitude
-// chunks).  Output F1[b][j][field][parity][m], fields (zeta, Phi', U, V).
+// K1: synthesis.  grid ((T+2)/2 order pairs, B states, latitude chunks): a
+// block serves orders m and T - m (equal work for every block).  Output
+// F1[b][j][field][parity][m], fields (zeta, Phi', U, V).  The wind
+// coefficients on degrees n' = m..T+1 come from host-computed factors
+// (c0, c1, c2) = syn[e]:
+//   U_n' = i c0 div_n' - c1 zeta_{n'-1} - c2 zeta_{n'+1}
+//   V_n' = i c0 zeta_n' + c1 div_{n'-1} + c2 div_{n'+1}
+// with c0 = (m/a) s_n', c1 = -(n'-1) eps_n' s_{n'-1} / a,
+// c2 = (n'+2) eps_{n'+1} s_{n'+1} / a and s_n = -a^2 / (n(n+1)) (0 at n = 0).
 // ---------------------------------------------------------------------------
 template <typename R>
-__global__ void k1_synthesis(const double2 *__restrict__ states, long long sstride, Dims d,
-                             const R *__restrict__ pbar, const double *__restrict__ eps,
-                             V2<R> *__restrict__ f1) {
+__global__ void __launch_bounds__(64) k1_synthesis(const double2 *__restrict__ states, long long sstride, Dims d,
+                                                   const R *__restrict__ pbar, const double *__restrict__ syn,
+                                                   V2<R> *__restrict__ f1) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    V2<R> *cf = reinterpret_cast<V2<R> *>(smem_raw);   // [nn][4]
-    const int m = blockIdx.x;
-    const int b = blockIdx.y;
+    V2<R> *cf = reinterpret_cast<V2<R> *>(smem_raw);   // [rows][4]
     const int T = d.T;
-    const int nn = T + 2 - m;                            // n' = m..T+1
+    const int m1 = blockIdx.x, m2 = T - blockIdx.x;
+    const int b = blockIdx.y;
+    const int nn1 = T + 2 - m1;
+    const int nn2 = (m2 > m1) ? T + 2 - m2 : 0;
+    const int rows = nn1 + nn2;
     const double2 *st = states + b * sstride;
-    const int off = order_offset(T, m);
-    const int eoff = ext_offset(T, m);
-    const double a = d.a, inv_a = 1.0 / d.a;
+    const int nc = d.ncoef;
 
-    // psi_n = -a^2 zeta_n / (n(n+1)) (zero outside m..T and at n = 0); the
-    // same map takes div to chi.
-    auto pot = [&](int field, int n) -> double2 {
-        if (n < m || n > T || n == 0) return make_double2(0.0, 0.0);
-        const double2 v = st[field * d.ncoef + off + n - m];
-        const double s = -a * a / (double(n) * double(n + 1));
-        return make_double2(s * v.x, s * v.y);
-    };
-    for (int t = threadIdx.x; t < nn; t += blockDim.x) {
+    for (int r = threadIdx.x; r < rows; r += blockDim.x) {
+        const int m = (r < nn1) ? m1 : m2;
+        const int t = (r < nn1) ? r : r - nn1;
         const int n = m + t;
-        double2 z = make_double2(0.0, 0.0), p = z;
-        if (n <= T) {
-            z = st[F_ZETA * d.ncoef + off + t];
-            p = st[F_PHI * d.ncoef + off + t];
-        }
-        // tilde-coefficients: sum_n c_n H_n = sum_n' Pbar_n' ctilde_n'
-        const double elo = (n - 1 >= m) ? -(n - 1.0) * eps[eoff + t] : 0.0;     // -(n'-1) eps_{n'}
-        const double ehi = (n + 1 <= T) ? (n + 2.0) * eps[eoff + t + 1] : 0.0;   // (n'+2) eps_{n'+1}
-        const double2 psm = pot(F_ZETA, n - 1), psp = pot(F_ZETA, n + 1), ps0 = pot(F_ZETA, n);
-        const double2 chm = pot(F_DIV, n - 1), chp = pot(F_DIV, n + 1), ch0 = pot(F_DIV, n);
-        const double2 pst = make_double2(elo * psm.x + ehi * psp.x, elo * psm.y + ehi * psp.y);
-        const double2 cht = make_double2(elo * chm.x + ehi * chp.x, elo * chm.y + ehi * chp.y);
-        const double mm = m;
-        // a U-coef = i m chi - psi~ ;  a V-coef = i m psi + chi~
-        const double2 uc = make_double2((-mm * ch0.y - pst.x) * inv_a, (mm * ch0.x - pst.y) * inv_a);
-        const double2 vc = make_double2((-mm * ps0.y + cht.x) * inv_a, (mm * ps0.x + cht.y) * inv_a);
-        cf[t * 4 + G_ZETA] = mk<R>(R(z.x), R(z.y));
-        cf[t * 4 + G_PHI] = mk<R>(R(p.x), R(p.y));
-        cf[t * 4 + G_U] = mk<R>(R(uc.x), R(uc.y));
-        cf[t * 4 + G_V] = mk<R>(R(vc.x), R(vc.y));
+        const int off = order_offset(T, m);
+        const int e = ext_offset(T, m) + t;
+        auto ld = [&](int f, int k) -> double2 {
+            return (k >= m && k <= T) ? st[f * nc + off + k - m] : make_double2(0.0, 0.0);
+        };
+        const double2 z0 = ld(F_ZETA, n), zm = ld(F_ZETA, n - 1), zp = ld(F_ZETA, n + 1);
+        const double2 d0 = ld(F_DIV, n), dm = ld(F_DIV, n - 1), dp = ld(F_DIV, n + 1);
+        const double2 p0 = ld(F_PHI, n);
+        const double c0 = syn[3 * e], c1 = syn[3 * e + 1], c2 = syn[3 * e + 2];
+        const double ux = -c0 * d0.y - c1 * zm.x - c2 * zp.x;
+        const double uy = c0 * d0.x - c1 * zm.y - c2 * zp.y;
+        const double vx = -c0 * z0.y + c1 * dm.x + c2 * dp.x;
+        const double vy = c0 * z0.x + c1 * dm.y + c2 * dp.y;
+        cf[r * 4 + G_ZETA] = mk<R>(R(z0.x), R(z0.y));
+        cf[r * 4 + G_PHI] = mk<R>(R(p0.x), R(p0.y));
+        cf[r * 4 + G_U] = mk<R>(R(ux), R(uy));
+        cf[r * 4 + G_V] = mk<R>(R(vx), R(vy));
     }
     __syncthreads();
 
     const int j = blockIdx.z * blockDim.x + threadIdx.x;
     if (j >= d.J2) return;
-    V2<R> ae[4], ao[4];
-#pragma unroll
-    for (int f = 0; f < 4; ++f) { ae[f] = mk<R>(0, 0); ao[f] = mk<R>(0, 0); }
-    const R *prow = pbar + static_cast<size_t>(eoff) * d.J2p + j;
-    int t = 0;
-    for (; t + 1 < nn; t += 2) {
-        const R pe = prow[static_cast<size_t>(t) * d.J2p];
-        const R po = prow[static_cast<size_t>(t + 1) * d.J2p];
-#pragma unroll
-        for (int f = 0; f < 4; ++f) {
-            const V2<R> ce = cf[t * 4 + f], co = cf[(t + 1) * 4 + f];
-            ae[f].x = fma(pe, ce.x, ae[f].x);
-            ae[f].y = fma(pe, ce.y, ae[f].y);
-            ao[f].x = fma(po, co.x, ao[f].x);
-            ao[f].y = fma(po, co.y, ao[f].y);
-        }
-    }
-    if (t < nn) {
-        const R pe = prow[static_cast<size_t>(t) * d.J2p];
-#pragma unroll
-        for (int f = 0; f < 4; ++f) {
-            const V2<R> ce = cf[t * 4 + f];
-            ae[f].x = fma(pe, ce.x, ae[f].x);
-            ae[f].y = fma(pe, ce.y, ae[f].y);
-        }
-    }
     V2<R> *o = f1 + (static_cast<size_t>(b) * d.J2 + j) * (4 * 2 * (T + 1));
+    for (int half = 0; half < 2; ++half) {
+        const int m = half ? m2 : m1;
+        const int nn = half ? nn2 : nn1;
+        if (nn == 0) break;
+        const V2<R> *c = cf + (half ? nn1 : 0) * 4;
+        V2<R> ae[4], ao[4];
 #pragma unroll
-    for (int f = 0; f < 4; ++f) {
-        o[(f * 2 + 0) * (T + 1) + m] = ae[f];
-        o[(f * 2 + 1) * (T + 1) + m] = ao[f];
+        for (int f = 0; f < 4; ++f) { ae[f] = mk<R>(0, 0); ao[f] = mk<R>(0, 0); }
+        const R *prow = pbar + static_cast<size_t>(ext_offset(T, m)) * d.J2p + j;
+        int t = 0;
+        for (; t + 1 < nn; t += 2) {
+            const R pe = prow[static_cast<size_t>(t) * d.J2p];
+            const R po = prow[static_cast<size_t>(t + 1) * d.J2p];
+#pragma unroll
+            for (int f = 0; f < 4; ++f) {
+                const V2<R> ce = c[t * 4 + f], co = c[(t + 1) * 4 + f];
+                ae[f].x = fma(pe, ce.x, ae[f].x);
+                ae[f].y = fma(pe, ce.y, ae[f].y);
+                ao[f].x = fma(po, co.x, ao[f].x);
+                ao[f].y = fma(po, co.y, ao[f].y);
+            }
+        }
+        if (t < nn) {
+            const R pe = prow[static_cast<size_t>(t) * d.J2p];
+#pragma unroll
+            for (int f = 0; f < 4; ++f) {
+                const V2<R> ce = c[t * 4 + f];
+                ae[f].x = fma(pe, ce.x, ae[f].x);
+                ae[f].y = fma(pe, ce.y, ae[f].y);
+            }
+        }
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+            o[(f * 2 + 0) * (T + 1) + m] = ae[f];
+            o[(f * 2 + 1) * (T + 1) + m] = ao[f];
+        }
     }
 }
 
+// Shared memory of one ring block: 5 field arrays plus s scratch arrays of L
+// complex values.  Prefer the largest s that still lets two blocks share an
+// SM; fall back to one block per SM for long rings.
 size_t ring_smem_bytes(int L, int elem_bytes, int *scratch_arrays) {
-    const size_t cap = 227 * 1024;
-    for (int s = 5; s >= 1; --s) {
-        const size_t bytes = static_cast<size_t>(5 + s) * L * elem_bytes;
-        if (bytes <= cap) {
-            if (scratch_arrays) *scratch_arrays = s;
-            return bytes;
+    const size_t per_sm = 227 * 1024;
+    for (size_t cap : {per_sm / 2 - 1024, per_sm}) {
+        for (int s = 5; s >= 1; --s) {
+            const size_t bytes = static_cast<size_t>(5 + s) * L * elem_bytes;
+            if (bytes <= cap) {
+                if (scratch_arrays) *scratch_arrays = s;
+                return bytes;
+            }
         }
     }
     if (scratch_arrays) *scratch_arrays = 0;
@@ -205,78 +214,96 @@ __global__ void k2_ring(const V2<R> *__restrict__ f1, V2<R> *__restrict__ f2, Di
 }
 
 // ---------------------------------------------------------------------------
-// K3: one block per (order m, state b).  Projections
-//   G^_n' = sum_j2 Pbar_n'(mu_j) W_g[parity(n'-m)][j2],  n' = m..T+1,
-// then per mode n = m..T (1/a folded in here):
+// K3a: Legendre projections, one thread per extended row e = (m, n'), all
+// orders flattened so that every block carries the same work:
+//   Y[b][e][g] = sum_j2 Pbar_n'(mu_j) W_g[parity(n'-m)][j2],  g in (A, B, C, D, E).
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void __launch_bounds__(64) k3_project(const V2<R> *__restrict__ f2, Dims d, const R *__restrict__ pbar,
+                                                 const int *__restrict__ row_m, V2<R> *__restrict__ y) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    const int b = blockIdx.y;
+    if (e >= d.next) return;
+    const int T = d.T, J2 = d.J2;
+    const int m = row_m[e];
+    const int par = (e - ext_offset(T, m)) & 1;
+    const V2<R> *W = f2 + (static_cast<size_t>(b) * (T + 1) + m) * 10 * J2 + par * J2;
+    const R *prow = pbar + static_cast<size_t>(e) * d.J2p;
+    V2<R> acc[5];
+#pragma unroll
+    for (int g = 0; g < 5; ++g) acc[g] = mk<R>(0, 0);
+    const int J2e = J2 & ~1;
+    for (int j = 0; j < J2e; j += 2) {
+        const V2<R> pp = *reinterpret_cast<const V2<R> *>(prow + j);
+#pragma unroll
+        for (int g = 0; g < 5; ++g) {
+            const V2<R> w0 = W[g * 2 * J2 + j], w1 = W[g * 2 * J2 + j + 1];
+            acc[g].x = fma(pp.x, w0.x, acc[g].x);
+            acc[g].y = fma(pp.x, w0.y, acc[g].y);
+            acc[g].x = fma(pp.y, w1.x, acc[g].x);
+            acc[g].y = fma(pp.y, w1.y, acc[g].y);
+        }
+    }
+    if (J2e < J2) {
+        const R p = prow[J2e];
+#pragma unroll
+        for (int g = 0; g < 5; ++g) {
+            const V2<R> w0 = W[g * 2 * J2 + J2e];
+            acc[g].x = fma(p, w0.x, acc[g].x);
+            acc[g].y = fma(p, w0.y, acc[g].y);
+        }
+    }
+    V2<R> *o = y + (static_cast<size_t>(b) * d.next + e) * 5;
+#pragma unroll
+    for (int g = 0; g < 5; ++g) o[g] = acc[g];
+}
+
+// ---------------------------------------------------------------------------
+// K3b: per spectral mode (n, m), n = m..T (1/a folded in here):
 //   T_E(zeta)_n = -(1/a) [i m A^_n + n eps_{n+1} B^_{n+1} - (n+1) eps_n B^_{n-1}]
 //   T_E(div)_n  =  (1/a) [i m B^_n - n eps_{n+1} A^_{n+1} + (n+1) eps_n A^_{n-1}] + lambda_n E^_n
 //   T_E(Phi')_n = -(1/a) [i m C^_n + n eps_{n+1} D^_{n+1} - (n+1) eps_n D^_{n-1}]
 // ---------------------------------------------------------------------------
 template <typename R>
-__global__ void k3_analysis(const V2<R> *__restrict__ f2, Dims d, const R *__restrict__ pbar,
-                            const double *__restrict__ eps, double2 *__restrict__ tend,
-                            long long tstride) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int m = blockIdx.x;
+__global__ void k3_epilogue(const V2<R> *__restrict__ y, Dims d, const double *__restrict__ eps,
+                            const double *__restrict__ lam, const int *__restrict__ coef_m,
+                            double2 *__restrict__ tend, long long tstride) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int b = blockIdx.y;
+    if (i >= d.ncoef) return;
     const int T = d.T;
-    const int J2 = d.J2;
-    const int nn = T + 2 - m;
-    V2<R> *W = reinterpret_cast<V2<R> *>(smem_raw);                  // [5][2][J2]
-    double2 *Y = reinterpret_cast<double2 *>(smem_raw + ((10 * J2 * sizeof(V2<R>) + 15) / 16) * 16);  // [nn][5]
-    const V2<R> *src = f2 + (static_cast<size_t>(b) * (T + 1) + m) * 10 * J2;
-    for (int i = threadIdx.x; i < 10 * J2; i += blockDim.x) W[i] = src[i];
-    __syncthreads();
-
-    const int eoff = ext_offset(T, m);
-    for (int t = threadIdx.x; t < nn; t += blockDim.x) {
-        const int par = t & 1;
-        V2<R> acc[5];
-#pragma unroll
-        for (int g = 0; g < 5; ++g) acc[g] = mk<R>(0, 0);
-        const R *prow = pbar + static_cast<size_t>(eoff + t) * d.J2p;
-        for (int j = 0; j < J2; ++j) {
-            const R p = prow[j];
-#pragma unroll
-            for (int g = 0; g < 5; ++g) {
-                const V2<R> wv = W[(g * 2 + par) * J2 + j];
-                acc[g].x = fma(p, wv.x, acc[g].x);
-                acc[g].y = fma(p, wv.y, acc[g].y);
-            }
-        }
-#pragma unroll
-        for (int g = 0; g < 5; ++g) Y[t * 5 + g] = make_double2(double(acc[g].x), double(acc[g].y));
-    }
-    __syncthreads();
-
+    const int m = coef_m[i];
+    const int t = i - order_offset(T, m);
+    const int n = m + t;
+    const int e = ext_offset(T, m) + t;
+    const V2<R> *Y = y + static_cast<size_t>(b) * d.next * 5;
+    auto ld = [&](int row, int g) -> double2 {
+        const V2<R> v = Y[static_cast<size_t>(row) * 5 + g];
+        return make_double2(double(v.x), double(v.y));
+    };
+    const double2 z0 = make_double2(0.0, 0.0);
+    const double2 Ah = ld(e, P_A), Bh = ld(e, P_B), Ch = ld(e, P_C), Eh = ld(e, P_E);
+    const double2 Au = ld(e + 1, P_A), Bu = ld(e + 1, P_B), Du = ld(e + 1, P_D);
+    const double2 Al = t > 0 ? ld(e - 1, P_A) : z0;
+    const double2 Bl = t > 0 ? ld(e - 1, P_B) : z0;
+    const double2 Dl = t > 0 ? ld(e - 1, P_D) : z0;
+    const double cu = n * eps[e + 1];
+    const double cl = t > 0 ? (n + 1.0) * eps[e] : 0.0;
     const double inv_a = 1.0 / d.a;
-    const int off = order_offset(T, m);
     const double mm = m;
+    const double lm = lam[i];
+    double2 tz, td, tp;
+    // i m X = (-m X.y, m X.x)
+    tz.x = -inv_a * (-mm * Ah.y + cu * Bu.x - cl * Bl.x);
+    tz.y = -inv_a * (mm * Ah.x + cu * Bu.y - cl * Bl.y);
+    td.x = inv_a * (-mm * Bh.y - cu * Au.x + cl * Al.x) + lm * Eh.x;
+    td.y = inv_a * (mm * Bh.x - cu * Au.y + cl * Al.y) + lm * Eh.y;
+    tp.x = -inv_a * (-mm * Ch.y + cu * Du.x - cl * Dl.x);
+    tp.y = -inv_a * (mm * Ch.x + cu * Du.y - cl * Dl.y);
     double2 *out = tend + b * tstride;
-    for (int t = threadIdx.x; t < nn - 1; t += blockDim.x) {
-        const int n = m + t;
-        const double cu = n * eps[eoff + t + 1];                        // n eps_{n+1}
-        const double cl = (t > 0) ? (n + 1.0) * eps[eoff + t] : 0.0;    // (n+1) eps_n
-        const double2 z0 = make_double2(0.0, 0.0);
-        const double2 Ah = Y[t * 5 + P_A], Bh = Y[t * 5 + P_B], Ch = Y[t * 5 + P_C];
-        const double2 Eh = Y[t * 5 + P_E];
-        const double2 Au = Y[(t + 1) * 5 + P_A], Bu = Y[(t + 1) * 5 + P_B], Du = Y[(t + 1) * 5 + P_D];
-        const double2 Al = t > 0 ? Y[(t - 1) * 5 + P_A] : z0;
-        const double2 Bl = t > 0 ? Y[(t - 1) * 5 + P_B] : z0;
-        const double2 Dl = t > 0 ? Y[(t - 1) * 5 + P_D] : z0;
-        const double lam = double(n) * double(n + 1) * inv_a * inv_a;
-        double2 tz, td, tp;
-        // i m X = (-m X.y, m X.x)
-        tz.x = -inv_a * (-mm * Ah.y + cu * Bu.x - cl * Bl.x);
-        tz.y = -inv_a * (mm * Ah.x + cu * Bu.y - cl * Bl.y);
-        td.x = inv_a * (-mm * Bh.y - cu * Au.x + cl * Al.x) + lam * Eh.x;
-        td.y = inv_a * (mm * Bh.x - cu * Au.y + cl * Al.y) + lam * Eh.y;
-        tp.x = -inv_a * (-mm * Ch.y + cu * Du.x - cl * Dl.x);
-        tp.y = -inv_a * (mm * Ch.x + cu * Du.y - cl * Dl.y);
-        out[F_PHI * d.ncoef + off + t] = tp;
-        out[F_ZETA * d.ncoef + off + t] = tz;
-        out[F_DIV * d.ncoef + off + t] = td;
-    }
+    out[F_PHI * d.ncoef + i] = tp;
+    out[F_ZETA * d.ncoef + i] = tz;
+    out[F_DIV * d.ncoef + i] = td;
 }
 
 // ---------------------------------------------------------------------------
@@ -289,12 +316,7 @@ __global__ void k_scalar_ring_forward(const double *__restrict__ grid, double2 *
                                       const double *__restrict__ w);
 constexpr int kK1Threads = 64;
 constexpr int kK2Threads = 256;
-constexpr int kK3Threads = 128;
-
-template <typename R>
-static size_t k3_smem(const Dims &d) {
-    return ((10 * d.J2 * sizeof(V2<R>) + 15) / 16) * 16 + static_cast<size_t>(d.T + 2) * 5 * sizeof(double2);
-}
+constexpr int kK3Threads = 64;
 
 template <typename R>
 static cudaError_t configure(const Dims &d, const FftPlan &plan) {
@@ -302,30 +324,33 @@ static cudaError_t configure(const Dims &d, const FftPlan &plan) {
     if (sm2 == 0) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(k2_ring<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k3_analysis<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k3_smem<R>(d));
-    if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(k1_synthesis<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)(static_cast<size_t>(d.T + 2) * 4 * sizeof(V2<R>)));
+                                (int)(static_cast<size_t>(d.T + 4) * 4 * sizeof(V2<R>)));
 }
 
 template <typename R>
-static cudaError_t launch_tendency(const Dims &d, const FftPlan &plan, int B, const double2 *states,
-                                   long long sstride, double2 *tend, long long tstride, const R *pbar,
-                                   const double *eps, const double *mu, const double *w,
-                                   const V2<R> *tw, V2<R> *f1, V2<R> *f2, cudaStream_t s,
-                                   int *launches, StageTimer *timer) {
-    const size_t sm1 = static_cast<size_t>(d.T + 2) * 4 * sizeof(V2<R>);
-    dim3 g1(d.T + 1, B, (d.J2 + kK1Threads - 1) / kK1Threads);
+static cudaError_t launch_tendency_t(const Dims &d, const FftPlan &plan, int B, const double2 *states,
+                                     long long sstride, double2 *tend, long long tstride, const DeviceTables &tb,
+                                     const Workspace &ws, cudaStream_t s, int *launches, StageTimer *timer) {
+    const R *pbar = static_cast<const R *>(tb.pbar);
+    const V2<R> *tw = static_cast<const V2<R> *>(tb.tw);
+    V2<R> *f1 = static_cast<V2<R> *>(ws.f1);
+    V2<R> *f2 = static_cast<V2<R> *>(ws.f2);
+    V2<R> *f3 = static_cast<V2<R> *>(ws.f3);
+    const size_t sm1 = static_cast<size_t>(d.T + 4) * 4 * sizeof(V2<R>);
+    dim3 g1((d.T + 2) / 2, B, (d.J2 + kK1Threads - 1) / kK1Threads);
     int nscratch = 0;
     const size_t sm2 = ring_smem_bytes(d.L, sizeof(V2<R>), &nscratch);
     if (sm2 == 0) return cudaErrorInvalidValue;
     if (timer) timer->mark(STAGE_SYNTH);
-    k1_synthesis<R><<<g1, kK1Threads, sm1, s>>>(states, sstride, d, pbar, eps, f1);
+    k1_synthesis<R><<<g1, kK1Threads, sm1, s>>>(states, sstride, d, pbar, tb.syn, f1);
     if (timer) timer->mark(STAGE_RING);
-    k2_ring<R><<<dim3(d.J2, B), kK2Threads, sm2, s>>>(f1, f2, d, plan, tw, mu, w, nscratch);
+    k2_ring<R><<<dim3(d.J2, B), kK2Threads, sm2, s>>>(f1, f2, d, plan, tw, tb.mu, tb.w, nscratch);
     if (timer) timer->mark(STAGE_ANALYSIS);
-    k3_analysis<R><<<dim3(d.T + 1, B), kK3Threads, k3_smem<R>(d), s>>>(f2, d, pbar, eps, tend, tstride);
-    if (launches) *launches += 3;
+    k3_project<R><<<dim3((d.next + kK3Threads - 1) / kK3Threads, B), kK3Threads, 0, s>>>(f2, d, pbar, tb.row_m, f3);
+    if (timer) timer->mark(STAGE_EPILOGUE);
+    k3_epilogue<R><<<dim3((d.ncoef + 127) / 128, B), 128, 0, s>>>(f3, d, tb.eps, tb.lam, tb.coef_m, tend, tstride);
+    if (launches) *launches += 4;
     return cudaGetLastError();
 }
 
@@ -338,24 +363,12 @@ cudaError_t configure_transform_kernels(const Dims &d, const FftPlan &plan, bool
     return cudaFuncSetAttribute(k_scalar_ring_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
 }
 
-cudaError_t launch_tendency_f64(const Dims &d, const FftPlan &plan, int B, const double2 *states,
-                                long long sstride, double2 *tend, long long tstride, const double *pbar,
-                                const double *eps, const double *lam, const double *mu, const double *w,
-                                const double2 *tw, double2 *f1, double2 *f2, cudaStream_t s, int *launches,
-                                StageTimer *timer) {
-    (void)lam;
-    return launch_tendency<double>(d, plan, B, states, sstride, tend, tstride, pbar, eps, mu, w, tw, f1, f2, s,
-                                   launches, timer);
-}
-
-cudaError_t launch_tendency_f32(const Dims &d, const FftPlan &plan, int B, const double2 *states,
-                                long long sstride, double2 *tend, long long tstride, const float *pbar,
-                                const double *eps, const double *lam, const double *mu, const double *w,
-                                const float2 *tw, float2 *f1, float2 *f2, cudaStream_t s, int *launches,
-                                StageTimer *timer) {
-    (void)lam;
-    return launch_tendency<float>(d, plan, B, states, sstride, tend, tstride, pbar, eps, mu, w, tw, f1, f2, s,
-                                  launches, timer);
+cudaError_t launch_tendency(const Dims &d, const FftPlan &plan, bool fp32, int B, const double2 *states,
+                            long long sstride, double2 *tend, long long tstride, const DeviceTables &tb,
+                            const Workspace &ws, cudaStream_t s, int *launches, StageTimer *timer) {
+    if (fp32)
+        return launch_tendency_t<float>(d, plan, B, states, sstride, tend, tstride, tb, ws, s, launches, timer);
+    return launch_tendency_t<double>(d, plan, B, states, sstride, tend, tstride, tb, ws, s, launches, timer);
 }
 
 // ---------------------------------------------------------------------------

@@ -125,13 +125,13 @@ class Solver:
         _lib.check(self.lib.sdc_counters(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), "sdc_counters")
         return a.value, b.value, c.value
 
-    STAGES = ("synthesis", "ring", "analysis", "sweep", "resid")
+    STAGES = ("synthesis", "ring", "analysis", "epilogue", "sweep", "resid")
 
     def profile_step(self, state: torch.Tensor):
         """One step launched kernel by kernel with CUDA events: {stage: (ms, launches)}."""
         self._check_state(state)
-        ms = (ctypes.c_double * 5)()
-        nl = (ctypes.c_int * 5)()
+        ms = (ctypes.c_double * 6)()
+        nl = (ctypes.c_int * 6)()
         _lib.check(self.lib.sdc_profile_step(self.h, _ptr(state), ms, nl), "sdc_profile_step")
         return {k: (ms[i], nl[i]) for i, k in enumerate(self.STAGES)}
 
