@@ -291,14 +291,28 @@ def cuda_arm(args, rank: int, world: int):
             sm.run(xs, 1)
         tm = time_device(sm, xs, args.steps, flush)
         mprof, _ = profile_stages(sm, u0, flush, max(3, min(10, args.steps)))
-        a64, a32 = u0.clone(), u0.clone()
-        s.run(a64, 20)
-        sm.run(a32, 20)
-        err = ((a32 - a64).abs().pow(2).sum(1) / a64.abs().pow(2).sum(1)).sqrt().cpu().numpy()
+        # fixed error: the mixed-mode error against the FP64 path must stay below the
+        # FP64 discretisation error, measured as FP64 at dt against FP64 at dt/4
+        nh = args.horizon
+        a64, a32, a64q = u0.clone(), u0.clone(), u0.clone()
+        s.run(a64, nh)
+        sm.run(a32, nh)
+        sq = Solver(wl.T, wl.nlat, wl.nlon, wl.nodes, wl.sweeps, wl.dt / 4, si.RADIUS, si.OMEGA, si.GRAVITY,
+                    si.MEAN_DEPTH, precision=SDC_FP64)
+        sq.run(a64q, 4 * nh)
+        sq.close()
+
+        def rel(x, y):
+            return ((x - y).abs().pow(2).sum(1) / y.abs().pow(2).sum(1)).sqrt().cpu().numpy()
+
+        err = rel(a32, a64)
+        edisc = rel(a64, a64q)
+        fields = ("phi", "zeta", "div")
         mixed = {"fp32": {"value": world * args.steps / (sum(tm) * 1e-3), "unit": "steps/s",
-                          "ms_per_step": sum(tm) / args.steps, "stages": mprof,
-                          "rel_l2_vs_fp64_20_steps": {"phi": float(err[0]), "zeta": float(err[1]),
-                                                      "div": float(err[2])}}}
+                          "ms_per_step": sum(tm) / args.steps, "stages": mprof, "horizon_steps": nh,
+                          "rel_l2_vs_fp64": dict(zip(fields, map(float, err))),
+                          "fp64_discretisation_rel_l2": dict(zip(fields, map(float, edisc))),
+                          "fixed_error": bool(np.all(err < edisc))}}
         sm.close()
 
     cpu = None
@@ -332,6 +346,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--horizon", type=int, default=40, help="steps of the fixed-error comparison")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
