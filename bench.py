@@ -208,6 +208,45 @@ def profile_stages(s, u0, flush, nprof: int):
     return prof, acc
 
 
+def time_adjoint(Solver, wl, nsteps: int, nsnap: int, reps: int):
+    """Adjoint/forward cost: one reversed step (retape + adjoint) against one forward
+    step, and a checkpointed gradient run against the forward run of nsteps."""
+    import torch
+    s = Solver.for_workload(wl)
+    u0 = s.initial_state(wl)
+    x = u0.clone()
+    ub = torch.ones_like(u0)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    s.run(x, 2)
+    s.step_adjoint(u0, ub)
+    torch.cuda.synchronize()
+    ev[0].record()
+    for _ in range(reps):
+        s.run(x, 1)
+    ev[1].record()
+    for _ in range(reps):
+        s.step_adjoint(u0, ub)
+    ev[2].record()
+    torch.cuda.synchronize()
+    fwd_ms = ev[0].elapsed_time(ev[1]) / reps
+    rev_ms = ev[1].elapsed_time(ev[2]) / reps
+    target = si.MEAN_DEPTH + s.spec_to_grid(u0[0].contiguous()) / si.GRAVITY
+    x = u0.clone()
+    ev[0].record()
+    s.run(x, nsteps)
+    ev[1].record()
+    loss, g = s.adjoint_run(u0, nsteps, target, nsnap)
+    ev[2].record()
+    torch.cuda.synchronize()
+    run_ms = ev[0].elapsed_time(ev[1])
+    adj_ms = ev[1].elapsed_time(ev[2])
+    _, nfwd = s.run_adjoint(u0, nsteps, ub, nsnap)
+    s.close()
+    return {"workload": wl.describe(), "step_fwd_ms": fwd_ms, "step_reverse_ms": rev_ms,
+            "step_ratio": rev_ms / fwd_ms, "run_steps": nsteps, "snapshots": nsnap, "run_fwd_ms": run_ms,
+            "run_adjoint_ms": adj_ms, "run_ratio": adj_ms / run_ms, "recomputed_forward_steps": nfwd}
+
+
 def time_e2e(s, host_state, dev_state, host_out, steps: int):
     """Host-buffer path: pinned H2D copy, one step through the C ABI, D2H copy."""
     import torch
@@ -315,6 +354,11 @@ def cuda_arm(args, rank: int, world: int):
                           "fixed_error": bool(np.all(err < edisc))}}
         sm.close()
 
+    adjoint = None
+    if not args.no_adjoint:
+        adjoint = {"t255": time_adjoint(Solver, wl, 20, 8, 5),
+                   "t127_differentiation": time_adjoint(Solver, si.WORKLOADS["t127adj"], 96, 8, 10)}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, n, el = oracle_steps_per_s(wl, budget_s=args.cpu_budget, max_steps=50)
@@ -330,7 +374,9 @@ def cuda_arm(args, rank: int, world: int):
                        "l2": "flushed (512 MiB write) before every timed step",
                        "parallelism": f"replicas x{world}"},
             "e2e": e2e, "gpu_launches": int(l1 - l0), "clocks": clocks, "roofline": roofline,
-            "stages": prof, "mixed": mixed, "adjoint_fwd_ratio": None, "cpu_baseline": cpu,
+            "stages": prof, "mixed": mixed,
+            "adjoint_fwd_ratio": adjoint["t255"]["step_ratio"] if adjoint else None, "adjoint": adjoint,
+            "cpu_baseline": cpu,
             "peaks_source": peak_kind,
         }
         print(json.dumps(line), flush=True)
@@ -345,8 +391,9 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
-    ap.add_argument("--horizon", type=int, default=40, help="steps of the fixed-error comparison")
+    ap.add_argument("--horizon", type=int, default=500, help="steps of the fixed-error comparison")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

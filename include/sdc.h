@@ -122,6 +122,36 @@ int sdc_run(sdc_ctx *ctx, void *state, int nsteps);
  * [batch][3][ncoef]; 1 <= batch <= nodes. */
 int sdc_tendency(sdc_ctx *ctx, const void *states, void *tend, int batch);
 
+/* Discrete adjoint (reverse-mode derivative) of T_E: ubar = J_E(states)^T abar
+ * for `batch` base states (1 <= batch <= nodes); states, abar and ubar are
+ * device [batch][3][ncoef].  Adjoints use the real degrees of freedom of the
+ * stored arrays: the real part of an adjoint coefficient is d/dRe, the
+ * imaginary part d/dIm (the convention of torch's complex gradients). */
+int sdc_tendency_adjoint(sdc_ctx *ctx, const void *states, const void *abar, void *ubar, int batch);
+
+/* Adjoint of one dSDC step (Algorithm 2 with Eq. (7) transposed):
+ * ubar_n = (d u_{n+1} / d u_n)^T ubar_next, where u_{n+1} is the step of
+ * state_n.  The step is first re-run to record its node evaluations.  All
+ * three are device state[3][ncoef]. */
+int sdc_step_adjoint(sdc_ctx *ctx, const void *state_n, const void *ubar_next, void *ubar_n);
+
+/* Adjoint of nsteps steps from state0: ubar_initial = (d u_N / d u_0)^T ubar_final.
+ * Memory stays bounded by binomial checkpointing: at most nsnapshots states
+ * (1..32, counting state0) are kept, the schedule minimising forward
+ * recomputation for that budget; each reversed step is re-run once more to
+ * record its evaluations.  forward_steps (HOST, nullable) receives the number
+ * of recomputed forward steps (synchronises).  nsteps in [0, 4096]. */
+int sdc_run_adjoint(sdc_ctx *ctx, const void *state0, int nsteps, int nsnapshots, const void *ubar_final,
+                    void *ubar_initial, long long *forward_steps);
+
+/* Height-misfit loss of the state after nsteps steps from state0,
+ * L = 0.5 sum over the nlat x nlon grid of (h - h_target)^2 with
+ * h = H + Phi'/g (h_target: device double[nlat][nlon]), written to *loss_out
+ * (HOST; synchronises), and its gradient with respect to state0 in grad_out
+ * (device state[3][ncoef]), with the checkpointing of sdc_run_adjoint. */
+int sdc_adjoint_run(sdc_ctx *ctx, const void *state0, int nsteps, int nsnapshots, const double *h_target,
+                    double *loss_out, void *grad_out);
+
 /* Scalar transforms of one field (helpers for initial states and grid
  * diagnostics): spec is device double2[ncoef], grid is device
  * double[nlat][nlon].  grid_to_spec is the Gauss-quadrature analysis onto

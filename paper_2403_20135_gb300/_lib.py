@@ -41,6 +41,10 @@ SIGNATURES = {
     "sdc_step": (_I, [_P, _P, _P, ctypes.POINTER(_D)]),
     "sdc_run": (_I, [_P, _P, _I]),
     "sdc_tendency": (_I, [_P, _P, _P, _I]),
+    "sdc_tendency_adjoint": (_I, [_P, _P, _P, _P, _I]),
+    "sdc_step_adjoint": (_I, [_P, _P, _P, _P]),
+    "sdc_run_adjoint": (_I, [_P, _P, _I, _I, _P, _P, ctypes.POINTER(_LL)]),
+    "sdc_adjoint_run": (_I, [_P, _P, _I, _I, _P, ctypes.POINTER(_D), _P]),
     "sdc_spec_to_grid": (_I, [_P, _P, _P]),
     "sdc_grid_to_spec": (_I, [_P, _P, _P]),
     "sdc_grid_coords": (_I, [_P, ctypes.POINTER(_D), ctypes.POINTER(_D)]),

@@ -8,6 +8,7 @@
 #include <new>
 #include <string>
 #include <vector>
+#include <algorithm>
 
 #include "sdc_internal.h"
 
@@ -66,8 +67,18 @@ struct sdc_ctx {
     double *resid_part = nullptr, *resid = nullptr;
     int sweep_nblocks = 0;
 
+    // adjoint workspaces
+    void *gstore = nullptr;                 // recorded grid fields of a step's evaluations
+    double2 *ub = nullptr, *eb = nullptr;   // node adjoints u-bar^k, E-bar^k [M]
+    double2 *ubn = nullptr, *ubnext = nullptr, *eb0 = nullptr;
+    double2 *snaps = nullptr;               // checkpoint pool [kMaxSnapshots]
+    double *phigrid = nullptr, *rgrid = nullptr, *loss_part = nullptr, *loss_dev = nullptr;
+    long long adj_forward_steps = 0;
+
     cudaGraphExec_t graph[2] = {nullptr, nullptr};   // [with residuals]
     int graph_launches[2] = {0, 0};
+    cudaGraphExec_t graph_retape = nullptr, graph_adjoint = nullptr;
+    int retape_launches = 0, adjoint_launches = 0;
     long long n_explicit = 0, n_solve = 0, n_launch = 0;
 
     long long state_elems() const { return 3LL * d.ncoef; }
@@ -79,8 +90,12 @@ void free_ctx(sdc_ctx *c) {
     if (!c) return;
     for (auto &g : c->graph)
         if (g) cudaGraphExecDestroy(g);
+    if (c->graph_retape) cudaGraphExecDestroy(c->graph_retape);
+    if (c->graph_adjoint) cudaGraphExecDestroy(c->graph_adjoint);
     void *ptrs[] = {c->pbar, c->pbar32, c->eps, c->lam, c->mu2, c->w2, c->syn, c->row_m, c->coef_m, c->tw,
-                    c->tw32, c->un, c->U, c->E, c->E0, c->f1, c->f2, c->f3, c->resid_part, c->resid};
+                    c->tw32, c->un, c->U, c->E, c->E0, c->f1, c->f2, c->f3, c->resid_part, c->resid,
+                    c->gstore, c->ub, c->eb, c->ubn, c->ubnext, c->eb0, c->snaps, c->phigrid, c->rgrid,
+                    c->loss_part, c->loss_dev};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->cap) cudaStreamDestroy(c->cap);
@@ -100,8 +115,33 @@ double qdelta_den(const sdc_ctx *c, int k) {
     return k < c->M ? k : c->M;
 }
 
+DeviceTables tables(const sdc_ctx *c) {
+    const bool fp32 = c->precision != SDC_FP64;
+    DeviceTables tb{};
+    tb.pbar = fp32 ? static_cast<const void *>(c->pbar32) : static_cast<const void *>(c->pbar);
+    tb.tw = fp32 ? static_cast<const void *>(c->tw32) : static_cast<const void *>(c->tw);
+    tb.eps = c->eps;
+    tb.lam = c->lam;
+    tb.mu = c->mu2;
+    tb.w = c->w2;
+    tb.syn = c->syn;
+    tb.row_m = c->row_m;
+    tb.coef_m = c->coef_m;
+    return tb;
+}
+
+size_t grid_slot_bytes(const sdc_ctx *c) {
+    const size_t elem = c->precision == SDC_FP64 ? sizeof(double2) : sizeof(float2);
+    return static_cast<size_t>(c->d.J2) * 4 * c->L * elem;
+}
+
+void *grid_slot(const sdc_ctx *c, int slot) {
+    return static_cast<char *>(c->gstore) + grid_slot_bytes(c) * slot;
+}
+
 cudaError_t tendency(sdc_ctx *c, int B, const double2 *states, long long sstride, double2 *tend,
-                     long long tstride, cudaStream_t s, int *launches, StageTimer *timer = nullptr) {
+                     long long tstride, cudaStream_t s, int *launches, StageTimer *timer = nullptr,
+                     void *grid_store = nullptr) {
     const bool fp32 = c->precision != SDC_FP64;
     DeviceTables tb{};
     tb.pbar = fp32 ? static_cast<const void *>(c->pbar32) : static_cast<const void *>(c->pbar);
@@ -114,17 +154,20 @@ cudaError_t tendency(sdc_ctx *c, int B, const double2 *states, long long sstride
     tb.row_m = c->row_m;
     tb.coef_m = c->coef_m;
     Workspace ws{c->f1, c->f2, c->f3};
-    return launch_tendency(c->d, c->plan, fp32, B, states, sstride, tend, tstride, tb, ws, s, launches, timer);
+    return launch_tendency(c->d, c->plan, fp32, B, states, sstride, tend, tstride, tb, ws, s, launches, timer,
+                           grid_store);
 }
 
 // Enqueue one step u_n -> u_n (in place on c->un), Algorithm 2.
+// With store_grid (the retape of the adjoint) every tendency evaluation also
+// records its grid fields: slot 0 for E0, slots 1 + k M + j for sweep k+1, node j.
 cudaError_t enqueue_step(sdc_ctx *c, cudaStream_t s, bool with_resid, int *launches,
-                         StageTimer *timer = nullptr) {
+                         StageTimer *timer = nullptr, bool store_grid = false) {
     const long long se = c->state_elems();
     const int M = c->M, K = c->K;
     cudaError_t e;
     // E0 = T_E(u_n)
-    e = tendency(c, 1, c->un, se, c->E0, se, s, launches, timer);
+    e = tendency(c, 1, c->un, se, c->E0, se, s, launches, timer, store_grid ? grid_slot(c, 0) : nullptr);
     if (e != cudaSuccess) return e;
 
     SweepParams p{};
@@ -165,7 +208,8 @@ cudaError_t enqueue_step(sdc_ctx *c, cudaStream_t s, bool with_resid, int *launc
             if (e != cudaSuccess) return e;
         }
         if (!last) {
-            e = tendency(c, M, c->U, se, c->E, se, s, launches, timer);
+            e = tendency(c, M, c->U, se, c->E, se, s, launches, timer,
+                         store_grid ? grid_slot(c, 1 + k * M) : nullptr);
             if (e != cudaSuccess) return e;
         }
     }
@@ -190,6 +234,180 @@ int ensure_graph(sdc_ctx *c, bool with_resid) {
     if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
     c->graph_launches[v] = launches;
     return SDC_OK;
+}
+
+// Reverse of one step (Algorithm 2 transposed), after a retape recorded the
+// grid fields: c->ubnext = u-bar_{n+1}  ->  c->ubn = u-bar_n.
+cudaError_t enqueue_step_adjoint(sdc_ctx *c, cudaStream_t s, int *launches) {
+    const long long se = c->state_elems();
+    const int M = c->M, K = c->K;
+    const bool fp32 = c->precision != SDC_FP64;
+    const DeviceTables tb = tables(c);
+    const Workspace ws{c->f1, c->f2, c->f3};
+    SweepAdjParams p{};
+    p.lam = c->lam;
+    p.ncoef = c->d.ncoef;
+    p.dt = c->dt;
+    p.phibar = c->phys.gravity * c->phys.mean_depth;
+    for (int m = 0; m < M; ++m)
+        for (int j = 0; j < M; ++j) p.Q[m][j] = c->Q[m * M + j];
+    p.ubn = c->ubn;
+    p.ebar0 = c->eb0;
+    p.ubout = c->ub;
+    p.ebout = c->eb;
+    p.ostride = se;
+    cudaError_t e;
+    for (int k = K - 1; k >= 0; --k) {           // transpose of sweep k+1
+        const bool last = (k == K - 1);
+        if (!last) {
+            // u-bar_j^{k+1} += J_E(u_j^{k+1})^T E-bar_j^{k+1}
+            e = launch_tendency_adjoint(c->d, c->plan, fp32, M, grid_slot(c, 1 + k * M), c->eb, se, c->ub, se, tb,
+                                        ws, s, launches);
+            if (e != cudaSuccess) return e;
+        }
+        p.ubin = last ? c->ubnext : c->ub;
+        p.ustride = last ? 0 : se;
+        p.m0 = last ? M - 1 : 0;
+        p.m1 = M;
+        p.fold = (k == 0);
+        p.init_un = last;
+        const double den = qdelta_den(c, k + 1);
+        for (int m = 0; m < M; ++m) p.alpha[m] = c->dt * c->tau[m] / den;
+        e = launch_sweep_adjoint(p, M, s, launches);
+        if (e != cudaSuccess) return e;
+    }
+    // u-bar_n += J_E(u_n)^T E-bar_0
+    return launch_tendency_adjoint(c->d, c->plan, fp32, 1, grid_slot(c, 0), c->eb0, se, c->ubn, se, tb, ws, s,
+                                   launches);
+}
+
+int capture(sdc_ctx *c, cudaGraphExec_t *exec, int *nlaunch, int which) {
+    if (*exec) return SDC_OK;
+    cudaGraph_t g = nullptr;
+    SDC_CUDA(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
+    int launches = 0;
+    cudaError_t e = which == 0 ? enqueue_step(c, c->cap, false, &launches, nullptr, true)
+                               : enqueue_step_adjoint(c, c->cap, &launches);
+    cudaError_t e2 = cudaStreamEndCapture(c->cap, &g);
+    if (e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return cuda_fail(e, "capture");
+    }
+    if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    *nlaunch = launches;
+    return SDC_OK;
+}
+
+// One reverse step from the state in c->un: retape (c->un becomes u_{n+1}),
+// optional loss seed from u_{n+1}, then the adjoint; the result u-bar_n is
+// left in c->ubnext for the next step down.
+int reverse_one(sdc_ctx *c, const double *h_target, bool seed) {
+    int st = capture(c, &c->graph_retape, &c->retape_launches, 0);
+    if (st != SDC_OK) return st;
+    st = capture(c, &c->graph_adjoint, &c->adjoint_launches, 1);
+    if (st != SDC_OK) return st;
+    const size_t sbytes = 3ULL * c->d.ncoef * sizeof(double2);
+    SDC_CUDA(cudaGraphLaunch(c->graph_retape, c->stream));
+    if (seed) {
+        SDC_CUDA(cudaMemsetAsync(c->ubnext, 0, sbytes, c->stream));
+        SDC_CUDA(launch_spec_to_grid(c->d, c->plan, c->un, c->phigrid, c->pbar, c->tw,
+                                     static_cast<double2 *>(c->f1), c->stream));
+        SDC_CUDA(launch_height_loss(c->d, c->plan, c->phigrid, h_target, 1.0 / c->phys.gravity, c->phys.mean_depth,
+                                    c->rgrid, c->loss_part, c->loss_dev, c->ubnext, c->pbar, c->tw,
+                                    static_cast<double2 *>(c->f2), c->stream));
+    }
+    SDC_CUDA(cudaGraphLaunch(c->graph_adjoint, c->stream));
+    SDC_CUDA(cudaMemcpyAsync(c->ubnext, c->ubn, sbytes, cudaMemcpyDeviceToDevice, c->stream));
+    c->n_explicit += 2LL * (1 + (c->K - 1) * c->M);
+    c->n_solve += 2LL * ((c->K - 1) * c->M + 1);
+    c->n_launch += c->retape_launches + c->adjoint_launches;
+    return SDC_OK;
+}
+
+// Optimal binomial checkpointing for uniform step costs: reversing n steps
+// from a stored state with s free snapshot slots costs
+//   C(n, s) = min_{0<m<n} [ m + C(n-m, s-1) + C(m, s) ],  C(1, s) = 0,  C(n, 0) = n(n-1)/2
+// forward recomputations (advance m steps and store, reverse the right part
+// with one slot less, restore and reverse the left part).
+struct Schedule {
+    int N = 0, S = 0;
+    std::vector<long long> cost;
+    std::vector<int> split;
+    long long &C(int n, int s) { return cost[static_cast<size_t>(n) * (S + 1) + s]; }
+    int &B(int n, int s) { return split[static_cast<size_t>(n) * (S + 1) + s]; }
+    void build(int n_, int s_) {
+        N = n_;
+        S = s_;
+        cost.assign(static_cast<size_t>(N + 1) * (S + 1), 0);
+        split.assign(static_cast<size_t>(N + 1) * (S + 1), 0);
+        for (int n = 1; n <= N; ++n) C(n, 0) = static_cast<long long>(n) * (n - 1) / 2;
+        for (int s = 1; s <= S; ++s)
+            for (int n = 2; n <= N; ++n) {
+                long long best = -1;
+                int arg = 1;
+                for (int m = 1; m < n; ++m) {
+                    const long long v = m + C(n - m, s - 1) + C(m, s);
+                    if (best < 0 || v < best) { best = v; arg = m; }
+                }
+                C(n, s) = best;
+                B(n, s) = arg;
+            }
+    }
+};
+
+struct Reverser {
+    sdc_ctx *c;
+    Schedule sched;
+    std::vector<int> free_slots;
+    const double *h_target;
+    int N;
+    size_t sbytes;
+
+    int store(int slot) {
+        SDC_CUDA(cudaMemcpyAsync(c->snaps + slot * c->state_elems(), c->un, sbytes, cudaMemcpyDeviceToDevice,
+                                 c->stream));
+        return SDC_OK;
+    }
+    int restore(int slot) {
+        SDC_CUDA(cudaMemcpyAsync(c->un, c->snaps + slot * c->state_elems(), sbytes, cudaMemcpyDeviceToDevice,
+                                 c->stream));
+        return SDC_OK;
+    }
+    int advance(int n);
+    int step(int i) { return reverse_one(c, h_target, h_target != nullptr && i == N - 1); }
+
+    // reverse steps [a, b) given u_a in c->un and in slot slot_a
+    int rev(int a, int b, int sfree, int slot_a) {
+        int st;
+        if (b - a == 1) return step(a);
+        if (sfree == 0 || free_slots.empty()) {
+            for (int i = b - 1; i >= a; --i) {
+                if (i < b - 1 && (st = restore(slot_a)) != SDC_OK) return st;
+                if ((st = advance(i - a)) != SDC_OK) return st;
+                if ((st = step(i)) != SDC_OK) return st;
+            }
+            return SDC_OK;
+        }
+        const int m = a + sched.B(b - a, sfree);
+        if ((st = advance(m - a)) != SDC_OK) return st;
+        const int slot_m = free_slots.back();
+        free_slots.pop_back();
+        if ((st = store(slot_m)) != SDC_OK) return st;
+        if ((st = rev(m, b, sfree - 1, slot_m)) != SDC_OK) return st;
+        free_slots.push_back(slot_m);
+        if ((st = restore(slot_a)) != SDC_OK) return st;
+        return rev(a, m, sfree, slot_a);
+    }
+};
+
+int run_steps(sdc_ctx *c, int nsteps, bool with_resid);
+
+int Reverser::advance(int n) {
+    c->adj_forward_steps += n;
+    return run_steps(c, n, false);
 }
 
 int run_steps(sdc_ctx *c, int nsteps, bool with_resid) {
@@ -289,6 +507,7 @@ int sdc_create(sdc_ctx **out, int T, int J, int L, int M, int K, double dt, cons
 
     SDC_TRY(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
     SDC_TRY(configure_transform_kernels(d, c->plan, precision != SDC_FP64));
+    SDC_TRY(configure_adjoint_kernels(d, c->plan, precision != SDC_FP64));
     if (precision != SDC_FP64) SDC_TRY(configure_transform_kernels(d, c->plan, false));
     if (precision == SDC_FP64) {
         SDC_TRY(upload(&c->pbar, table.data(), table.size()));
@@ -324,6 +543,20 @@ int sdc_create(sdc_ctx **out, int T, int J, int L, int M, int K, double dt, cons
     c->sweep_nblocks = sweep_blocks(d.ncoef);
     SDC_TRY(cudaMalloc(&c->resid_part, static_cast<size_t>(c->sweep_nblocks) * M * 3 * sizeof(double)));
     SDC_TRY(cudaMalloc(&c->resid, static_cast<size_t>(K) * 3 * sizeof(double)));
+    // adjoint: recorded grid fields of one step's evaluations, node adjoints,
+    // checkpoint pool, loss buffers
+    const int nslots = std::max(1 + (K - 1) * M, M);
+    SDC_TRY(cudaMalloc(&c->gstore, grid_slot_bytes(c) * nslots));
+    SDC_TRY(cudaMalloc(&c->ub, sbytes * M));
+    SDC_TRY(cudaMalloc(&c->eb, sbytes * M));
+    SDC_TRY(cudaMalloc(&c->ubn, sbytes));
+    SDC_TRY(cudaMalloc(&c->ubnext, sbytes));
+    SDC_TRY(cudaMalloc(&c->eb0, sbytes));
+    SDC_TRY(cudaMalloc(&c->snaps, sbytes * kMaxSnapshots));
+    SDC_TRY(cudaMalloc(&c->phigrid, sizeof(double) * J * L));
+    SDC_TRY(cudaMalloc(&c->rgrid, sizeof(double) * J * L));
+    SDC_TRY(cudaMalloc(&c->loss_part, sizeof(double) * loss_blocks()));
+    SDC_TRY(cudaMalloc(&c->loss_dev, sizeof(double)));
     SDC_TRY(cudaDeviceSynchronize());
 #undef SDC_TRY
     *out = c;
@@ -345,6 +578,8 @@ int sdc_set_option(sdc_ctx *c, int key, int value) {
             c->qdelta_rule = value;
             for (auto &g : c->graph)
                 if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+            if (c->graph_retape) { cudaGraphExecDestroy(c->graph_retape); c->graph_retape = nullptr; }
+            if (c->graph_adjoint) { cudaGraphExecDestroy(c->graph_adjoint); c->graph_adjoint = nullptr; }
         }
         return SDC_OK;
     }
@@ -432,6 +667,95 @@ int sdc_counters(const sdc_ctx *c, long long *evals, long long *solves, long lon
     if (solves) *solves = c->n_solve;
     if (launches) *launches = c->n_launch;
     return SDC_OK;
+}
+
+int sdc_tendency_adjoint(sdc_ctx *c, const void *states, const void *abar, void *ubar, int batch) {
+    if (!c || !states || !abar || !ubar) return fail(SDC_EINVAL, "NULL argument");
+    if (batch < 1 || batch > c->M) return fail(SDC_EINVAL, "batch must be in [1, nodes]");
+    const long long se = c->state_elems();
+    int launches = 0;
+    // forward evaluation records the base grid fields (its tendency output is scratch)
+    cudaError_t e = tendency(c, batch, static_cast<const double2 *>(states), se, c->E, se, c->stream, &launches,
+                             nullptr, grid_slot(c, 0));
+    if (e != cudaSuccess) return cuda_fail(e, "tendency (record)");
+    SDC_CUDA(cudaMemsetAsync(ubar, 0, sizeof(double2) * se * batch, c->stream));
+    e = launch_tendency_adjoint(c->d, c->plan, c->precision != SDC_FP64, batch, grid_slot(c, 0),
+                                static_cast<const double2 *>(abar), se, static_cast<double2 *>(ubar), se,
+                                tables(c), Workspace{c->f1, c->f2, c->f3}, c->stream, &launches);
+    if (e != cudaSuccess) return cuda_fail(e, "tendency adjoint");
+    c->n_launch += launches;
+    return SDC_OK;
+}
+
+int sdc_step_adjoint(sdc_ctx *c, const void *state_n, const void *ubar_next, void *ubar_n) {
+    if (!c || !state_n || !ubar_next || !ubar_n) return fail(SDC_EINVAL, "NULL argument");
+    const size_t sbytes = 3ULL * c->d.ncoef * sizeof(double2);
+    SDC_CUDA(cudaMemcpyAsync(c->un, state_n, sbytes, cudaMemcpyDeviceToDevice, c->stream));
+    SDC_CUDA(cudaMemcpyAsync(c->ubnext, ubar_next, sbytes, cudaMemcpyDeviceToDevice, c->stream));
+    int st = reverse_one(c, nullptr, false);
+    if (st != SDC_OK) return st;
+    SDC_CUDA(cudaMemcpyAsync(ubar_n, c->ubnext, sbytes, cudaMemcpyDeviceToDevice, c->stream));
+    return SDC_OK;
+}
+
+static int adjoint_common(sdc_ctx *c, const void *state0, int nsteps, int nsnapshots, const void *ubar_final,
+                          const double *h_target, double *loss_out, void *ubar_initial) {
+    if (!c || !state0 || !ubar_initial) return fail(SDC_EINVAL, "NULL argument");
+    if (nsteps < 0 || nsteps > 4096) return fail(SDC_EINVAL, "nsteps must be in [0, 4096]");
+    if (nsnapshots < 1 || nsnapshots > kMaxSnapshots) return fail(SDC_EINVAL, "nsnapshots must be in [1, 32]");
+    const size_t sbytes = 3ULL * c->d.ncoef * sizeof(double2);
+    SDC_CUDA(cudaMemcpyAsync(c->un, state0, sbytes, cudaMemcpyDeviceToDevice, c->stream));
+    c->adj_forward_steps = 0;
+    if (nsteps == 0) {
+        if (h_target) {
+            SDC_CUDA(cudaMemsetAsync(c->ubnext, 0, sbytes, c->stream));
+            SDC_CUDA(launch_spec_to_grid(c->d, c->plan, c->un, c->phigrid, c->pbar, c->tw,
+                                         static_cast<double2 *>(c->f1), c->stream));
+            SDC_CUDA(launch_height_loss(c->d, c->plan, c->phigrid, h_target, 1.0 / c->phys.gravity,
+                                        c->phys.mean_depth, c->rgrid, c->loss_part, c->loss_dev, c->ubnext,
+                                        c->pbar, c->tw, static_cast<double2 *>(c->f2), c->stream));
+        } else {
+            SDC_CUDA(cudaMemcpyAsync(c->ubnext, ubar_final, sbytes, cudaMemcpyDeviceToDevice, c->stream));
+        }
+    } else {
+        if (!h_target)
+            SDC_CUDA(cudaMemcpyAsync(c->ubnext, ubar_final, sbytes, cudaMemcpyDeviceToDevice, c->stream));
+        Reverser r;
+        r.c = c;
+        r.h_target = h_target;
+        r.N = nsteps;
+        r.sbytes = sbytes;
+        const int sfree = nsnapshots - 1;
+        r.sched.build(nsteps, sfree);
+        for (int k = nsnapshots - 1; k >= 1; --k) r.free_slots.push_back(k);
+        int st = r.store(0);
+        if (st != SDC_OK) return st;
+        st = r.rev(0, nsteps, sfree, 0);
+        if (st != SDC_OK) return st;
+    }
+    SDC_CUDA(cudaMemcpyAsync(ubar_initial, c->ubnext, sbytes, cudaMemcpyDeviceToDevice, c->stream));
+    if (loss_out) {
+        SDC_CUDA(cudaMemcpyAsync(loss_out, c->loss_dev, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        SDC_CUDA(cudaStreamSynchronize(c->stream));
+    }
+    return SDC_OK;
+}
+
+int sdc_run_adjoint(sdc_ctx *c, const void *state0, int nsteps, int nsnapshots, const void *ubar_final,
+                    void *ubar_initial, long long *forward_steps) {
+    if (!ubar_final) return fail(SDC_EINVAL, "NULL argument");
+    int st = adjoint_common(c, state0, nsteps, nsnapshots, ubar_final, nullptr, nullptr, ubar_initial);
+    if (st == SDC_OK && forward_steps) {
+        SDC_CUDA(cudaStreamSynchronize(c->stream));
+        *forward_steps = c->adj_forward_steps;
+    }
+    return st;
+}
+
+int sdc_adjoint_run(sdc_ctx *c, const void *state0, int nsteps, int nsnapshots, const double *h_target,
+                    double *loss_out, void *grad_out) {
+    if (!h_target || !loss_out) return fail(SDC_EINVAL, "NULL argument");
+    return adjoint_common(c, state0, nsteps, nsnapshots, nullptr, h_target, loss_out, grad_out);
 }
 
 int sdc_profile_step(sdc_ctx *c, void *state, double *ms, int *launches) {

@@ -12,6 +12,7 @@ namespace sdc {
 
 constexpr int kMaxNodes = 8;
 constexpr int kMaxStages = 16;
+constexpr int kMaxSnapshots = 32;
 
 // Field order of a spectral state (the paper's U-hat, Sec. 3.2).
 enum { F_PHI = 0, F_ZETA = 1, F_DIV = 2 };
@@ -104,6 +105,26 @@ struct Workspace {
     void *f1, *f2, *f3;
 };
 
+// Parameters of the sweep adjoint (transpose of one sweep kernel).
+struct SweepAdjParams {
+    const double2 *ubin;          // node adjoints u-bar_m^{k+1} at ubin + m * ustride
+    long long ustride;
+    double2 *ubout;               // u-bar_j^k at ubout + j * ostride (unless fold)
+    double2 *ebout;               // E-bar_j^k at ebout + j * ostride (unless fold)
+    long long ostride;
+    double2 *ubn;                 // u-bar_n, accumulated (or initialised with init_un)
+    double2 *ebar0;               // with fold: E-bar_0 (the adjoint of T_E(u_n))
+    const double *lam;
+    int ncoef;
+    int m0, m1;                   // nodes the sweep updated
+    int fold;                     // first sweep: sum node adjoints into u-bar_n / E-bar_0
+    int init_un;
+    double dt;
+    double phibar;
+    double Q[kMaxNodes][kMaxNodes];
+    double alpha[kMaxNodes];
+};
+
 // ---- host-side precompute (tables.cpp) ----------------------------------
 void gauss_legendre(int J, std::vector<double> &mu, std::vector<double> &w);
 void radau_right(int M, std::vector<double> &tau, std::vector<double> &Q);
@@ -120,7 +141,8 @@ void twiddles(int L, std::vector<double> &re, std::vector<double> &im);   // e^{
 // Explicit tendency of B states (K1 -> K2 -> K3a -> K3b).
 cudaError_t launch_tendency(const Dims &d, const FftPlan &plan, bool fp32, int B, const double2 *states,
                             long long sstride, double2 *tend, long long tstride, const DeviceTables &tb,
-                            const Workspace &ws, cudaStream_t s, int *launches, StageTimer *timer = nullptr);
+                            const Workspace &ws, cudaStream_t s, int *launches, StageTimer *timer = nullptr,
+                            void *grid_store = nullptr);
 cudaError_t launch_sweep(const SweepParams &p, int M, cudaStream_t s, int *launches,
                          StageTimer *timer = nullptr);
 cudaError_t launch_resid_reduce(const double *part, int nblocks, int M, int m0, int m1,
@@ -134,6 +156,20 @@ cudaError_t launch_spec_to_grid(const Dims &d, const FftPlan &plan, const double
 cudaError_t launch_grid_to_spec(const Dims &d, const FftPlan &plan, const double *grid,
                                 double2 *spec, const double *pbar, const double *w,
                                 const double2 *tw, double2 *f2, cudaStream_t s);
+
+// ---- adjoint (adjoint.cu) ------------------------------------------------
+cudaError_t configure_adjoint_kernels(const Dims &d, const FftPlan &plan, bool fp32);
+// u-bar (accumulated) += J_E^T a-bar for B states whose forward ring kernel
+// recorded its grid fields in grid_base [B][J2][4][L].
+cudaError_t launch_tendency_adjoint(const Dims &d, const FftPlan &plan, bool fp32, int B, const void *grid_base,
+                                    const double2 *abar, long long astride, double2 *ubar, long long ustride,
+                                    const DeviceTables &tb, const Workspace &ws, cudaStream_t s, int *launches);
+cudaError_t launch_sweep_adjoint(const SweepAdjParams &p, int M, cudaStream_t s, int *launches);
+int loss_blocks();
+cudaError_t launch_height_loss(const Dims &d, const FftPlan &plan, const double *phigrid, const double *htarget,
+                               double inv_g, double H, double *rgrid, double *part, double *loss,
+                               double2 *seed_phi, const double *pbar64, const double2 *tw64, double2 *fbuf,
+                               cudaStream_t s);
 
 size_t ring_smem_bytes(int L, int elem_bytes, int *scratch_arrays);
 cudaError_t configure_transform_kernels(const Dims &d, const FftPlan &plan, bool fp32);

@@ -146,7 +146,7 @@ size_t ring_smem_bytes(int L, int elem_bytes, int *scratch_arrays) {
 template <typename R>
 __global__ void k2_ring(const V2<R> *__restrict__ f1, V2<R> *__restrict__ f2, Dims d, FftPlan plan,
                         const V2<R> *__restrict__ tw, const double *__restrict__ mu,
-                        const double *__restrict__ w, int nscratch) {
+                        const double *__restrict__ w, int nscratch, V2<R> *__restrict__ gstore) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V2<R> *X = reinterpret_cast<V2<R> *>(smem_raw);   // [5][L]
     V2<R> *S = X + 5 * plan.L;                          // [nscratch][L]
@@ -180,9 +180,18 @@ __global__ void k2_ring(const V2<R> *__restrict__ f1, V2<R> *__restrict__ f2, Di
     const R cosl2 = R((1.0 - mun) * (1.0 + mun));
     const R fN = R(d.two_omega * mun);
     const R inv2c = R(0.5) / cosl2;
+    // optional record of the grid fields (north ring .x, south ring .y) for
+    // the adjoint: gstore[b][j2][field][L]
+    V2<R> *gs = gstore ? gstore + (static_cast<size_t>(b) * d.J2 + j2) * 4 * L : nullptr;
     for (int k = threadIdx.x; k < L; k += blockDim.x) {
         const V2<R> zz = X[G_ZETA * L + k], pp = X[G_PHI * L + k];
         const V2<R> uu = X[G_U * L + k], vv = X[G_V * L + k];
+        if (gs) {
+            gs[G_ZETA * L + k] = zz;
+            gs[G_PHI * L + k] = pp;
+            gs[G_U * L + k] = uu;
+            gs[G_V * L + k] = vv;
+        }
         // .x = north ring, .y = south ring (where f = -fN)
         const R etaN = zz.x + fN, etaS = zz.y - fN;
         X[P_A * L + k] = mk<R>(etaN * uu.x, etaS * uu.y);
@@ -331,7 +340,8 @@ static cudaError_t configure(const Dims &d, const FftPlan &plan) {
 template <typename R>
 static cudaError_t launch_tendency_t(const Dims &d, const FftPlan &plan, int B, const double2 *states,
                                      long long sstride, double2 *tend, long long tstride, const DeviceTables &tb,
-                                     const Workspace &ws, cudaStream_t s, int *launches, StageTimer *timer) {
+                                     const Workspace &ws, cudaStream_t s, int *launches, StageTimer *timer,
+                                     void *grid_store) {
     const R *pbar = static_cast<const R *>(tb.pbar);
     const V2<R> *tw = static_cast<const V2<R> *>(tb.tw);
     V2<R> *f1 = static_cast<V2<R> *>(ws.f1);
@@ -345,7 +355,8 @@ static cudaError_t launch_tendency_t(const Dims &d, const FftPlan &plan, int B, 
     if (timer) timer->mark(STAGE_SYNTH);
     k1_synthesis<R><<<g1, kK1Threads, sm1, s>>>(states, sstride, d, pbar, tb.syn, f1);
     if (timer) timer->mark(STAGE_RING);
-    k2_ring<R><<<dim3(d.J2, B), kK2Threads, sm2, s>>>(f1, f2, d, plan, tw, tb.mu, tb.w, nscratch);
+    k2_ring<R><<<dim3(d.J2, B), kK2Threads, sm2, s>>>(f1, f2, d, plan, tw, tb.mu, tb.w, nscratch,
+                                                     static_cast<V2<R> *>(grid_store));
     if (timer) timer->mark(STAGE_ANALYSIS);
     k3_project<R><<<dim3((d.next + kK3Threads - 1) / kK3Threads, B), kK3Threads, 0, s>>>(f2, d, pbar, tb.row_m, f3);
     if (timer) timer->mark(STAGE_EPILOGUE);
@@ -365,10 +376,13 @@ cudaError_t configure_transform_kernels(const Dims &d, const FftPlan &plan, bool
 
 cudaError_t launch_tendency(const Dims &d, const FftPlan &plan, bool fp32, int B, const double2 *states,
                             long long sstride, double2 *tend, long long tstride, const DeviceTables &tb,
-                            const Workspace &ws, cudaStream_t s, int *launches, StageTimer *timer) {
+                            const Workspace &ws, cudaStream_t s, int *launches, StageTimer *timer,
+                            void *grid_store) {
     if (fp32)
-        return launch_tendency_t<float>(d, plan, B, states, sstride, tend, tstride, tb, ws, s, launches, timer);
-    return launch_tendency_t<double>(d, plan, B, states, sstride, tend, tstride, tb, ws, s, launches, timer);
+        return launch_tendency_t<float>(d, plan, B, states, sstride, tend, tstride, tb, ws, s, launches, timer,
+                                        grid_store);
+    return launch_tendency_t<double>(d, plan, B, states, sstride, tend, tstride, tb, ws, s, launches, timer,
+                                     grid_store);
 }
 
 // ---------------------------------------------------------------------------

@@ -94,6 +94,48 @@ class Solver:
         _lib.check(self.lib.sdc_tendency(self.h, _ptr(s), _ptr(o), s.shape[0]), "sdc_tendency")
         return o[0] if squeeze else o
 
+    # ---- adjoint ---------------------------------------------------------
+    def tendency_adjoint(self, states: torch.Tensor, abar: torch.Tensor) -> torch.Tensor:
+        """J_E(states)^T abar (batch of states, or one state)."""
+        squeeze = states.dim() == 2
+        s = (states.unsqueeze(0) if squeeze else states).contiguous()
+        a = (abar.unsqueeze(0) if squeeze else abar).contiguous()
+        self._check_state(s, s.shape[0])
+        self._check_state(a, s.shape[0])
+        o = torch.empty_like(s)
+        _lib.check(self.lib.sdc_tendency_adjoint(self.h, _ptr(s), _ptr(a), _ptr(o), s.shape[0]),
+                   "sdc_tendency_adjoint")
+        return o[0] if squeeze else o
+
+    def step_adjoint(self, state: torch.Tensor, ubar_next: torch.Tensor) -> torch.Tensor:
+        self._check_state(state)
+        self._check_state(ubar_next)
+        o = torch.empty_like(state)
+        _lib.check(self.lib.sdc_step_adjoint(self.h, _ptr(state), _ptr(ubar_next), _ptr(o)), "sdc_step_adjoint")
+        return o
+
+    def run_adjoint(self, state0: torch.Tensor, nsteps: int, ubar_final: torch.Tensor, nsnapshots: int = 8):
+        """((d u_N / d u_0)^T ubar_final, number of recomputed forward steps)."""
+        self._check_state(state0)
+        self._check_state(ubar_final)
+        o = torch.empty_like(state0)
+        n = ctypes.c_longlong()
+        _lib.check(self.lib.sdc_run_adjoint(self.h, _ptr(state0), int(nsteps), int(nsnapshots), _ptr(ubar_final),
+                                            _ptr(o), ctypes.byref(n)), "sdc_run_adjoint")
+        return o, n.value
+
+    def adjoint_run(self, state0: torch.Tensor, nsteps: int, h_target: torch.Tensor, nsnapshots: int = 8):
+        """(loss, gradient) of 0.5 sum (h(T) - h_target)^2 with respect to state0."""
+        self._check_state(state0)
+        if h_target.dtype != torch.float64 or tuple(h_target.shape) != (self.nlat, self.nlon):
+            raise ValueError("h_target must be float64 of shape (nlat, nlon)")
+        g = torch.empty_like(state0)
+        loss = ctypes.c_double()
+        _lib.check(self.lib.sdc_adjoint_run(self.h, _ptr(state0), int(nsteps), int(nsnapshots),
+                                            _ptr(h_target.contiguous()), ctypes.byref(loss), _ptr(g)),
+                   "sdc_adjoint_run")
+        return loss.value, g
+
     def spec_to_grid(self, spec: torch.Tensor) -> torch.Tensor:
         if spec.dtype != torch.complex128 or tuple(spec.shape) != (self.ncoef,):
             raise ValueError("spec must be complex128 of shape (ncoef,)")
