@@ -267,7 +267,7 @@ def cuda_arm(args, rank: int, world: int):
     import torch
     import torch.distributed as dist
 
-    from paper_2403_20135_gb300 import SDC_FP64, SDC_MIXED_FP32, Solver
+    from paper_2403_20135_gb300 import SDC_FP64, SDC_MIXED_BF16X3, SDC_MIXED_BF16X6, SDC_MIXED_FP32, Solver
 
     dev = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev)
@@ -321,21 +321,14 @@ def cuda_arm(args, rank: int, world: int):
     e2e = {"value": world * ne2e / (e2e_ms * 1e-3), "unit": "steps/s", "h2d_bytes_per_step": sbytes,
            "d2h_bytes_per_step": sbytes}
 
-    # FP32 mixed mode beside it: throughput and error against the FP64 path
+    # mixed modes beside it: throughput and error against the FP64 path, and the
+    # fixed-error test: the mixed-mode error must stay below the FP64
+    # discretisation error (FP64 at dt against FP64 at dt/4 over the same horizon)
     mixed = None
     if not args.no_mixed:
-        sm = Solver.for_workload(wl, precision=SDC_MIXED_FP32)
-        xs = u0.clone()
-        for _ in range(args.warmup):
-            sm.run(xs, 1)
-        tm = time_device(sm, xs, args.steps, flush)
-        mprof, _ = profile_stages(sm, u0, flush, max(3, min(10, args.steps)))
-        # fixed error: the mixed-mode error against the FP64 path must stay below the
-        # FP64 discretisation error, measured as FP64 at dt against FP64 at dt/4
         nh = args.horizon
-        a64, a32, a64q = u0.clone(), u0.clone(), u0.clone()
+        a64, a64q = u0.clone(), u0.clone()
         s.run(a64, nh)
-        sm.run(a32, nh)
         sq = Solver(wl.T, wl.nlat, wl.nlon, wl.nodes, wl.sweeps, wl.dt / 4, si.RADIUS, si.OMEGA, si.GRAVITY,
                     si.MEAN_DEPTH, precision=SDC_FP64)
         sq.run(a64q, 4 * nh)
@@ -344,15 +337,25 @@ def cuda_arm(args, rank: int, world: int):
         def rel(x, y):
             return ((x - y).abs().pow(2).sum(1) / y.abs().pow(2).sum(1)).sqrt().cpu().numpy()
 
-        err = rel(a32, a64)
         edisc = rel(a64, a64q)
         fields = ("phi", "zeta", "div")
-        mixed = {"fp32": {"value": world * args.steps / (sum(tm) * 1e-3), "unit": "steps/s",
-                          "ms_per_step": sum(tm) / args.steps, "stages": mprof, "horizon_steps": nh,
-                          "rel_l2_vs_fp64": dict(zip(fields, map(float, err))),
-                          "fp64_discretisation_rel_l2": dict(zip(fields, map(float, edisc))),
-                          "fixed_error": bool(np.all(err < edisc))}}
-        sm.close()
+        mixed = {"horizon_steps": nh, "fp64_discretisation_rel_l2": dict(zip(fields, map(float, edisc)))}
+        for name, prec in (("fp32", SDC_MIXED_FP32), ("bf16x3", SDC_MIXED_BF16X3), ("bf16x6", SDC_MIXED_BF16X6)):
+            sm = Solver.for_workload(wl, precision=prec)
+            xs = u0.clone()
+            for _ in range(args.warmup):
+                sm.run(xs, 1)
+            tm = time_device(sm, xs, args.steps, flush)
+            mprof, _ = profile_stages(sm, u0, flush, max(3, min(10, args.steps)))
+            am = u0.clone()
+            sm.run(am, nh)
+            sm.sync()
+            err = rel(am, a64)
+            mixed[name] = {"value": world * args.steps / (sum(tm) * 1e-3), "unit": "steps/s",
+                           "ms_per_step": sum(tm) / args.steps, "stages": mprof,
+                           "rel_l2_vs_fp64": dict(zip(fields, map(float, err))),
+                           "fixed_error": bool(np.all(err < edisc))}
+            sm.close()
 
     adjoint = None
     if not args.no_adjoint:
@@ -383,6 +386,20 @@ def cuda_arm(args, rank: int, world: int):
     s.close()
 
 
+PRECISIONS = {"fp64": 0, "fp32": 1, "bf16x3": 2, "bf16x6": 3}
+
+
+def profile_run(name: str, steps: int):
+    """A few untimed steps of one precision mode (the command profilers wrap)."""
+    from paper_2403_20135_gb300 import Solver
+    wl = si.WORKLOADS[WORKLOAD]
+    s = Solver.for_workload(wl, precision=PRECISIONS[name])
+    u = s.initial_state(wl)
+    s.run(u, steps)
+    s.sync()
+    print(f"profile-run {name}: {steps} steps of {wl.describe()} ok")
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -394,7 +411,12 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--horizon", type=int, default=500, help="steps of the fixed-error comparison")
+    ap.add_argument("--profile-run", choices=sorted(PRECISIONS), default=None,
+                    help="only run --steps untimed steps of this precision (for profilers)")
     args = ap.parse_args()
+    if args.profile_run:
+        profile_run(args.profile_run, args.steps)
+        return
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -54,8 +54,11 @@ typedef struct {
 typedef enum {
     SDC_FP64 = 0,          /* transforms in FP64 */
     SDC_MIXED_FP32 = 1,    /* Legendre contractions and ring FFTs in FP32 */
-    SDC_MIXED_BF16X3 = 2   /* Legendre contractions as 3-term split-BF16 products
-                              on the tensor cores, FP32 accumulation */
+    SDC_MIXED_BF16X3 = 2,  /* ring FFTs in FP32; Legendre contractions on the
+                              tensor cores (tcgen05) with operands split into 2
+                              BF16 pieces, 3 piece products, FP32 accumulation */
+    SDC_MIXED_BF16X6 = 3   /* as SDC_MIXED_BF16X3 with 3 BF16 pieces and 6
+                              piece products (about FP32 accuracy) */
 } sdc_precision;
 
 typedef enum {
@@ -181,6 +184,10 @@ int sdc_counters(const sdc_ctx *ctx, long long *explicit_evals, long long *solve
  * (div/curl recombination per mode), 4 quadrature + implicit solve (sweep),
  * 5 residual reduction. */
 int sdc_profile_step(sdc_ctx *ctx, void *state, double *ms, int *launches);
+
+/* Wait for the context's stream; SDC_ECUDA if a CUDA error is pending or a
+ * tensor-core kernel gave up a bounded wait (its results are then invalid). */
+int sdc_sync(sdc_ctx *ctx);
 
 /* Launches per step of the captured step graph (HOST output): 4 per tendency
  * batch (K per step) plus one sweep kernel per sweep. */

@@ -4,10 +4,10 @@ The hot path (spherical-harmonic tendencies, collocation quadrature, per-mode
 implicit solves, residuals) runs in hand-written CUDA kernels for sm_103a
 behind the C ABI of include/sdc.h; ``Solver`` is its thin Python face.
 """
-from ._lib import (SDC_FP64, SDC_MIXED_FP32, SDC_MIXED_BF16X3, SDC_QDELTA_CLAMPED,
+from ._lib import (SDC_FP64, SDC_MIXED_FP32, SDC_MIXED_BF16X3, SDC_MIXED_BF16X6, SDC_QDELTA_CLAMPED,
                    SDC_QDELTA_LITERAL, SdcError, LIB_PATH, load)
 
-__all__ = ["Solver", "SDC_FP64", "SDC_MIXED_FP32", "SDC_MIXED_BF16X3", "SDC_QDELTA_CLAMPED",
+__all__ = ["Solver", "SDC_FP64", "SDC_MIXED_FP32", "SDC_MIXED_BF16X3", "SDC_MIXED_BF16X6", "SDC_QDELTA_CLAMPED",
            "SDC_QDELTA_LITERAL", "SdcError", "LIB_PATH", "load"]
 
 

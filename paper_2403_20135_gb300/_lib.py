@@ -12,7 +12,7 @@ import os
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "lib", "libsdc_swe.so")
 
-SDC_FP64, SDC_MIXED_FP32, SDC_MIXED_BF16X3 = 0, 1, 2
+SDC_FP64, SDC_MIXED_FP32, SDC_MIXED_BF16X3, SDC_MIXED_BF16X6 = 0, 1, 2, 3
 SDC_OK, SDC_EINVAL, SDC_ENOMEM, SDC_ECUDA, SDC_EDIVERGED, SDC_ESTATE, SDC_EUNSUPPORTED = range(7)
 SDC_OPT_QDELTA_RULE = 1
 SDC_QDELTA_CLAMPED, SDC_QDELTA_LITERAL = 0, 1
@@ -51,6 +51,7 @@ SIGNATURES = {
     "sdc_collocation": (_I, [_P, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
     "sdc_counters": (_I, [_P, ctypes.POINTER(_LL), ctypes.POINTER(_LL), ctypes.POINTER(_LL)]),
     "sdc_launches_per_step": (_I, [_P, ctypes.POINTER(_I)]),
+    "sdc_sync": (_I, [_P]),
     "sdc_profile_step": (_I, [_P, _P, ctypes.POINTER(_D), ctypes.POINTER(_I)]),
     "sdc_spec_to_grid_static": (_I, [_I, _I, _I, _P, _P, _P]),
     "sdc_strerror": (ctypes.c_char_p, [_I]),

@@ -147,9 +147,11 @@ __global__ void k2t_ring(const V2<R> *__restrict__ wbar, const V2<R> *__restrict
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V2<R> *X = reinterpret_cast<V2<R> *>(smem_raw);   // [5][L]
     V2<R> *S = X + 5 * plan.L;
+    V2<R> *TW = S + nscratch * plan.L;                  // twiddles [L]
     const int j2 = blockIdx.x;
     const int b = blockIdx.y;
     const int T = d.T, L = plan.L, J2 = d.J2;
+    for (int k = threadIdx.x; k < L; k += blockDim.x) TW[k] = tw[k];
     const double mun = mu[j2];
     const double c2 = (1.0 - mun) * (1.0 + mun);
     const R wt = R(w[j2] / c2), wp = R(w[j2]);
@@ -175,7 +177,7 @@ __global__ void k2t_ring(const V2<R> *__restrict__ wbar, const V2<R> *__restrict
         X[i] = z;
     }
     __syncthreads();
-    fft_inplace<R>(X, S, nscratch, 5, plan, tw, true);
+    fft_inplace<R>(X, S, nscratch, 5, plan, TW, true);
 
     const V2<R> *gb = gbase + (static_cast<size_t>(b) * J2 + j2) * 4 * L;
     const R fN = R(d.two_omega * mun);
@@ -194,7 +196,7 @@ __global__ void k2t_ring(const V2<R> *__restrict__ wbar, const V2<R> *__restrict
                                Bb.y * etaS + Db.y * pp.y + Eb.y * vv.y * ic2);
     }
     __syncthreads();
-    fft_inplace<R>(X, S, nscratch, 4, plan, tw, false);
+    fft_inplace<R>(X, S, nscratch, 4, plan, TW, false);
 
     V2<R> *o = f1bar + (static_cast<size_t>(b) * J2 + j2) * 8 * (T + 1);
     for (int i = threadIdx.x; i < 4 * (T + 1); i += blockDim.x) {

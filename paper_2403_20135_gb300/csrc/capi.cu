@@ -65,6 +65,7 @@ struct sdc_ctx {
     double2 *un = nullptr, *U = nullptr, *E = nullptr, *E0 = nullptr;
     void *f1 = nullptr, *f2 = nullptr, *f3 = nullptr;
     double *resid_part = nullptr, *resid = nullptr;
+    double *den = nullptr;                  // [K][M][ncoef] solve denominators per sweep
     int sweep_nblocks = 0;
 
     // adjoint workspaces
@@ -74,6 +75,13 @@ struct sdc_ctx {
     double2 *snaps = nullptr;               // checkpoint pool [kMaxSnapshots]
     double *phigrid = nullptr, *rgrid = nullptr, *loss_part = nullptr, *loss_dev = nullptr;
     long long adj_forward_steps = 0;
+
+    // tensor-core Legendre tables (split-BF16 modes)
+    TcTables tc{};
+    uint16_t *tc_a3 = nullptr, *tc_a1 = nullptr;
+    TcTile3 *tc_t3 = nullptr;
+    TcTile1 *tc_t1 = nullptr;
+    int *tc_err = nullptr;
 
     cudaGraphExec_t graph[2] = {nullptr, nullptr};   // [with residuals]
     int graph_launches[2] = {0, 0};
@@ -95,7 +103,7 @@ void free_ctx(sdc_ctx *c) {
     void *ptrs[] = {c->pbar, c->pbar32, c->eps, c->lam, c->mu2, c->w2, c->syn, c->row_m, c->coef_m, c->tw,
                     c->tw32, c->un, c->U, c->E, c->E0, c->f1, c->f2, c->f3, c->resid_part, c->resid,
                     c->gstore, c->ub, c->eb, c->ubn, c->ubnext, c->eb0, c->snaps, c->phigrid, c->rgrid,
-                    c->loss_part, c->loss_dev};
+                    c->loss_part, c->loss_dev, c->tc_a3, c->tc_a1, c->tc_t3, c->tc_t1, c->tc_err, c->den};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->cap) cudaStreamDestroy(c->cap);
@@ -154,8 +162,9 @@ cudaError_t tendency(sdc_ctx *c, int B, const double2 *states, long long sstride
     tb.row_m = c->row_m;
     tb.coef_m = c->coef_m;
     Workspace ws{c->f1, c->f2, c->f3};
+    const bool use_tc = c->precision == SDC_MIXED_BF16X3 || c->precision == SDC_MIXED_BF16X6;
     return launch_tendency(c->d, c->plan, fp32, B, states, sstride, tend, tstride, tb, ws, s, launches, timer,
-                           grid_store);
+                           grid_store, use_tc ? &c->tc : nullptr);
 }
 
 // Enqueue one step u_n -> u_n (in place on c->un), Algorithm 2.
@@ -189,6 +198,7 @@ cudaError_t enqueue_step(sdc_ctx *c, cudaStream_t s, bool with_resid, int *launc
         p.estride = first ? 0 : se;
         const double den = qdelta_den(c, k + 1);
         for (int m = 0; m < M; ++m) p.alpha[m] = c->dt * c->tau[m] / den;
+        p.den = c->den + static_cast<size_t>(k) * M * c->d.ncoef;
         if (last) {                           // node M only, written to u_{n+1}
             p.m0 = M - 1;
             p.m1 = M;
@@ -214,6 +224,24 @@ cudaError_t enqueue_step(sdc_ctx *c, cudaStream_t s, bool with_resid, int *launc
         }
     }
     return cudaSuccess;
+}
+
+// 1 / (1 + alpha^2 Phibar lambda_n) for every sweep, node and mode.
+cudaError_t upload_denominators(sdc_ctx *c) {
+    const int nc = c->d.ncoef, M = c->M, K = c->K;
+    std::vector<double> lam(nc), den(static_cast<size_t>(K) * M * nc);
+    for (int m = 0; m <= c->T; ++m)
+        for (int n = m; n <= c->T; ++n)
+            lam[order_offset(c->T, m) + n - m] = double(n) * double(n + 1) / (c->phys.radius * c->phys.radius);
+    const double phibar = c->phys.gravity * c->phys.mean_depth;
+    for (int k = 0; k < K; ++k) {
+        const double q = qdelta_den(c, k + 1);
+        for (int m = 0; m < M; ++m) {
+            const double al = c->dt * c->tau[m] / q;
+            for (int i = 0; i < nc; ++i) den[(static_cast<size_t>(k) * M + m) * nc + i] = 1.0 / (1.0 + al * al * phibar * lam[i]);
+        }
+    }
+    return cudaMemcpy(c->den, den.data(), den.size() * sizeof(double), cudaMemcpyHostToDevice);
 }
 
 int ensure_graph(sdc_ctx *c, bool with_resid) {
@@ -451,9 +479,9 @@ int sdc_create(sdc_ctx **out, int T, int J, int L, int M, int K, double dt, cons
     if (!(dt > 0.0) || !std::isfinite(dt)) return fail(SDC_EINVAL, "dt must be positive and finite");
     if (!phys || !(phys->radius > 0) || !(phys->gravity > 0) || !(phys->mean_depth > 0) || !std::isfinite(phys->omega))
         return fail(SDC_EINVAL, "physical constants invalid");
-    if (precision != SDC_FP64 && precision != SDC_MIXED_FP32 && precision != SDC_MIXED_BF16X3)
+    if (precision != SDC_FP64 && precision != SDC_MIXED_FP32 && precision != SDC_MIXED_BF16X3 &&
+        precision != SDC_MIXED_BF16X6)
         return fail(SDC_EINVAL, "unknown precision");
-    if (precision == SDC_MIXED_BF16X3) return fail(SDC_EUNSUPPORTED, "split-BF16 precision not built");
 
     sdc_ctx *c = new (std::nothrow) sdc_ctx();
     if (!c) return fail(SDC_ENOMEM, "host allocation");
@@ -521,6 +549,32 @@ int sdc_create(sdc_ctx **out, int T, int J, int L, int M, int K, double dt, cons
         SDC_TRY(upload(&c->pbar, table.data(), table.size()));
         SDC_TRY(upload(&c->tw, tw.data(), tw.size()));
     }
+    if (precision == SDC_MIXED_BF16X3 || precision == SDC_MIXED_BF16X6) {
+        std::vector<uint16_t> a3, a1;
+        std::vector<TcTile3> t3;
+        std::vector<TcTile1> t1;
+        int kj = 0;
+        const int np = precision == SDC_MIXED_BF16X3 ? 2 : 3;
+        build_tc_tables(T, d.J2, d.J2p, table, np, a3, t3, a1, t1, &kj);
+        SDC_TRY(upload(&c->tc_a3, a3.data(), a3.size()));
+        SDC_TRY(upload(&c->tc_a1, a1.data(), a1.size()));
+        SDC_TRY(upload(&c->tc_t3, t3.data(), t3.size()));
+        SDC_TRY(upload(&c->tc_t1, t1.data(), t1.size()));
+        SDC_TRY(cudaMalloc(&c->tc_err, sizeof(int)));
+        SDC_TRY(cudaMemset(c->tc_err, 0, sizeof(int)));
+        SDC_TRY(configure_tc_kernels());
+        c->tc.a3 = c->tc_a3;
+        c->tc.a1 = c->tc_a1;
+        c->tc.elems3 = static_cast<long long>(a3.size() / np);
+        c->tc.elems1 = static_cast<long long>(a1.size() / np);
+        c->tc.tiles3 = c->tc_t3;
+        c->tc.tiles1 = c->tc_t1;
+        c->tc.ntiles3 = static_cast<int>(t3.size());
+        c->tc.ntiles1 = static_cast<int>(t1.size());
+        c->tc.npieces = np;
+        c->tc.kj = kj;
+        c->tc.err = c->tc_err;
+    }
     SDC_TRY(upload(&c->eps, eps.data(), eps.size()));
     SDC_TRY(upload(&c->syn, syn.data(), syn.size()));
     SDC_TRY(upload(&c->row_m, row_m.data(), row_m.size()));
@@ -543,6 +597,8 @@ int sdc_create(sdc_ctx **out, int T, int J, int L, int M, int K, double dt, cons
     c->sweep_nblocks = sweep_blocks(d.ncoef);
     SDC_TRY(cudaMalloc(&c->resid_part, static_cast<size_t>(c->sweep_nblocks) * M * 3 * sizeof(double)));
     SDC_TRY(cudaMalloc(&c->resid, static_cast<size_t>(K) * 3 * sizeof(double)));
+    SDC_TRY(cudaMalloc(&c->den, static_cast<size_t>(K) * M * d.ncoef * sizeof(double)));
+    SDC_TRY(upload_denominators(c));
     // adjoint: recorded grid fields of one step's evaluations, node adjoints,
     // checkpoint pool, loss buffers
     const int nslots = std::max(1 + (K - 1) * M, M);
@@ -576,6 +632,8 @@ int sdc_set_option(sdc_ctx *c, int key, int value) {
         if (value != SDC_QDELTA_CLAMPED && value != SDC_QDELTA_LITERAL) return fail(SDC_EINVAL, "bad q-delta rule");
         if (value != c->qdelta_rule) {
             c->qdelta_rule = value;
+            SDC_CUDA(cudaStreamSynchronize(c->stream));
+            SDC_CUDA(upload_denominators(c));
             for (auto &g : c->graph)
                 if (g) { cudaGraphExecDestroy(g); g = nullptr; }
             if (c->graph_retape) { cudaGraphExecDestroy(c->graph_retape); c->graph_retape = nullptr; }
@@ -790,6 +848,18 @@ int sdc_profile_step(sdc_ctx *c, void *state, double *ms, int *launches) {
     }
     for (int i = 0; i <= StageTimer::kMax; ++i) cudaEventDestroy(tm.ev[i]);
     if (e != cudaSuccess) return cuda_fail(e, "profiled step");
+    return SDC_OK;
+}
+
+int sdc_sync(sdc_ctx *c) {
+    if (!c) return fail(SDC_EINVAL, "ctx is NULL");
+    SDC_CUDA(cudaStreamSynchronize(c->stream));
+    SDC_CUDA(cudaGetLastError());
+    if (c->tc_err) {
+        int flag = 0;
+        SDC_CUDA(cudaMemcpy(&flag, c->tc_err, sizeof(int), cudaMemcpyDeviceToHost));
+        if (flag) return fail(SDC_ECUDA, "a tensor-core kernel gave up a bounded wait (code " + std::to_string(flag) + ")");
+    }
     return SDC_OK;
 }
 

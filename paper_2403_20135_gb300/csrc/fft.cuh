@@ -29,9 +29,9 @@ template <typename R> __device__ __forceinline__ V2<R> mul_mi(V2<R> a) { return 
 // memory, all threads of the block cooperating.  Forward: e^{-i...};
 // inverse: e^{+i...}, unscaled.  Returns the buffer that holds the result.
 // ---------------------------------------------------------------------------
-template <typename R>
-__device__ __forceinline__ void butterfly(V2<R> *v, int radix, bool inv) {
-    if (radix == 4) {
+template <typename R, int RADIX>
+__device__ __forceinline__ void butterfly(V2<R> *v, bool inv) {
+    if constexpr (RADIX == 4) {
         const V2<R> a0 = cadd<R>(v[0], v[2]), a1 = csub<R>(v[0], v[2]);
         const V2<R> b0 = cadd<R>(v[1], v[3]), b1 = csub<R>(v[1], v[3]);
         v[0] = cadd<R>(a0, b0);
@@ -39,7 +39,7 @@ __device__ __forceinline__ void butterfly(V2<R> *v, int radix, bool inv) {
         const V2<R> ib1 = inv ? mul_i<R>(b1) : mul_mi<R>(b1);
         v[1] = cadd<R>(a1, ib1);
         v[3] = csub<R>(a1, ib1);
-    } else if (radix == 2) {
+    } else if constexpr (RADIX == 2) {
         const V2<R> a = v[0];
         v[0] = cadd<R>(a, v[1]);
         v[1] = csub<R>(a, v[1]);
@@ -47,11 +47,40 @@ __device__ __forceinline__ void butterfly(V2<R> *v, int radix, bool inv) {
         const R h = R(0.86602540378443864676);   // sqrt(3)/2
         const V2<R> t1 = cadd<R>(v[1], v[2]);
         const V2<R> t2 = csub<R>(v[0], cscale<R>(t1, R(0.5)));
-        V2<R> t3 = cscale<R>(csub<R>(v[1], v[2]), inv ? h : -h);
+        const V2<R> t3 = cscale<R>(csub<R>(v[1], v[2]), inv ? h : -h);
         const V2<R> it3 = mul_i<R>(t3);
         v[0] = cadd<R>(v[0], t1);
         v[1] = cadd<R>(t2, it3);
         v[2] = csub<R>(t2, it3);
+    }
+}
+
+// One Stockham stage of radix RADIX over nb sequences (compile-time radix so
+// the butterfly operands stay in registers).
+template <typename R, int RADIX>
+__device__ __forceinline__ void fft_stage(const V2<R> *src, V2<R> *dst, int nb, int L, int Ns,
+                                          const V2<R> *__restrict__ tw, bool inv) {
+    const int Lr = L / RADIX;
+    const int tws = L / (Ns * RADIX);
+    const bool pow2 = (Ns & (Ns - 1)) == 0;
+    for (int bb = 0; bb < nb; ++bb) {
+        const V2<R> *in = src + bb * L;
+        V2<R> *out = dst + bb * L;
+        for (int j = threadIdx.x; j < Lr; j += blockDim.x) {
+            const int k = pow2 ? (j & (Ns - 1)) : (j % Ns);
+            V2<R> v[RADIX];
+            v[0] = in[j];
+#pragma unroll
+            for (int r = 1; r < RADIX; ++r) {
+                V2<R> w = tw[r * k * tws];
+                if (inv) w.y = -w.y;
+                v[r] = cmul<R>(in[j + r * Lr], w);
+            }
+            butterfly<R, RADIX>(v, inv);
+            const int base = (j - k) * RADIX + k;
+#pragma unroll
+            for (int r = 0; r < RADIX; ++r) out[base + r * Ns] = v[r];
+        }
     }
 }
 
@@ -63,25 +92,9 @@ __device__ V2<R> *fft_batch(V2<R> *x, V2<R> *y, int nb, const FftPlan &plan,
     int Ns = 1;
     for (int s = 0; s < plan.nstages; ++s) {
         const int radix = plan.radix[s];
-        const int Lr = L / radix;
-        const int tws = L / (Ns * radix);
-        for (int idx = threadIdx.x; idx < nb * Lr; idx += blockDim.x) {
-            const int bb = idx / Lr;
-            const int j = idx - bb * Lr;
-            const V2<R> *in = src + bb * L;
-            V2<R> *out = dst + bb * L;
-            const int k = j % Ns;
-            V2<R> v[4];
-            v[0] = in[j];
-            for (int r = 1; r < radix; ++r) {
-                V2<R> w = tw[r * k * tws];
-                if (inv) w.y = -w.y;
-                v[r] = cmul<R>(in[j + r * Lr], w);
-            }
-            butterfly<R>(v, radix, inv);
-            const int base = (j - k) * radix + k;
-            for (int r = 0; r < radix; ++r) out[base + r * Ns] = v[r];
-        }
+        if (radix == 4) fft_stage<R, 4>(src, dst, nb, L, Ns, tw, inv);
+        else if (radix == 2) fft_stage<R, 2>(src, dst, nb, L, Ns, tw, inv);
+        else fft_stage<R, 3>(src, dst, nb, L, Ns, tw, inv);
         __syncthreads();
         V2<R> *t = src; src = dst; dst = t;
         Ns *= radix;

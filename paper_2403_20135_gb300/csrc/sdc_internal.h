@@ -57,6 +57,7 @@ struct SweepParams {
     double2 *out;                 // node m result at out + (m - m0) * ostride
     long long ostride;
     const double *lam;            // n(n+1)/a^2 per packed coefficient
+    const double *den;            // [M][ncoef] 1 / (1 + alpha_m^2 Phibar lambda_n) of this sweep
     double *resid_part;           // [gridDim.x][M][3] or nullptr
     int ncoef;
     int T;
@@ -125,6 +126,36 @@ struct SweepAdjParams {
     double alpha[kMaxNodes];
 };
 
+// Tensor-core (tcgen05) Legendre contractions with split-BF16 operands.
+// Rows of order m with parity p of n' - m ("group (m, p)"): n' = m + p + 2q,
+// q = 0..R-1.  The static Legendre operand is stored pre-split into npieces
+// BF16 pieces, tile by tile and chunk by chunk in the canonical K-major
+// shared-memory layout (8 x 8 core matrices, [row block][k block][8][8]), so
+// one chunk of one piece is one contiguous bulk copy.
+constexpr int kTcChunkKB = 8;     // k blocks (of 8 elements) per chunk
+struct TcTile3 {                  // analysis: rows q0..q0+nrows of group (m, p), K = latitudes
+    int m, p, q0, nrows, nrb;
+    long long aoff;               // element offset of chunk 0 in each piece table
+};
+struct TcTile1 {                  // synthesis: latitudes j0..j0+nj of group (m, p), K = rows (padded to KR)
+    int m, p, j0, nj, njb, R, KR;
+    long long aoff;
+};
+struct TcTables {
+    const uint16_t *a3;           // analysis pieces [npieces][elems3]
+    const uint16_t *a1;           // synthesis pieces [npieces][elems1]
+    long long elems3, elems1;
+    const TcTile3 *tiles3;
+    const TcTile1 *tiles1;
+    int ntiles3, ntiles1;
+    int npieces;
+    int kj;                       // latitudes padded to a multiple of 16
+    int *err;                     // device flag: a bounded wait gave up
+};
+void build_tc_tables(int T, int J2, int J2p, const std::vector<double> &pbar, int npieces,
+                     std::vector<uint16_t> &a3, std::vector<TcTile3> &tiles3, std::vector<uint16_t> &a1,
+                     std::vector<TcTile1> &tiles1, int *kj_out);
+
 // ---- host-side precompute (tables.cpp) ----------------------------------
 void gauss_legendre(int J, std::vector<double> &mu, std::vector<double> &w);
 void radau_right(int M, std::vector<double> &tau, std::vector<double> &Q);
@@ -138,11 +169,17 @@ bool fft_plan(int L, FftPlan &plan);
 void twiddles(int L, std::vector<double> &re, std::vector<double> &im);   // e^{-2 pi i k / L}
 
 // ---- kernel launchers (transforms.cu, sweep.cu) -------------------------
-// Explicit tendency of B states (K1 -> K2 -> K3a -> K3b).
+// Explicit tendency of B states (K1 -> K2 -> K3a -> K3b).  With tc (FP32
+// transforms only) the two Legendre contractions run on the tensor cores.
 cudaError_t launch_tendency(const Dims &d, const FftPlan &plan, bool fp32, int B, const double2 *states,
                             long long sstride, double2 *tend, long long tstride, const DeviceTables &tb,
                             const Workspace &ws, cudaStream_t s, int *launches, StageTimer *timer = nullptr,
-                            void *grid_store = nullptr);
+                            void *grid_store = nullptr, const TcTables *tc = nullptr);
+cudaError_t launch_tc_synthesis(const TcTables &tc, const Dims &d, int B, const double2 *states, long long sstride,
+                                const double *syn, const int *row_m, float2 *cbuf, float2 *f1, cudaStream_t s);
+cudaError_t launch_tc_projection(const TcTables &tc, const Dims &d, int B, const float2 *f2, float2 *y,
+                                 cudaStream_t s);
+cudaError_t configure_tc_kernels();
 cudaError_t launch_sweep(const SweepParams &p, int M, cudaStream_t s, int *launches,
                          StageTimer *timer = nullptr);
 cudaError_t launch_resid_reduce(const double *part, int nblocks, int M, int m0, int m1,

@@ -6,7 +6,8 @@
 // Per mode (n, m) with lambda_n = n(n+1)/a^2 and F_j = L_g(u_j^k) + T_E(u_j^k):
 //   R_m   = u_n + dt sum_j q_{m,j} F_j                   (collocation right side)
 //   rhs_m = R_m - alpha_m L_g(u_m^k),  alpha_m = dt q^Delta_{m,m}
-//   (I - alpha_m L_g) u_m^{k+1} = rhs_m, in closed form for
+//   (I - alpha_m L_g) u_m^{k+1} = rhs_m, in closed form (the denominators
+//   1 / (1 + alpha_m^2 Phibar lambda_n) of the sweep come from a host table) for
 //   L_g(Phi', zeta, div) = (-Phibar div, 0, lambda_n Phi'):
 //     Phi' = (rhs_Phi - alpha Phibar rhs_div) / (1 + alpha^2 Phibar lambda_n)
 //     div  = rhs_div + alpha lambda_n Phi',  zeta = rhs_zeta
@@ -18,11 +19,11 @@
 
 namespace sdc {
 
-constexpr int kSweepThreads = 256;
+constexpr int kSweepThreads = 64;
 
 int sweep_blocks(int ncoef) { return (ncoef + kSweepThreads - 1) / kSweepThreads; }
 
-template <int M>
+template <int M, bool RESID>
 __global__ void __launch_bounds__(kSweepThreads) k4_sweep(SweepParams p) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int nc = p.ncoef;
@@ -65,18 +66,19 @@ __global__ void __launch_bounds__(kSweepThreads) k4_sweep(SweepParams p) {
             Rp = make_double2(fma(dt, Rp.x, un_p.x), fma(dt, Rp.y, un_p.y));
             Rz = make_double2(fma(dt, Rz.x, un_z.x), fma(dt, Rz.y, un_z.y));
             Rd = make_double2(fma(dt, Rd.x, un_d.x), fma(dt, Rd.y, un_d.y));
-            // residual of the current iterate
-            const double rpx = Rp.x - up[m].x, rpy = Rp.y - up[m].y;
-            const double rzx = Rz.x - uz[m].x, rzy = Rz.y - uz[m].y;
-            const double rdx = Rd.x - ud[m].x, rdy = Rd.y - ud[m].y;
-            rs[m][F_PHI] = wgt * (rpx * rpx + rpy * rpy);
-            rs[m][F_ZETA] = wgt * (rzx * rzx + rzy * rzy);
-            rs[m][F_DIV] = wgt * (rdx * rdx + rdy * rdy);
+            if (RESID) {   // residual of the current iterate
+                const double rpx = Rp.x - up[m].x, rpy = Rp.y - up[m].y;
+                const double rzx = Rz.x - uz[m].x, rzy = Rz.y - uz[m].y;
+                const double rdx = Rd.x - ud[m].x, rdy = Rd.y - ud[m].y;
+                rs[m][F_PHI] = wgt * (rpx * rpx + rpy * rpy);
+                rs[m][F_ZETA] = wgt * (rzx * rzx + rzy * rzy);
+                rs[m][F_DIV] = wgt * (rdx * rdx + rdy * rdy);
+            }
             // rhs = R - alpha L_g(u_m^k)
             const double al = p.alpha[m];
             const double2 bp = make_double2(Rp.x + al * p.phibar * ud[m].x, Rp.y + al * p.phibar * ud[m].y);
             const double2 bd = make_double2(Rd.x - al * lam * up[m].x, Rd.y - al * lam * up[m].y);
-            const double den = 1.0 / (1.0 + al * al * p.phibar * lam);
+            const double den = p.den[m * nc + i];             // 1 / (1 + alpha^2 Phibar lambda_n)
             const double2 np = make_double2((bp.x - al * p.phibar * bd.x) * den, (bp.y - al * p.phibar * bd.y) * den);
             const double2 nd = make_double2(bd.x + al * lam * np.x, bd.y + al * lam * np.y);
             double2 *o = p.out + (m - p.m0) * p.ostride;
@@ -86,7 +88,7 @@ __global__ void __launch_bounds__(kSweepThreads) k4_sweep(SweepParams p) {
         }
     }
 
-    if (p.resid_part == nullptr) return;
+    if (!RESID) return;
     // block reduction of the residual partial sums (warp shuffle, then smem)
     __shared__ double red[kSweepThreads / 32][M * 3];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -135,17 +137,17 @@ __global__ void k5_resid_reduce(const double *__restrict__ part, int nblocks, in
 cudaError_t launch_sweep(const SweepParams &p, int M, cudaStream_t s, int *launches, StageTimer *timer) {
     const int nb = sweep_blocks(p.ncoef);
     if (timer) timer->mark(STAGE_SWEEP);
+#define SDC_SWEEP_CASE(MM)                                                        \
+    case MM:                                                                      \
+        if (p.resid_part) k4_sweep<MM, true><<<nb, kSweepThreads, 0, s>>>(p);     \
+        else k4_sweep<MM, false><<<nb, kSweepThreads, 0, s>>>(p);                 \
+        break;
     switch (M) {
-        case 1: k4_sweep<1><<<nb, kSweepThreads, 0, s>>>(p); break;
-        case 2: k4_sweep<2><<<nb, kSweepThreads, 0, s>>>(p); break;
-        case 3: k4_sweep<3><<<nb, kSweepThreads, 0, s>>>(p); break;
-        case 4: k4_sweep<4><<<nb, kSweepThreads, 0, s>>>(p); break;
-        case 5: k4_sweep<5><<<nb, kSweepThreads, 0, s>>>(p); break;
-        case 6: k4_sweep<6><<<nb, kSweepThreads, 0, s>>>(p); break;
-        case 7: k4_sweep<7><<<nb, kSweepThreads, 0, s>>>(p); break;
-        case 8: k4_sweep<8><<<nb, kSweepThreads, 0, s>>>(p); break;
+        SDC_SWEEP_CASE(1) SDC_SWEEP_CASE(2) SDC_SWEEP_CASE(3) SDC_SWEEP_CASE(4)
+        SDC_SWEEP_CASE(5) SDC_SWEEP_CASE(6) SDC_SWEEP_CASE(7) SDC_SWEEP_CASE(8)
         default: return cudaErrorInvalidValue;
     }
+#undef SDC_SWEEP_CASE
     if (launches) *launches += 1;
     return cudaGetLastError();
 }

@@ -2,7 +2,9 @@
 // table, recurrence coefficients, Radau-right collocation data, FFT plans and
 // twiddles.  Runs once in sdc_create; everything here is uploaded to the
 // device and never recomputed on the hot path.
+#include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <vector>
 
 #include "sdc_internal.h"
@@ -186,6 +188,114 @@ void order_maps(int T, std::vector<int> &row_m, std::vector<int> &coef_m) {
     for (int m = 0; m <= T; ++m) {
         for (int n = m; n <= T + 1; ++n) row_m.push_back(m);
         for (int n = m; n <= T; ++n) coef_m.push_back(m);
+    }
+}
+
+namespace {
+
+// Round to the nearest BF16 (ties to even) through the float bit pattern.
+uint16_t to_bf16(double x) {
+    const float f = static_cast<float>(x);
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    if ((u & 0x7F800000u) == 0x7F800000u) return static_cast<uint16_t>(u >> 16);   // inf / nan
+    const uint32_t lsb = (u >> 16) & 1u;
+    u += 0x7FFFu + lsb;
+    return static_cast<uint16_t>(u >> 16);
+}
+
+double from_bf16(uint16_t h) {
+    const uint32_t u = static_cast<uint32_t>(h) << 16;
+    float f;
+    std::memcpy(&f, &u, 4);
+    return f;
+}
+
+// x = sum of npieces BF16 values, each the rounded residual of the previous.
+void split_pieces(double x, int npieces, uint16_t *out) {
+    double r = x;
+    for (int i = 0; i < npieces; ++i) {
+        out[i] = to_bf16(r);
+        r -= from_bf16(out[i]);
+    }
+}
+
+}  // namespace
+
+// Pre-split Legendre operands of the tensor-core contractions (see TcTables).
+// Analysis tiles: group (m, p) rows in tiles of 128, K = latitudes padded to
+// 16 (kj), chunks of kTcChunkKB k-blocks; synthesis tiles: latitudes in
+// tiles of 128, K = the group's rows padded to 16.
+void build_tc_tables(int T, int J2, int J2p, const std::vector<double> &pbar, int npieces,
+                     std::vector<uint16_t> &a3, std::vector<TcTile3> &tiles3, std::vector<uint16_t> &a1,
+                     std::vector<TcTile1> &tiles1, int *kj_out) {
+    const int kj = (J2 + 15) / 16 * 16;
+    const int kjb = kj / 8;
+    *kj_out = kj;
+    tiles3.clear();
+    tiles1.clear();
+    long long n3 = 0, n1 = 0;
+    for (int m = 0; m <= T; ++m)
+        for (int p = 0; p < 2; ++p) {
+            const int R = (T + 2 - m - p + 1) / 2;      // n' = m + p + 2q <= T + 1
+            if (R <= 0) continue;
+            for (int q0 = 0; q0 < R; q0 += 128) {
+                TcTile3 t{m, p, q0, std::min(128, R - q0), 0, n3};
+                t.nrb = (t.nrows + 7) / 8;
+                tiles3.push_back(t);
+                n3 += static_cast<long long>(t.nrb) * kjb * 64;
+            }
+            const int KR = (R + 15) / 16 * 16;
+            for (int j0 = 0; j0 < J2; j0 += 128) {
+                TcTile1 t{m, p, j0, std::min(128, J2 - j0), 0, R, KR, n1};
+                t.njb = (t.nj + 7) / 8;
+                tiles1.push_back(t);
+                n1 += static_cast<long long>(t.njb) * (KR / 8) * 64;
+            }
+        }
+    a3.assign(static_cast<size_t>(n3) * npieces, 0);
+    a1.assign(static_cast<size_t>(n1) * npieces, 0);
+    uint16_t pc[4];
+    auto P = [&](int m, int n, int j) { return pbar[static_cast<size_t>(ext_offset(T, m) + n - m) * J2p + j]; };
+    for (const TcTile3 &t : tiles3) {
+        // chunk c: k blocks [8c, 8c + kbc); layout [rb][kb < kbc][8][8] per chunk
+        long long off = t.aoff;
+        for (int c0 = 0; c0 < kjb; c0 += kTcChunkKB) {
+            const int kbc = std::min(kTcChunkKB, kjb - c0);
+            for (int rb = 0; rb < t.nrb; ++rb)
+                for (int kb = 0; kb < kbc; ++kb)
+                    for (int r8 = 0; r8 < 8; ++r8)
+                        for (int k8 = 0; k8 < 8; ++k8) {
+                            const int q = t.q0 + rb * 8 + r8;
+                            const int j = (c0 + kb) * 8 + k8;
+                            double v = 0.0;
+                            if (q < t.q0 + t.nrows && j < J2) v = P(t.m, t.m + t.p + 2 * q, j);
+                            split_pieces(v, npieces, pc);
+                            const long long e = off + ((rb * kbc + kb) * 8 + r8) * 8 + k8;
+                            for (int i = 0; i < npieces; ++i) a3[static_cast<size_t>(i) * n3 + e] = pc[i];
+                        }
+            off += static_cast<long long>(t.nrb) * kbc * 64;
+        }
+    }
+    for (const TcTile1 &t : tiles1) {
+        const int krb = t.KR / 8;
+        long long off = t.aoff;
+        for (int c0 = 0; c0 < krb; c0 += kTcChunkKB) {
+            const int kbc = std::min(kTcChunkKB, krb - c0);
+            for (int jb = 0; jb < t.njb; ++jb)
+                for (int kb = 0; kb < kbc; ++kb)
+                    for (int r8 = 0; r8 < 8; ++r8)
+                        for (int k8 = 0; k8 < 8; ++k8) {
+                            const int j = t.j0 + jb * 8 + r8;
+                            const int q = (c0 + kb) * 8 + k8;
+                            double v = 0.0;
+                            if (j < t.j0 + t.nj && q < t.R) v = P(t.m, t.m + t.p + 2 * q, j);
+                            split_pieces(v, npieces, pc);
+                            const long long e = off + ((jb * kbc + kb) * 8 + r8) * 8 + k8;
+                            for (int i = 0; i < npieces; ++i) a1[static_cast<size_t>(i) * n1 + e] = pc[i];
+                        }
+            off += static_cast<long long>(t.njb) * kbc * 64;
+        }
     }
 }
 

@@ -116,14 +116,14 @@ __global__ void __launch_bounds__(64) k1_synthesis(const double2 *__restrict__ s
     }
 }
 
-// Shared memory of one ring block: 5 field arrays plus s scratch arrays of L
-// complex values.  Prefer the largest s that still lets two blocks share an
+// Shared memory of one ring block: 5 field arrays, s scratch arrays and the
+// twiddle table, L complex values each.  Prefer the largest s that still lets two blocks share an
 // SM; fall back to one block per SM for long rings.
 size_t ring_smem_bytes(int L, int elem_bytes, int *scratch_arrays) {
     const size_t per_sm = 227 * 1024;
     for (size_t cap : {per_sm / 2 - 1024, per_sm}) {
         for (int s = 5; s >= 1; --s) {
-            const size_t bytes = static_cast<size_t>(5 + s) * L * elem_bytes;
+            const size_t bytes = static_cast<size_t>(5 + s + 1) * L * elem_bytes;   // + twiddles
             if (bytes <= cap) {
                 if (scratch_arrays) *scratch_arrays = s;
                 return bytes;
@@ -150,31 +150,29 @@ __global__ void k2_ring(const V2<R> *__restrict__ f1, V2<R> *__restrict__ f2, Di
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V2<R> *X = reinterpret_cast<V2<R> *>(smem_raw);   // [5][L]
     V2<R> *S = X + 5 * plan.L;                          // [nscratch][L]
+    V2<R> *TW = S + nscratch * plan.L;                  // twiddles [L]
     const int j2 = blockIdx.x;
     const int b = blockIdx.y;
     const int T = d.T, L = plan.L;
     const V2<R> *in = f1 + (static_cast<size_t>(b) * d.J2 + j2) * (4 * 2 * (T + 1));
-
-    // Hermitian packing of north (real part) and south (imaginary part).
-    for (int i = threadIdx.x; i < 4 * L; i += blockDim.x) {
-        const int f = i / L, k = i - f * L;
-        V2<R> z = mk<R>(0, 0);
-        int m = -1;
-        bool conj = false;
-        if (k <= T) m = k;
-        else if (k >= L - T) { m = L - k; conj = true; }
-        if (m >= 0) {
-            V2<R> e = in[(f * 2 + 0) * (T + 1) + m];
-            V2<R> o = in[(f * 2 + 1) * (T + 1) + m];
-            if (m == 0) { e.y = 0; o.y = 0; }
-            V2<R> n = cadd<R>(e, o), s = csub<R>(e, o);
-            if (conj) { n.y = -n.y; s.y = -s.y; }
-            z = mk<R>(n.x - s.y, n.y + s.x);       // n + i s
-        }
-        X[f * L + k] = z;
+    for (int k = threadIdx.x; k < L; k += blockDim.x) TW[k] = tw[k];
+    // Hermitian packing of north (real part) and south (imaginary part):
+    // the band m <= T and its mirror L - m from one load, zeros in between.
+    for (int i = threadIdx.x; i < 4 * (L - 2 * T - 1); i += blockDim.x) {
+        const int f = i / (L - 2 * T - 1), k = T + 1 + (i - f * (L - 2 * T - 1));
+        X[f * L + k] = mk<R>(0, 0);
+    }
+    for (int i = threadIdx.x; i < 4 * (T + 1); i += blockDim.x) {
+        const int f = i / (T + 1), m = i - f * (T + 1);
+        V2<R> e = in[(f * 2 + 0) * (T + 1) + m];
+        V2<R> o = in[(f * 2 + 1) * (T + 1) + m];
+        if (m == 0) { e.y = 0; o.y = 0; }
+        const V2<R> n = cadd<R>(e, o), s = csub<R>(e, o);
+        X[f * L + m] = mk<R>(n.x - s.y, n.y + s.x);            // n + i s
+        if (m > 0) X[f * L + L - m] = mk<R>(n.x + s.y, -n.y + s.x);   // conj(n) + i conj(s)
     }
     __syncthreads();
-    fft_inplace<R>(X, S, nscratch, 4, plan, tw, true);
+    fft_inplace<R>(X, S, nscratch, 4, plan, TW, true);
 
     const double mun = mu[j2];
     const R cosl2 = R((1.0 - mun) * (1.0 + mun));
@@ -201,7 +199,7 @@ __global__ void k2_ring(const V2<R> *__restrict__ f1, V2<R> *__restrict__ f2, Di
         X[P_E * L + k] = mk<R>((uu.x * uu.x + vv.x * vv.x) * inv2c, (uu.y * uu.y + vv.y * vv.y) * inv2c);
     }
     __syncthreads();
-    fft_inplace<R>(X, S, nscratch, 5, plan, tw, false);
+    fft_inplace<R>(X, S, nscratch, 5, plan, TW, false);
 
     const double wj = w[j2];
     const R wt = R(wj / ((1.0 - mun) * (1.0 + mun)));
@@ -341,7 +339,7 @@ template <typename R>
 static cudaError_t launch_tendency_t(const Dims &d, const FftPlan &plan, int B, const double2 *states,
                                      long long sstride, double2 *tend, long long tstride, const DeviceTables &tb,
                                      const Workspace &ws, cudaStream_t s, int *launches, StageTimer *timer,
-                                     void *grid_store) {
+                                     void *grid_store, const TcTables *tc) {
     const R *pbar = static_cast<const R *>(tb.pbar);
     const V2<R> *tw = static_cast<const V2<R> *>(tb.tw);
     V2<R> *f1 = static_cast<V2<R> *>(ws.f1);
@@ -353,12 +351,33 @@ static cudaError_t launch_tendency_t(const Dims &d, const FftPlan &plan, int B, 
     const size_t sm2 = ring_smem_bytes(d.L, sizeof(V2<R>), &nscratch);
     if (sm2 == 0) return cudaErrorInvalidValue;
     if (timer) timer->mark(STAGE_SYNTH);
-    k1_synthesis<R><<<g1, kK1Threads, sm1, s>>>(states, sstride, d, pbar, tb.syn, f1);
+    if constexpr (sizeof(R) == sizeof(float)) {
+        if (tc) {
+            // the prepared coefficients go through f3 (free until the projection)
+            cudaError_t e = launch_tc_synthesis(*tc, d, B, states, sstride, tb.syn, tb.row_m, f3, f1, s);
+            if (e != cudaSuccess) return e;
+        } else {
+            k1_synthesis<R><<<g1, kK1Threads, sm1, s>>>(states, sstride, d, pbar, tb.syn, f1);
+        }
+    } else {
+        k1_synthesis<R><<<g1, kK1Threads, sm1, s>>>(states, sstride, d, pbar, tb.syn, f1);
+    }
     if (timer) timer->mark(STAGE_RING);
     k2_ring<R><<<dim3(d.J2, B), kK2Threads, sm2, s>>>(f1, f2, d, plan, tw, tb.mu, tb.w, nscratch,
                                                      static_cast<V2<R> *>(grid_store));
     if (timer) timer->mark(STAGE_ANALYSIS);
-    k3_project<R><<<dim3((d.next + kK3Threads - 1) / kK3Threads, B), kK3Threads, 0, s>>>(f2, d, pbar, tb.row_m, f3);
+    if constexpr (sizeof(R) == sizeof(float)) {
+        if (tc) {
+            cudaError_t e = launch_tc_projection(*tc, d, B, f2, f3, s);
+            if (e != cudaSuccess) return e;
+        } else {
+            k3_project<R><<<dim3((d.next + kK3Threads - 1) / kK3Threads, B), kK3Threads, 0, s>>>(f2, d, pbar,
+                                                                                                  tb.row_m, f3);
+        }
+    } else {
+        k3_project<R><<<dim3((d.next + kK3Threads - 1) / kK3Threads, B), kK3Threads, 0, s>>>(f2, d, pbar, tb.row_m,
+                                                                                              f3);
+    }
     if (timer) timer->mark(STAGE_EPILOGUE);
     k3_epilogue<R><<<dim3((d.ncoef + 127) / 128, B), 128, 0, s>>>(f3, d, tb.eps, tb.lam, tb.coef_m, tend, tstride);
     if (launches) *launches += 4;
@@ -377,12 +396,12 @@ cudaError_t configure_transform_kernels(const Dims &d, const FftPlan &plan, bool
 cudaError_t launch_tendency(const Dims &d, const FftPlan &plan, bool fp32, int B, const double2 *states,
                             long long sstride, double2 *tend, long long tstride, const DeviceTables &tb,
                             const Workspace &ws, cudaStream_t s, int *launches, StageTimer *timer,
-                            void *grid_store) {
+                            void *grid_store, const TcTables *tc) {
     if (fp32)
         return launch_tendency_t<float>(d, plan, B, states, sstride, tend, tstride, tb, ws, s, launches, timer,
-                                        grid_store);
+                                        grid_store, tc);
     return launch_tendency_t<double>(d, plan, B, states, sstride, tend, tstride, tb, ws, s, launches, timer,
-                                     grid_store);
+                                     grid_store, nullptr);
 }
 
 // ---------------------------------------------------------------------------

@@ -177,6 +177,10 @@ class Solver:
         _lib.check(self.lib.sdc_profile_step(self.h, _ptr(state), ms, nl), "sdc_profile_step")
         return {k: (ms[i], nl[i]) for i, k in enumerate(self.STAGES)}
 
+    def sync(self):
+        """Wait for the stream; raises if a kernel reported an expired wait."""
+        _lib.check(self.lib.sdc_sync(self.h), "sdc_sync")
+
     def launches_per_step(self) -> int:
         n = ctypes.c_int()
         _lib.check(self.lib.sdc_launches_per_step(self.h, ctypes.byref(n)), "sdc_launches_per_step")
