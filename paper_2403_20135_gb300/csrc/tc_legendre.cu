@@ -32,7 +32,6 @@ namespace {
 constexpr int kTcThreads = 128;
 constexpr int kTcMaxPieces = 3;
 constexpr int kTileRows = 128;                       // M of every MMA
-constexpr int kChunkElems = kTcChunkKB * 8;          // K elements per chunk
 constexpr uint32_t kWaitLimit = 1u << 22;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -94,12 +93,15 @@ __device__ __forceinline__ void expect_tx(uint64_t *mbar, uint32_t bytes) {
 }
 
 // x = h_0 + h_1 (+ h_2): each piece the BF16 rounding of the remaining FP32
-// residual (the residual of a BF16 rounding is exact in FP32).
-__device__ __forceinline__ void split_store(float x, int np, __nv_bfloat16 *const *dst, int idx) {
+// residual (the residual of a BF16 rounding is exact in FP32).  Piece i of
+// element idx lives at base[i * stride + idx].
+template <int NP>
+__device__ __forceinline__ void split_store(float x, __nv_bfloat16 *base, int stride, int idx) {
     float r = x;
-    for (int i = 0; i < np; ++i) {
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
         const __nv_bfloat16 h = __float2bfloat16_rn(r);
-        dst[i][idx] = h;
+        base[i * stride + idx] = h;
         r -= __bfloat162float(h);
     }
 }
@@ -130,8 +132,6 @@ struct TcSmem {
     uint64_t mbar_mma;
     uint32_t tmem;
     int abort;
-    __nv_bfloat16 *a[kTcMaxPieces];
-    __nv_bfloat16 *b[kTcMaxPieces];
 };
 constexpr int kAElems = 16 * kTcChunkKB * 64;
 constexpr int kBElems = 10 * kTcChunkKB * 64;
@@ -141,28 +141,45 @@ size_t tc_smem_bytes(int np) {
     return kCtrlBytes + static_cast<size_t>(np) * (kAElems + kBElems) * sizeof(__nv_bfloat16);
 }
 
-__device__ __forceinline__ TcSmem &tc_smem_setup(unsigned char *raw, int np) {
-    TcSmem &sm = *reinterpret_cast<TcSmem *>(raw);
-    __nv_bfloat16 *base = reinterpret_cast<__nv_bfloat16 *>(raw + kCtrlBytes);
+// piece i of the A chunk at a_base + i * kAElems, of the B chunk at b_base + i * kBElems
+template <int NP>
+__device__ __forceinline__ __nv_bfloat16 *a_base(unsigned char *raw) {
+    return reinterpret_cast<__nv_bfloat16 *>(raw + kCtrlBytes);
+}
+template <int NP>
+__device__ __forceinline__ __nv_bfloat16 *b_base(unsigned char *raw) {
+    return reinterpret_cast<__nv_bfloat16 *>(raw + kCtrlBytes) + NP * kAElems;
+}
+
+// one thread waits (bounded) on an mbarrier phase while the block sleeps at
+// the barrier; returns false everywhere if the wait expired
+__device__ __forceinline__ bool block_wait(TcSmem &sm, uint64_t *mbar, uint32_t phase, int *err, int code) {
     if (threadIdx.x == 0) {
-        for (int i = 0; i < kTcMaxPieces; ++i) {
-            sm.a[i] = base + i * kAElems;
-            sm.b[i] = base + np * kAElems + i * kBElems;
+        if (!mbar_wait(mbar, phase)) {
+            sm.abort = 1;
+            atomicExch(err, code);
+            mbar_wait(mbar, phase);                 // work may still be landing: wait again (bounded)
         }
     }
-    return sm;
+    __syncthreads();
+    return sm.abort == 0;
 }
 
 // The MMAs of one chunk: kbc k-blocks, K step 16 (two core matrices).
-__device__ __forceinline__ void issue_chunk(TcSmem &sm, uint32_t tmem, int np, int kbc, int N, bool first) {
+template <int NP>
+__device__ __forceinline__ void issue_chunk(const __nv_bfloat16 *abase, const __nv_bfloat16 *bbase, uint32_t tmem,
+                                            int kbc, int N, bool first) {
     const uint32_t idesc = mma_idesc(kTileRows, N);
     const uint32_t sbo = static_cast<uint32_t>(kbc) * 128;
+    const uint32_t a0 = smem_u32(abase), b0 = smem_u32(bbase);
     for (int ks = 0; ks < kbc / 2; ++ks) {
         int prod = 0;
-        for (int i = 0; i < np; ++i)
-            for (int j = 0; i + j < np; ++j, ++prod) {
-                const uint64_t ad = smem_desc(smem_u32(sm.a[i]) + ks * 256, 128, sbo);
-                const uint64_t bd = smem_desc(smem_u32(sm.b[j]) + ks * 256, 128, sbo);
+#pragma unroll
+        for (int i = 0; i < NP; ++i)
+#pragma unroll
+            for (int j = 0; i + j < NP; ++j, ++prod) {
+                const uint64_t ad = smem_desc(a0 + i * kAElems * 2 + ks * 256, 128, sbo);
+                const uint64_t bd = smem_desc(b0 + j * kBElems * 2 + ks * 256, 128, sbo);
                 mma_bf16(tmem, ad, bd, idesc, (first && ks == 0 && prod == 0) ? 0u : 1u);
             }
     }
@@ -197,11 +214,13 @@ __device__ __forceinline__ void tc_epilogue_free(TcSmem &sm, uint32_t ncols) {
 // states.  Columns col = b*10 + g*2 + (re, im) of W = F2[b][m][g][p][j].
 // Output Y[b][e][g] (float2), e = ext_offset(m) + p + 2q.
 // ---------------------------------------------------------------------------
+template <int NP>
 __global__ void __launch_bounds__(kTcThreads) k3_tc(TcTables tc, Dims d, int B, const float2 *__restrict__ f2,
                                                     float2 *__restrict__ y) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    const int np = tc.npieces;
-    TcSmem &sm = tc_smem_setup(smem_raw, np);
+    TcSmem &sm = *reinterpret_cast<TcSmem *>(smem_raw);
+    __nv_bfloat16 *sa = a_base<NP>(smem_raw);
+    __nv_bfloat16 *sb = b_base<NP>(smem_raw);
     const TcTile3 t = tc.tiles3[blockIdx.x];
     const int ncols = 10 * B;
     const int N = (ncols + 15) / 16 * 16;
@@ -210,23 +229,25 @@ __global__ void __launch_bounds__(kTcThreads) k3_tc(TcTables tc, Dims d, int B, 
     const int T = d.T, J2 = d.J2;
     const int kjb = tc.kj / 8;
     tc_prologue(sm, tcols);
-    __nv_bfloat16 *bptr[kTcMaxPieces] = {sm.b[0], sm.b[1], sm.b[2]};   // set before the prologue barrier
 
     int chunk = 0;
     for (int c0 = 0; c0 < kjb; c0 += kTcChunkKB, ++chunk) {
         const int kbc = min(kTcChunkKB, kjb - c0);
+        const int kw = kbc * 8;                 // latitudes in this chunk
         const uint32_t abytes = static_cast<uint32_t>(t.nrb) * kbc * 128;
         if (threadIdx.x == 0) {
-            expect_tx(&sm.mbar_ld, abytes * np);
-            for (int i = 0; i < np; ++i)
-                bulk_copy(sm.a[i], tc.a3 + i * tc.elems3 + t.aoff + static_cast<long long>(t.nrb) * 64 * c0, abytes,
-                          &sm.mbar_ld);
+            expect_tx(&sm.mbar_ld, abytes * NP);
+#pragma unroll
+            for (int i = 0; i < NP; ++i)
+                bulk_copy(sa + i * kAElems, tc.a3 + i * tc.elems3 + t.aoff + static_cast<long long>(t.nrb) * 64 * c0,
+                          abytes, &sm.mbar_ld);
         }
         // zero the A row blocks beyond the tile's rows (not touched by the copy)
-        for (int i = 0; i < np; ++i) zero_range(sm.a[i], t.nrb * kbc * 64, 16 * kbc * 64);
+#pragma unroll
+        for (int i = 0; i < NP; ++i) zero_range(sa + i * kAElems, t.nrb * kbc * 64, 16 * kbc * 64);
         // B = W^T chunk: [col block][kb][8 cols][8 latitudes]; loads issued in
         // batches of 8 independent requests per thread, then split and stored
-        const int items = (N / 2) * kbc * 8;
+        const int items = (N / 2) * kw;
         for (int base0 = 0; base0 < items; base0 += 8 * kTcThreads) {
             float2 wv[8];
 #pragma unroll
@@ -234,8 +255,8 @@ __global__ void __launch_bounds__(kTcThreads) k3_tc(TcTables tc, Dims d, int B, 
                 const int k = base0 + u * kTcThreads + threadIdx.x;
                 wv[u] = make_float2(0.f, 0.f);
                 if (k < items) {
-                    const int cp = k / (kbc * 8), jj = k - cp * (kbc * 8);
-                    const int j = (c0 * 8) + jj;
+                    const int cp = k / kw, jj = k - cp * kw;
+                    const int j = c0 * 8 + jj;
                     if (2 * cp < ncols && j < J2) {
                         const int b = cp / 5, g = cp - b * 5;
                         wv[u] = f2[((static_cast<size_t>(b) * (T + 1) + t.m) * 5 + g) * 2 * J2 + t.p * J2 + j];
@@ -246,38 +267,24 @@ __global__ void __launch_bounds__(kTcThreads) k3_tc(TcTables tc, Dims d, int B, 
             for (int u = 0; u < 8; ++u) {
                 const int k = base0 + u * kTcThreads + threadIdx.x;
                 if (k < items) {
-                    const int cp = k / (kbc * 8), jj = k - cp * (kbc * 8);
+                    const int cp = k / kw, jj = k - cp * kw;
                     const int c = 2 * cp;
-                    const int base = ((c >> 3) * kbc + (jj >> 3)) * 64 + (c & 7) * 8 + (jj & 7);
-                    split_store(wv[u].x, np, bptr, base);
-                    split_store(wv[u].y, np, bptr, base + 8);   // column c + 1 sits one core row below
+                    const int e = ((c >> 3) * kbc + (jj >> 3)) * 64 + (c & 7) * 8 + (jj & 7);
+                    split_store<NP>(wv[u].x, sb, kBElems, e);
+                    split_store<NP>(wv[u].y, sb, kBElems, e + 8);   // column c + 1: next core row
                 }
             }
         }
         asm volatile("fence.proxy.async.shared::cta;");
         __syncthreads();
-        const bool ok_ld = mbar_wait(&sm.mbar_ld, chunk & 1);
-        if (!ok_ld && threadIdx.x == 0) {
-            sm.abort = 1;
-            atomicExch(tc.err, 1);
-            mbar_wait(&sm.mbar_ld, chunk & 1);          // the copy may still be landing
-        }
+        if (!block_wait(sm, &sm.mbar_ld, chunk & 1, tc.err, 1)) break;
         asm volatile("tcgen05.fence::after_thread_sync;");
-        __syncthreads();
-        if (sm.abort) break;
         if (threadIdx.x == 0) {
-            issue_chunk(sm, sm.tmem, np, kbc, N, chunk == 0);
+            issue_chunk<NP>(sa, sb, sm.tmem, kbc, N, chunk == 0);
             mma_commit(&sm.mbar_mma);
         }
-        const bool ok = mbar_wait(&sm.mbar_mma, chunk & 1);
-        if (!ok && threadIdx.x == 0) {
-            sm.abort = 1;
-            atomicExch(tc.err, 2);
-            mbar_wait(&sm.mbar_mma, chunk & 1);         // MMAs may still be writing TMEM
-        }
+        if (!block_wait(sm, &sm.mbar_mma, chunk & 1, tc.err, 2)) break;
         asm volatile("tcgen05.fence::after_thread_sync;");
-        __syncthreads();
-        if (sm.abort) break;
     }
 
     if (!sm.abort) {
@@ -306,14 +313,16 @@ __global__ void __launch_bounds__(kTcThreads) k3_tc(TcTables tc, Dims d, int B, 
 // ---------------------------------------------------------------------------
 // Synthesis: one block per tile (m, p, latitudes j0..j0+nj), all B states.
 // Columns col = b*8 + f*2 + (re, im) of the prepared coefficients
-// C[q][col] (fields zeta, Phi', U, V as in the FP64/FP32 synthesis).
-// Output F1[b][j][f][p][m] (float2).
+// C[q][col] (fields zeta, Phi', U, V as in the FP64/FP32 synthesis), read
+// from cbuf[b][e][4] (FP32).  Output F1[b][j][f][p][m] (float2).
 // ---------------------------------------------------------------------------
+template <int NP>
 __global__ void __launch_bounds__(kTcThreads) k1_tc(TcTables tc, Dims d, int B, const float2 *__restrict__ cbuf,
                                                     float2 *__restrict__ f1) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    const int np = tc.npieces;
-    TcSmem &sm = tc_smem_setup(smem_raw, np);
+    TcSmem &sm = *reinterpret_cast<TcSmem *>(smem_raw);
+    __nv_bfloat16 *sa = a_base<NP>(smem_raw);
+    __nv_bfloat16 *sb = b_base<NP>(smem_raw);
     const TcTile1 t = tc.tiles1[blockIdx.x];
     const int ncols = 8 * B;
     const int N = (ncols + 15) / 16 * 16;
@@ -323,22 +332,24 @@ __global__ void __launch_bounds__(kTcThreads) k1_tc(TcTables tc, Dims d, int B, 
     const int m = t.m;
     const int krb = t.KR / 8;
     tc_prologue(sm, tcols);
-    __nv_bfloat16 *bptr[kTcMaxPieces] = {sm.b[0], sm.b[1], sm.b[2]};   // set before the prologue barrier
 
     int chunk = 0;
     for (int c0 = 0; c0 < krb; c0 += kTcChunkKB, ++chunk) {
         const int kbc = min(kTcChunkKB, krb - c0);
+        const int kw = kbc * 8;                 // rows q in this chunk
         const uint32_t abytes = static_cast<uint32_t>(t.njb) * kbc * 128;
         if (threadIdx.x == 0) {
-            expect_tx(&sm.mbar_ld, abytes * np);
-            for (int i = 0; i < np; ++i)
-                bulk_copy(sm.a[i], tc.a1 + i * tc.elems1 + t.aoff + static_cast<long long>(t.njb) * 64 * c0, abytes,
-                          &sm.mbar_ld);
+            expect_tx(&sm.mbar_ld, abytes * NP);
+#pragma unroll
+            for (int i = 0; i < NP; ++i)
+                bulk_copy(sa + i * kAElems, tc.a1 + i * tc.elems1 + t.aoff + static_cast<long long>(t.njb) * 64 * c0,
+                          abytes, &sm.mbar_ld);
         }
-        for (int i = 0; i < np; ++i) zero_range(sm.a[i], t.njb * kbc * 64, 16 * kbc * 64);
+#pragma unroll
+        for (int i = 0; i < NP; ++i) zero_range(sa + i * kAElems, t.njb * kbc * 64, 16 * kbc * 64);
         // B = C^T chunk: [col block][kb][8 cols][8 rows q]; one column block
         // per state holds the 4 complex prepared coefficients of row q
-        const int items = (N / 8) * kbc * 8;
+        const int items = nbc * kw;
         for (int base0 = 0; base0 < items; base0 += 2 * kTcThreads) {
             float4 cv[2][2];
 #pragma unroll
@@ -346,7 +357,7 @@ __global__ void __launch_bounds__(kTcThreads) k1_tc(TcTables tc, Dims d, int B, 
                 const int k = base0 + u * kTcThreads + threadIdx.x;
                 cv[u][0] = cv[u][1] = make_float4(0.f, 0.f, 0.f, 0.f);
                 if (k < items) {
-                    const int bb = k / (kbc * 8), qq = k - bb * (kbc * 8);
+                    const int bb = k / kw, qq = k - bb * kw;
                     const int q = c0 * 8 + qq;
                     if (bb < B && q < t.R) {
                         const float4 *src = reinterpret_cast<const float4 *>(
@@ -360,39 +371,29 @@ __global__ void __launch_bounds__(kTcThreads) k1_tc(TcTables tc, Dims d, int B, 
             for (int u = 0; u < 2; ++u) {
                 const int k = base0 + u * kTcThreads + threadIdx.x;
                 if (k < items) {
-                    const int bb = k / (kbc * 8), qq = k - bb * (kbc * 8);
-                    const int base = (bb * kbc + (qq >> 3)) * 64 + (qq & 7);
-                    const float v[8] = {cv[u][0].x, cv[u][0].y, cv[u][0].z, cv[u][0].w,
-                                        cv[u][1].x, cv[u][1].y, cv[u][1].z, cv[u][1].w};
-#pragma unroll
-                    for (int c = 0; c < 8; ++c) split_store(v[c], np, bptr, base + c * 8);
+                    const int bb = k / kw, qq = k - bb * kw;
+                    const int e = (bb * kbc + (qq >> 3)) * 64 + (qq & 7);
+                    split_store<NP>(cv[u][0].x, sb, kBElems, e + 0 * 8);
+                    split_store<NP>(cv[u][0].y, sb, kBElems, e + 1 * 8);
+                    split_store<NP>(cv[u][0].z, sb, kBElems, e + 2 * 8);
+                    split_store<NP>(cv[u][0].w, sb, kBElems, e + 3 * 8);
+                    split_store<NP>(cv[u][1].x, sb, kBElems, e + 4 * 8);
+                    split_store<NP>(cv[u][1].y, sb, kBElems, e + 5 * 8);
+                    split_store<NP>(cv[u][1].z, sb, kBElems, e + 6 * 8);
+                    split_store<NP>(cv[u][1].w, sb, kBElems, e + 7 * 8);
                 }
             }
         }
         asm volatile("fence.proxy.async.shared::cta;");
         __syncthreads();
-        const bool ok_ld = mbar_wait(&sm.mbar_ld, chunk & 1);
-        if (!ok_ld && threadIdx.x == 0) {
-            sm.abort = 1;
-            atomicExch(tc.err, 3);
-            mbar_wait(&sm.mbar_ld, chunk & 1);
-        }
+        if (!block_wait(sm, &sm.mbar_ld, chunk & 1, tc.err, 3)) break;
         asm volatile("tcgen05.fence::after_thread_sync;");
-        __syncthreads();
-        if (sm.abort) break;
         if (threadIdx.x == 0) {
-            issue_chunk(sm, sm.tmem, np, kbc, N, chunk == 0);
+            issue_chunk<NP>(sa, sb, sm.tmem, kbc, N, chunk == 0);
             mma_commit(&sm.mbar_mma);
         }
-        const bool ok = mbar_wait(&sm.mbar_mma, chunk & 1);
-        if (!ok && threadIdx.x == 0) {
-            sm.abort = 1;
-            atomicExch(tc.err, 4);
-            mbar_wait(&sm.mbar_mma, chunk & 1);
-        }
+        if (!block_wait(sm, &sm.mbar_mma, chunk & 1, tc.err, 4)) break;
         asm volatile("tcgen05.fence::after_thread_sync;");
-        __syncthreads();
-        if (sm.abort) break;
     }
 
     if (!sm.abort) {
@@ -441,23 +442,28 @@ __global__ void k1_prep_f32(const double2 *__restrict__ states, long long sstrid
 }  // namespace
 
 cudaError_t configure_tc_kernels() {
-    cudaError_t e = cudaFuncSetAttribute(k3_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem_bytes(3));
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k1_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem_bytes(3));
+    const int s2 = (int)tc_smem_bytes(2), s3 = (int)tc_smem_bytes(3);
+    cudaError_t e = cudaFuncSetAttribute(k3_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, s2);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k3_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, s3);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k1_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, s2);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k1_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, s3);
+    return e;
 }
 
 cudaError_t launch_tc_synthesis(const TcTables &tc, const Dims &d, int B, const double2 *states, long long sstride,
                                 const double *syn, const int *row_m, float2 *cbuf, float2 *f1, cudaStream_t s) {
     if (B < 1 || B > kMaxNodes) return cudaErrorInvalidValue;
     k1_prep_f32<<<dim3((d.next + 127) / 128, B), 128, 0, s>>>(states, sstride, d, syn, row_m, cbuf);
-    k1_tc<<<tc.ntiles1, kTcThreads, tc_smem_bytes(tc.npieces), s>>>(tc, d, B, cbuf, f1);
+    if (tc.npieces == 2) k1_tc<2><<<tc.ntiles1, kTcThreads, tc_smem_bytes(2), s>>>(tc, d, B, cbuf, f1);
+    else k1_tc<3><<<tc.ntiles1, kTcThreads, tc_smem_bytes(3), s>>>(tc, d, B, cbuf, f1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_tc_projection(const TcTables &tc, const Dims &d, int B, const float2 *f2, float2 *y,
                                  cudaStream_t s) {
     if (B < 1 || B > kMaxNodes) return cudaErrorInvalidValue;
-    k3_tc<<<tc.ntiles3, kTcThreads, tc_smem_bytes(tc.npieces), s>>>(tc, d, B, f2, y);
+    if (tc.npieces == 2) k3_tc<2><<<tc.ntiles3, kTcThreads, tc_smem_bytes(2), s>>>(tc, d, B, f2, y);
+    else k3_tc<3><<<tc.ntiles3, kTcThreads, tc_smem_bytes(3), s>>>(tc, d, B, f2, y);
     return cudaGetLastError();
 }
 
