@@ -78,7 +78,8 @@ struct sdc_ctx {
 
     // tensor-core Legendre tables (split-BF16 modes)
     TcTables tc{};
-    uint16_t *tc_a3 = nullptr, *tc_a1 = nullptr;
+    uint16_t *tc_a3 = nullptr, *tc_a1 = nullptr, *tc_wb = nullptr, *tc_cb = nullptr;
+    long long *tc_cboff = nullptr;
     TcTile3 *tc_t3 = nullptr;
     TcTile1 *tc_t1 = nullptr;
     int *tc_err = nullptr;
@@ -103,7 +104,8 @@ void free_ctx(sdc_ctx *c) {
     void *ptrs[] = {c->pbar, c->pbar32, c->eps, c->lam, c->mu2, c->w2, c->syn, c->row_m, c->coef_m, c->tw,
                     c->tw32, c->un, c->U, c->E, c->E0, c->f1, c->f2, c->f3, c->resid_part, c->resid,
                     c->gstore, c->ub, c->eb, c->ubn, c->ubnext, c->eb0, c->snaps, c->phigrid, c->rgrid,
-                    c->loss_part, c->loss_dev, c->tc_a3, c->tc_a1, c->tc_t3, c->tc_t1, c->tc_err, c->den};
+                    c->loss_part, c->loss_dev, c->tc_a3, c->tc_a1, c->tc_t3, c->tc_t1, c->tc_err, c->den,
+                    c->tc_wb, c->tc_cb, c->tc_cboff};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->cap) cudaStreamDestroy(c->cap);
@@ -573,6 +575,26 @@ int sdc_create(sdc_ctx **out, int T, int J, int L, int M, int K, double dt, cons
         c->tc.ntiles1 = static_cast<int>(t1.size());
         c->tc.npieces = np;
         c->tc.kj = kj;
+        // dynamic operands, split per launch; zero once so that K padding
+        // and never-written columns stay zero
+        std::vector<long long> cboff(2 * (T + 1));
+        long long ncb = 0;
+        for (int m = 0; m <= T; ++m)
+            for (int p = 0; p < 2; ++p) {
+                cboff[2 * m + p] = ncb;
+                ncb += static_cast<long long>(kNbc1) * (tc_group_krows(T, m, p) / 8) * 64;
+            }
+        const long long nwb = 2LL * (T + 1) * kNbc3 * (kj / 8) * 64;
+        SDC_TRY(cudaMalloc(&c->tc_wb, static_cast<size_t>(nwb) * np * sizeof(uint16_t)));
+        SDC_TRY(cudaMemset(c->tc_wb, 0, static_cast<size_t>(nwb) * np * sizeof(uint16_t)));
+        SDC_TRY(cudaMalloc(&c->tc_cb, static_cast<size_t>(ncb) * np * sizeof(uint16_t)));
+        SDC_TRY(cudaMemset(c->tc_cb, 0, static_cast<size_t>(ncb) * np * sizeof(uint16_t)));
+        SDC_TRY(upload(&c->tc_cboff, cboff.data(), cboff.size()));
+        c->tc.wb = c->tc_wb;
+        c->tc.cb = c->tc_cb;
+        c->tc.wb_elems = nwb;
+        c->tc.cb_elems = ncb;
+        c->tc.cb_off = c->tc_cboff;
         c->tc.err = c->tc_err;
     }
     SDC_TRY(upload(&c->eps, eps.data(), eps.size()));

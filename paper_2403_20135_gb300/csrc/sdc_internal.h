@@ -141,10 +141,21 @@ struct TcTile1 {                  // synthesis: latitudes j0..j0+nj of group (m,
     int m, p, j0, nj, njb, R, KR;
     long long aoff;
 };
+// The dynamic operands are split by their own kernels into the same layout,
+// group by group: the projection's W^T as [group][chunk][col block < kNbc3]
+// [k block][8][8], the synthesis coefficients as [group][chunk][col block <
+// kNbc1][k block][8][8].  Col blocks come first inside a chunk, so the
+// blocks of a batch of B states are one contiguous prefix.
+constexpr int kNbc3 = (10 * kMaxNodes + 7) / 8;   // projection columns b*10 + g*2 + (re, im)
+constexpr int kNbc1 = kMaxNodes;                  // synthesis columns b*8 + f*2 + (re, im)
 struct TcTables {
     const uint16_t *a3;           // analysis pieces [npieces][elems3]
     const uint16_t *a1;           // synthesis pieces [npieces][elems1]
     long long elems3, elems1;
+    uint16_t *wb;                 // projection B operand pieces [npieces][wb_elems]
+    uint16_t *cb;                 // synthesis B operand pieces [npieces][cb_elems]
+    long long wb_elems, cb_elems;
+    const long long *cb_off;      // [2 (T+1)] start of group (m, p) = 2 m + p in each cb piece
     const TcTile3 *tiles3;
     const TcTile1 *tiles1;
     int ntiles3, ntiles1;
@@ -155,6 +166,9 @@ struct TcTables {
 void build_tc_tables(int T, int J2, int J2p, const std::vector<double> &pbar, int npieces,
                      std::vector<uint16_t> &a3, std::vector<TcTile3> &tiles3, std::vector<uint16_t> &a1,
                      std::vector<TcTile1> &tiles1, int *kj_out);
+// rows of group (m, p) and their count padded to a multiple of 16
+__host__ __device__ inline int tc_group_rows(int T, int m, int p) { return (T + 3 - m - p) / 2; }
+__host__ __device__ inline int tc_group_krows(int T, int m, int p) { return (tc_group_rows(T, m, p) + 15) / 16 * 16; }
 
 // ---- host-side precompute (tables.cpp) ----------------------------------
 void gauss_legendre(int J, std::vector<double> &mu, std::vector<double> &w);
@@ -175,10 +189,11 @@ cudaError_t launch_tendency(const Dims &d, const FftPlan &plan, bool fp32, int B
                             long long sstride, double2 *tend, long long tstride, const DeviceTables &tb,
                             const Workspace &ws, cudaStream_t s, int *launches, StageTimer *timer = nullptr,
                             void *grid_store = nullptr, const TcTables *tc = nullptr);
+// Each adds its two launches (operand split + MMA kernel) to *launches.
 cudaError_t launch_tc_synthesis(const TcTables &tc, const Dims &d, int B, const double2 *states, long long sstride,
-                                const double *syn, const int *row_m, float2 *cbuf, float2 *f1, cudaStream_t s);
+                                const double *syn, const int *row_m, float2 *f1, cudaStream_t s, int *launches);
 cudaError_t launch_tc_projection(const TcTables &tc, const Dims &d, int B, const float2 *f2, float2 *y,
-                                 cudaStream_t s);
+                                 cudaStream_t s, int *launches);
 cudaError_t configure_tc_kernels();
 cudaError_t launch_sweep(const SweepParams &p, int M, cudaStream_t s, int *launches,
                          StageTimer *timer = nullptr);

@@ -93,26 +93,26 @@ __device__ __forceinline__ void expect_tx(uint64_t *mbar, uint32_t bytes) {
 }
 
 // x = h_0 + h_1 (+ h_2): each piece the BF16 rounding of the remaining FP32
-// residual (the residual of a BF16 rounding is exact in FP32).  Piece i of
-// element idx lives at base[i * stride + idx].
+// residual (the residual of a BF16 rounding is exact in FP32).  split8 does
+// this for 8 values and packs piece i of all 8 into one 16-byte word.
 template <int NP>
-__device__ __forceinline__ void split_store(float x, __nv_bfloat16 *base, int stride, int idx) {
-    float r = x;
+__device__ __forceinline__ void split8(const float (&x)[8], uint4 (&out)[NP]) {
+    float r[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) r[k] = x[k];
 #pragma unroll
     for (int i = 0; i < NP; ++i) {
-        const __nv_bfloat16 h = __float2bfloat16_rn(r);
-        base[i * stride + idx] = h;
-        r -= __bfloat162float(h);
+        uint32_t w[4];
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            const __nv_bfloat16 lo = __float2bfloat16_rn(r[2 * h]), hi = __float2bfloat16_rn(r[2 * h + 1]);
+            r[2 * h] -= __bfloat162float(lo);
+            r[2 * h + 1] -= __bfloat162float(hi);
+            w[h] = static_cast<uint32_t>(__bfloat16_as_ushort(lo)) |
+                   (static_cast<uint32_t>(__bfloat16_as_ushort(hi)) << 16);
+        }
+        out[i] = make_uint4(w[0], w[1], w[2], w[3]);
     }
-}
-
-// zero [from, to) elements of a BF16 array with 16-byte stores where aligned
-__device__ __forceinline__ void zero_range(__nv_bfloat16 *a, int from, int to) {
-    const int vfrom = (from + 7) & ~7, vto = to & ~7;
-    for (int k = from + threadIdx.x; k < min(vfrom, to); k += blockDim.x) a[k] = __float2bfloat16(0.0f);
-    uint4 *v = reinterpret_cast<uint4 *>(a);
-    for (int k = vfrom / 8 + threadIdx.x; k < vto / 8; k += blockDim.x) v[k] = make_uint4(0, 0, 0, 0);
-    for (int k = max(vto, vfrom) + threadIdx.x; k < to; k += blockDim.x) a[k] = __float2bfloat16(0.0f);
 }
 
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float *v) {
@@ -126,7 +126,10 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float *v) {
 }
 
 // Shared memory of one block: a control block, then npieces A chunks
-// [16 rb][8 kb][64] and npieces B chunks [<= 10 rb][8 kb][64] (BF16).
+// [16 rb][kbc][64] and npieces B chunks [nbc][kbc][64] (BF16).  Only the
+// async proxy writes the operand areas (bulk copies), so rows of A beyond a
+// partial tile hold stale finite data: they only feed accumulator rows the
+// epilogue never reads.  K padding is zero in both operands' global copies.
 struct TcSmem {
     uint64_t mbar_ld;
     uint64_t mbar_mma;
@@ -134,41 +137,18 @@ struct TcSmem {
     int abort;
 };
 constexpr int kAElems = 16 * kTcChunkKB * 64;
-constexpr int kBElems = 10 * kTcChunkKB * 64;
 constexpr size_t kCtrlBytes = 128;
 
-size_t tc_smem_bytes(int np) {
-    return kCtrlBytes + static_cast<size_t>(np) * (kAElems + kBElems) * sizeof(__nv_bfloat16);
-}
+__host__ __device__ inline int b_elems(int nbc) { return nbc * kTcChunkKB * 64; }
 
-// piece i of the A chunk at a_base + i * kAElems, of the B chunk at b_base + i * kBElems
-template <int NP>
-__device__ __forceinline__ __nv_bfloat16 *a_base(unsigned char *raw) {
-    return reinterpret_cast<__nv_bfloat16 *>(raw + kCtrlBytes);
-}
-template <int NP>
-__device__ __forceinline__ __nv_bfloat16 *b_base(unsigned char *raw) {
-    return reinterpret_cast<__nv_bfloat16 *>(raw + kCtrlBytes) + NP * kAElems;
-}
-
-// one thread waits (bounded) on an mbarrier phase while the block sleeps at
-// the barrier; returns false everywhere if the wait expired
-__device__ __forceinline__ bool block_wait(TcSmem &sm, uint64_t *mbar, uint32_t phase, int *err, int code) {
-    if (threadIdx.x == 0) {
-        if (!mbar_wait(mbar, phase)) {
-            sm.abort = 1;
-            atomicExch(err, code);
-            mbar_wait(mbar, phase);                 // work may still be landing: wait again (bounded)
-        }
-    }
-    __syncthreads();
-    return sm.abort == 0;
+size_t tc_smem_bytes(int np, int nbc) {
+    return kCtrlBytes + static_cast<size_t>(np) * (kAElems + b_elems(nbc)) * sizeof(__nv_bfloat16);
 }
 
 // The MMAs of one chunk: kbc k-blocks, K step 16 (two core matrices).
 template <int NP>
-__device__ __forceinline__ void issue_chunk(const __nv_bfloat16 *abase, const __nv_bfloat16 *bbase, uint32_t tmem,
-                                            int kbc, int N, bool first) {
+__device__ __forceinline__ void issue_chunk(const __nv_bfloat16 *abase, const __nv_bfloat16 *bbase, int belems,
+                                            uint32_t tmem, int kbc, int N, bool first) {
     const uint32_t idesc = mma_idesc(kTileRows, N);
     const uint32_t sbo = static_cast<uint32_t>(kbc) * 128;
     const uint32_t a0 = smem_u32(abase), b0 = smem_u32(bbase);
@@ -179,10 +159,51 @@ __device__ __forceinline__ void issue_chunk(const __nv_bfloat16 *abase, const __
 #pragma unroll
             for (int j = 0; i + j < NP; ++j, ++prod) {
                 const uint64_t ad = smem_desc(a0 + i * kAElems * 2 + ks * 256, 128, sbo);
-                const uint64_t bd = smem_desc(b0 + j * kBElems * 2 + ks * 256, 128, sbo);
+                const uint64_t bd = smem_desc(b0 + j * belems * 2 + ks * 256, 128, sbo);
                 mma_bf16(tmem, ad, bd, idesc, (first && ks == 0 && prod == 0) ? 0u : 1u);
             }
     }
+}
+
+// Thread 0 only: for every chunk of kb_total k blocks, bulk-copy the NP
+// pieces of the A chunk (a_rb row blocks, chunks of a_rb * kbc core
+// matrices back to back from a_src) and of the B chunk (the first nbc col
+// blocks of a chunk of b_cb col blocks from b_src), then issue its MMAs and
+// wait for them before the next copy overwrites the operands.  Returns false
+// (flag set) if a bounded wait expired; it then waits once more, bounded,
+// for work still in flight.
+template <int NP>
+__device__ bool run_chunks(TcSmem &sm, __nv_bfloat16 *sa, __nv_bfloat16 *sb, int belems, const uint16_t *a_src,
+                           long long a_piece, int a_rb, const uint16_t *b_src, long long b_piece, int b_cb, int nbc,
+                           int N, int kb_total, int *err, int code) {
+    int chunk = 0;
+    for (int c0 = 0; c0 < kb_total; c0 += kTcChunkKB, ++chunk) {
+        const int kbc = min(kTcChunkKB, kb_total - c0);
+        const uint32_t abytes = static_cast<uint32_t>(a_rb) * kbc * 128;
+        const uint32_t bbytes = static_cast<uint32_t>(nbc) * kbc * 128;
+        expect_tx(&sm.mbar_ld, NP * (abytes + bbytes));
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+            bulk_copy(sa + i * kAElems, a_src + i * a_piece + static_cast<long long>(a_rb) * 64 * c0, abytes,
+                      &sm.mbar_ld);
+            bulk_copy(sb + i * belems, b_src + i * b_piece + static_cast<long long>(b_cb) * 64 * c0, bbytes,
+                      &sm.mbar_ld);
+        }
+        if (!mbar_wait(&sm.mbar_ld, chunk & 1)) {
+            atomicExch(err, code);
+            mbar_wait(&sm.mbar_ld, chunk & 1);
+            return false;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        issue_chunk<NP>(sa, sb, belems, sm.tmem, kbc, N, chunk == 0);
+        mma_commit(&sm.mbar_mma);
+        if (!mbar_wait(&sm.mbar_mma, chunk & 1)) {
+            atomicExch(err, code + 1);
+            mbar_wait(&sm.mbar_mma, chunk & 1);
+            return false;
+        }
+    }
+    return true;
 }
 
 __device__ __forceinline__ void tc_prologue(TcSmem &sm, uint32_t ncols) {
@@ -211,81 +232,32 @@ __device__ __forceinline__ void tc_epilogue_free(TcSmem &sm, uint32_t ncols) {
 
 // ---------------------------------------------------------------------------
 // Analysis projection: one block per tile (m, p, rows q0..q0+nrows), all B
-// states.  Columns col = b*10 + g*2 + (re, im) of W = F2[b][m][g][p][j].
-// Output Y[b][e][g] (float2), e = ext_offset(m) + p + 2q.
+// states.  Columns col = b*10 + g*2 + (re, im) of W = F2[b][m][g][p][j],
+// pre-split by k2_split_w.  Output Y[b][e][g] (float2), e = ext_offset(m) + p + 2q.
 // ---------------------------------------------------------------------------
 template <int NP>
-__global__ void __launch_bounds__(kTcThreads) k3_tc(TcTables tc, Dims d, int B, const float2 *__restrict__ f2,
-                                                    float2 *__restrict__ y) {
+__global__ void __launch_bounds__(kTcThreads) k3_tc(TcTables tc, Dims d, int B, float2 *__restrict__ y) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     TcSmem &sm = *reinterpret_cast<TcSmem *>(smem_raw);
-    __nv_bfloat16 *sa = a_base<NP>(smem_raw);
-    __nv_bfloat16 *sb = b_base<NP>(smem_raw);
     const TcTile3 t = tc.tiles3[blockIdx.x];
     const int ncols = 10 * B;
     const int N = (ncols + 15) / 16 * 16;
     const int nbc = N / 8;                      // column blocks
+    const int belems = b_elems(nbc);
+    __nv_bfloat16 *sa = reinterpret_cast<__nv_bfloat16 *>(smem_raw + kCtrlBytes);
+    __nv_bfloat16 *sb = sa + NP * kAElems;
     const uint32_t tcols = N <= 32 ? 32u : (N <= 64 ? 64u : 128u);
-    const int T = d.T, J2 = d.J2;
+    const int T = d.T;
     const int kjb = tc.kj / 8;
     tc_prologue(sm, tcols);
-
-    int chunk = 0;
-    for (int c0 = 0; c0 < kjb; c0 += kTcChunkKB, ++chunk) {
-        const int kbc = min(kTcChunkKB, kjb - c0);
-        const int kw = kbc * 8;                 // latitudes in this chunk
-        const uint32_t abytes = static_cast<uint32_t>(t.nrb) * kbc * 128;
-        if (threadIdx.x == 0) {
-            expect_tx(&sm.mbar_ld, abytes * NP);
-#pragma unroll
-            for (int i = 0; i < NP; ++i)
-                bulk_copy(sa + i * kAElems, tc.a3 + i * tc.elems3 + t.aoff + static_cast<long long>(t.nrb) * 64 * c0,
-                          abytes, &sm.mbar_ld);
-        }
-        // zero the A row blocks beyond the tile's rows (not touched by the copy)
-#pragma unroll
-        for (int i = 0; i < NP; ++i) zero_range(sa + i * kAElems, t.nrb * kbc * 64, 16 * kbc * 64);
-        // B = W^T chunk: [col block][kb][8 cols][8 latitudes]; loads issued in
-        // batches of 8 independent requests per thread, then split and stored
-        const int items = (N / 2) * kw;
-        for (int base0 = 0; base0 < items; base0 += 8 * kTcThreads) {
-            float2 wv[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int k = base0 + u * kTcThreads + threadIdx.x;
-                wv[u] = make_float2(0.f, 0.f);
-                if (k < items) {
-                    const int cp = k / kw, jj = k - cp * kw;
-                    const int j = c0 * 8 + jj;
-                    if (2 * cp < ncols && j < J2) {
-                        const int b = cp / 5, g = cp - b * 5;
-                        wv[u] = f2[((static_cast<size_t>(b) * (T + 1) + t.m) * 5 + g) * 2 * J2 + t.p * J2 + j];
-                    }
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int k = base0 + u * kTcThreads + threadIdx.x;
-                if (k < items) {
-                    const int cp = k / kw, jj = k - cp * kw;
-                    const int c = 2 * cp;
-                    const int e = ((c >> 3) * kbc + (jj >> 3)) * 64 + (c & 7) * 8 + (jj & 7);
-                    split_store<NP>(wv[u].x, sb, kBElems, e);
-                    split_store<NP>(wv[u].y, sb, kBElems, e + 8);   // column c + 1: next core row
-                }
-            }
-        }
-        asm volatile("fence.proxy.async.shared::cta;");
-        __syncthreads();
-        if (!block_wait(sm, &sm.mbar_ld, chunk & 1, tc.err, 1)) break;
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        if (threadIdx.x == 0) {
-            issue_chunk<NP>(sa, sb, sm.tmem, kbc, N, chunk == 0);
-            mma_commit(&sm.mbar_mma);
-        }
-        if (!block_wait(sm, &sm.mbar_mma, chunk & 1, tc.err, 2)) break;
-        asm volatile("tcgen05.fence::after_thread_sync;");
+    if (threadIdx.x == 0) {
+        const long long gbase = static_cast<long long>(2 * t.m + t.p) * kNbc3 * kjb * 64;
+        if (!run_chunks<NP>(sm, sa, sb, belems, tc.a3 + t.aoff, tc.elems3, t.nrb, tc.wb + gbase, tc.wb_elems,
+                            kNbc3, nbc, N, kjb, tc.err, 1))
+            sm.abort = 1;
     }
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
 
     if (!sm.abort) {
         const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -312,89 +284,32 @@ __global__ void __launch_bounds__(kTcThreads) k3_tc(TcTables tc, Dims d, int B, 
 
 // ---------------------------------------------------------------------------
 // Synthesis: one block per tile (m, p, latitudes j0..j0+nj), all B states.
-// Columns col = b*8 + f*2 + (re, im) of the prepared coefficients
-// C[q][col] (fields zeta, Phi', U, V as in the FP64/FP32 synthesis), read
-// from cbuf[b][e][4] (FP32).  Output F1[b][j][f][p][m] (float2).
+// Columns col = b*8 + f*2 + (re, im) of the prepared coefficients C[q][col]
+// (fields zeta, Phi', U, V as in the FP64/FP32 synthesis), pre-split by
+// k1_prep_split.  Output F1[b][j][f][p][m] (float2).
 // ---------------------------------------------------------------------------
 template <int NP>
-__global__ void __launch_bounds__(kTcThreads) k1_tc(TcTables tc, Dims d, int B, const float2 *__restrict__ cbuf,
-                                                    float2 *__restrict__ f1) {
+__global__ void __launch_bounds__(kTcThreads) k1_tc(TcTables tc, Dims d, int B, float2 *__restrict__ f1) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     TcSmem &sm = *reinterpret_cast<TcSmem *>(smem_raw);
-    __nv_bfloat16 *sa = a_base<NP>(smem_raw);
-    __nv_bfloat16 *sb = b_base<NP>(smem_raw);
     const TcTile1 t = tc.tiles1[blockIdx.x];
     const int ncols = 8 * B;
     const int N = (ncols + 15) / 16 * 16;
     const int nbc = N / 8;
+    const int belems = b_elems(nbc);
+    __nv_bfloat16 *sa = reinterpret_cast<__nv_bfloat16 *>(smem_raw + kCtrlBytes);
+    __nv_bfloat16 *sb = sa + NP * kAElems;
     const uint32_t tcols = N <= 32 ? 32u : 64u;
     const int T = d.T;
     const int m = t.m;
-    const int krb = t.KR / 8;
     tc_prologue(sm, tcols);
-
-    int chunk = 0;
-    for (int c0 = 0; c0 < krb; c0 += kTcChunkKB, ++chunk) {
-        const int kbc = min(kTcChunkKB, krb - c0);
-        const int kw = kbc * 8;                 // rows q in this chunk
-        const uint32_t abytes = static_cast<uint32_t>(t.njb) * kbc * 128;
-        if (threadIdx.x == 0) {
-            expect_tx(&sm.mbar_ld, abytes * NP);
-#pragma unroll
-            for (int i = 0; i < NP; ++i)
-                bulk_copy(sa + i * kAElems, tc.a1 + i * tc.elems1 + t.aoff + static_cast<long long>(t.njb) * 64 * c0,
-                          abytes, &sm.mbar_ld);
-        }
-#pragma unroll
-        for (int i = 0; i < NP; ++i) zero_range(sa + i * kAElems, t.njb * kbc * 64, 16 * kbc * 64);
-        // B = C^T chunk: [col block][kb][8 cols][8 rows q]; one column block
-        // per state holds the 4 complex prepared coefficients of row q
-        const int items = nbc * kw;
-        for (int base0 = 0; base0 < items; base0 += 2 * kTcThreads) {
-            float4 cv[2][2];
-#pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                const int k = base0 + u * kTcThreads + threadIdx.x;
-                cv[u][0] = cv[u][1] = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (k < items) {
-                    const int bb = k / kw, qq = k - bb * kw;
-                    const int q = c0 * 8 + qq;
-                    if (bb < B && q < t.R) {
-                        const float4 *src = reinterpret_cast<const float4 *>(
-                            cbuf + (static_cast<size_t>(bb) * d.next + ext_offset(T, m) + t.p + 2 * q) * 4);
-                        cv[u][0] = src[0];
-                        cv[u][1] = src[1];
-                    }
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                const int k = base0 + u * kTcThreads + threadIdx.x;
-                if (k < items) {
-                    const int bb = k / kw, qq = k - bb * kw;
-                    const int e = (bb * kbc + (qq >> 3)) * 64 + (qq & 7);
-                    split_store<NP>(cv[u][0].x, sb, kBElems, e + 0 * 8);
-                    split_store<NP>(cv[u][0].y, sb, kBElems, e + 1 * 8);
-                    split_store<NP>(cv[u][0].z, sb, kBElems, e + 2 * 8);
-                    split_store<NP>(cv[u][0].w, sb, kBElems, e + 3 * 8);
-                    split_store<NP>(cv[u][1].x, sb, kBElems, e + 4 * 8);
-                    split_store<NP>(cv[u][1].y, sb, kBElems, e + 5 * 8);
-                    split_store<NP>(cv[u][1].z, sb, kBElems, e + 6 * 8);
-                    split_store<NP>(cv[u][1].w, sb, kBElems, e + 7 * 8);
-                }
-            }
-        }
-        asm volatile("fence.proxy.async.shared::cta;");
-        __syncthreads();
-        if (!block_wait(sm, &sm.mbar_ld, chunk & 1, tc.err, 3)) break;
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        if (threadIdx.x == 0) {
-            issue_chunk<NP>(sa, sb, sm.tmem, kbc, N, chunk == 0);
-            mma_commit(&sm.mbar_mma);
-        }
-        if (!block_wait(sm, &sm.mbar_mma, chunk & 1, tc.err, 4)) break;
-        asm volatile("tcgen05.fence::after_thread_sync;");
+    if (threadIdx.x == 0) {
+        if (!run_chunks<NP>(sm, sa, sb, belems, tc.a1 + t.aoff, tc.elems1, t.njb, tc.cb + tc.cb_off[2 * m + t.p],
+                            tc.cb_elems, kNbc1, nbc, N, t.KR / 8, tc.err, 3))
+            sm.abort = 1;
     }
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
 
     if (!sm.abort) {
         const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -413,17 +328,60 @@ __global__ void __launch_bounds__(kTcThreads) k1_tc(TcTables tc, Dims d, int B, 
     tc_epilogue_free(sm, tcols);
 }
 
-// Synthesis coefficients in FP32, one thread per (extended row e, state b):
-// cbuf[b][e] = (zeta, Phi', U, V) of degree n' (the wind factors as in the
-// FP64/FP32 synthesis), each state value converted once.
-__global__ void k1_prep_f32(const double2 *__restrict__ states, long long sstride, Dims d,
-                            const double *__restrict__ syn, const int *__restrict__ row_m, float2 *__restrict__ cbuf) {
+// W^T pieces of the projection, one thread per (group, col block, k block):
+// 8 columns x 8 latitudes of F2 (zero beyond B states and J2 latitudes),
+// split and written as NP core matrices.
+template <int NP>
+__global__ void k2_split_w(TcTables tc, Dims d, int B, int nbc, const float2 *__restrict__ f2) {
+    const int kjb = tc.kj / 8;
+    const int per_group = nbc * kjb;
+    const long long idx = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (idx >= 2LL * (d.T + 1) * per_group) return;
+    const int g = static_cast<int>(idx / per_group);
+    const int rem = static_cast<int>(idx - static_cast<long long>(g) * per_group);
+    const int cb = rem / kjb, kb = rem - cb * kjb;
+    const int m = g >> 1, p = g & 1;
+    const int T = d.T, J2 = d.J2;
+    const int c0 = kb / kTcChunkKB * kTcChunkKB, kbc = min(kTcChunkKB, kjb - c0);
+    float v[8][8];                              // [column in block][latitude in k block]
+#pragma unroll
+    for (int cp = 0; cp < 4; ++cp) {
+        const int c = cb * 8 + 2 * cp;          // even: (re, im) of one (b, g) pair
+        const int b = c / 10;
+        const float2 *src = nullptr;
+        if (b < B) src = f2 + ((static_cast<size_t>(b) * (T + 1) + m) * 5 + (c - 10 * b) / 2) * 2 * J2 + p * J2;
+#pragma unroll
+        for (int kr = 0; kr < 8; ++kr) {
+            const int j = kb * 8 + kr;
+            const float2 w = (src && j < J2) ? src[j] : make_float2(0.f, 0.f);
+            v[2 * cp][kr] = w.x;
+            v[2 * cp + 1][kr] = w.y;
+        }
+    }
+    uint16_t *dst = tc.wb + static_cast<long long>(g) * kNbc3 * kjb * 64 + static_cast<long long>(c0) * kNbc3 * 64 +
+                    (cb * kbc + kb - c0) * 64;
+#pragma unroll
+    for (int cr = 0; cr < 8; ++cr) {
+        uint4 out[NP];
+        split8<NP>(v[cr], out);
+#pragma unroll
+        for (int i = 0; i < NP; ++i) *reinterpret_cast<uint4 *>(dst + i * tc.wb_elems + cr * 8) = out[i];
+    }
+}
+
+// Synthesis coefficients, one thread per (extended row e, state b): the
+// FP32 values (zeta, Phi', U, V) of degree n' (the wind factors as in the
+// FP64/FP32 synthesis), split into NP pieces at row q of column block b.
+template <int NP>
+__global__ void k1_prep_split(TcTables tc, const double2 *__restrict__ states, long long sstride, Dims d,
+                              const double *__restrict__ syn, const int *__restrict__ row_m) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     const int b = blockIdx.y;
     if (e >= d.next) return;
     const int T = d.T, nc = d.ncoef;
     const int m = row_m[e];
-    const int n = m + (e - ext_offset(T, m));
+    const int ne = e - ext_offset(T, m);
+    const int n = m + ne;
     const int off = order_offset(T, m);
     const double2 *st = states + b * sstride;
     auto ld = [&](int f, int k) -> double2 {
@@ -433,37 +391,76 @@ __global__ void k1_prep_f32(const double2 *__restrict__ states, long long sstrid
     const double2 d0 = ld(F_DIV, n), dm = ld(F_DIV, n - 1), dp = ld(F_DIV, n + 1);
     const double2 p0 = ld(F_PHI, n);
     const double c0 = syn[3 * e], c1 = syn[3 * e + 1], c2 = syn[3 * e + 2];
-    float4 *o = reinterpret_cast<float4 *>(cbuf + (static_cast<size_t>(b) * d.next + e) * 4);
-    o[0] = make_float4(float(z0.x), float(z0.y), float(p0.x), float(p0.y));
-    o[1] = make_float4(float(-c0 * d0.y - c1 * zm.x - c2 * zp.x), float(c0 * d0.x - c1 * zm.y - c2 * zp.y),
-                       float(-c0 * z0.y + c1 * dm.x + c2 * dp.x), float(c0 * z0.x + c1 * dm.y + c2 * dp.y));
+    const float x[8] = {float(z0.x),
+                        float(z0.y),
+                        float(p0.x),
+                        float(p0.y),
+                        float(-c0 * d0.y - c1 * zm.x - c2 * zp.x),
+                        float(c0 * d0.x - c1 * zm.y - c2 * zp.y),
+                        float(-c0 * z0.y + c1 * dm.x + c2 * dp.x),
+                        float(c0 * z0.x + c1 * dm.y + c2 * dp.y)};
+    const int p = ne & 1, q = ne >> 1;
+    const int krb = tc_group_krows(T, m, p) / 8;
+    const int kb = q >> 3, kr = q & 7;
+    const int cc0 = kb / kTcChunkKB * kTcChunkKB, kbc = min(kTcChunkKB, krb - cc0);
+    uint16_t *dst = tc.cb + tc.cb_off[2 * m + p] + static_cast<long long>(cc0) * kNbc1 * 64 +
+                    (b * kbc + kb - cc0) * 64 + kr;
+#pragma unroll
+    for (int cr = 0; cr < 8; ++cr) {
+        float r = x[cr];
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+            const __nv_bfloat16 h = __float2bfloat16_rn(r);
+            dst[i * tc.cb_elems + cr * 8] = __bfloat16_as_ushort(h);
+            r -= __bfloat162float(h);
+        }
+    }
 }
 
 }  // namespace
 
 cudaError_t configure_tc_kernels() {
-    const int s2 = (int)tc_smem_bytes(2), s3 = (int)tc_smem_bytes(3);
-    cudaError_t e = cudaFuncSetAttribute(k3_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, s2);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k3_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, s3);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k1_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, s2);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k1_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, s3);
+    cudaError_t e = cudaSuccess;
+    auto set = [&](const void *f, int bytes) {
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    };
+    set(reinterpret_cast<const void *>(k3_tc<2>), (int)tc_smem_bytes(2, kNbc3));
+    set(reinterpret_cast<const void *>(k3_tc<3>), (int)tc_smem_bytes(3, kNbc3));
+    set(reinterpret_cast<const void *>(k1_tc<2>), (int)tc_smem_bytes(2, kNbc1));
+    set(reinterpret_cast<const void *>(k1_tc<3>), (int)tc_smem_bytes(3, kNbc1));
     return e;
 }
 
 cudaError_t launch_tc_synthesis(const TcTables &tc, const Dims &d, int B, const double2 *states, long long sstride,
-                                const double *syn, const int *row_m, float2 *cbuf, float2 *f1, cudaStream_t s) {
+                                const double *syn, const int *row_m, float2 *f1, cudaStream_t s, int *launches) {
     if (B < 1 || B > kMaxNodes) return cudaErrorInvalidValue;
-    k1_prep_f32<<<dim3((d.next + 127) / 128, B), 128, 0, s>>>(states, sstride, d, syn, row_m, cbuf);
-    if (tc.npieces == 2) k1_tc<2><<<tc.ntiles1, kTcThreads, tc_smem_bytes(2), s>>>(tc, d, B, cbuf, f1);
-    else k1_tc<3><<<tc.ntiles1, kTcThreads, tc_smem_bytes(3), s>>>(tc, d, B, cbuf, f1);
+    const int nbc = (8 * B + 15) / 16 * 2;
+    const dim3 gp((d.next + 127) / 128, B);
+    if (tc.npieces == 2) {
+        k1_prep_split<2><<<gp, 128, 0, s>>>(tc, states, sstride, d, syn, row_m);
+        k1_tc<2><<<tc.ntiles1, kTcThreads, tc_smem_bytes(2, nbc), s>>>(tc, d, B, f1);
+    } else {
+        k1_prep_split<3><<<gp, 128, 0, s>>>(tc, states, sstride, d, syn, row_m);
+        k1_tc<3><<<tc.ntiles1, kTcThreads, tc_smem_bytes(3, nbc), s>>>(tc, d, B, f1);
+    }
+    if (launches) *launches += 2;
     return cudaGetLastError();
 }
 
 cudaError_t launch_tc_projection(const TcTables &tc, const Dims &d, int B, const float2 *f2, float2 *y,
-                                 cudaStream_t s) {
+                                 cudaStream_t s, int *launches) {
     if (B < 1 || B > kMaxNodes) return cudaErrorInvalidValue;
-    if (tc.npieces == 2) k3_tc<2><<<tc.ntiles3, kTcThreads, tc_smem_bytes(2), s>>>(tc, d, B, f2, y);
-    else k3_tc<3><<<tc.ntiles3, kTcThreads, tc_smem_bytes(3), s>>>(tc, d, B, f2, y);
+    const int nbc = (10 * B + 15) / 16 * 2;
+    const long long nsplit = 2LL * (d.T + 1) * nbc * (tc.kj / 8);
+    const unsigned gs = static_cast<unsigned>((nsplit + 127) / 128);
+    if (tc.npieces == 2) {
+        k2_split_w<2><<<gs, 128, 0, s>>>(tc, d, B, nbc, f2);
+        k3_tc<2><<<tc.ntiles3, kTcThreads, tc_smem_bytes(2, nbc), s>>>(tc, d, B, y);
+    } else {
+        k2_split_w<3><<<gs, 128, 0, s>>>(tc, d, B, nbc, f2);
+        k3_tc<3><<<tc.ntiles3, kTcThreads, tc_smem_bytes(3, nbc), s>>>(tc, d, B, y);
+    }
+    if (launches) *launches += 2;
     return cudaGetLastError();
 }
 

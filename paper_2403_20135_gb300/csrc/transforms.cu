@@ -266,6 +266,253 @@ __global__ void __launch_bounds__(64) k3_project(const V2<R> *__restrict__ f2, D
 }
 
 // ---------------------------------------------------------------------------
+// FP32 contractions, register-tiled for the FMA pipe (the FP64 kernels above
+// are bound by GB300's FP64 rate; in FP32 the same loops would be bound by
+// load issue and latency).
+//
+// K1 (FP32): one block per (state, order pair), all latitudes.  A thread
+// owns four consecutive latitudes and keeps the even/odd sums of the four
+// fields for all four in registers; S neighbouring lanes split the rows and
+// are summed with shuffles at the end (S = 4, 2, 1 keeps a block at <= 256
+// threads for up to 256, 512, 1024 northern latitudes).  Each step issues the table
+// loads of two row pairs before their 128 FMAs.  The coefficients are
+// prepared in FP32 (the precision of this path).
+// ---------------------------------------------------------------------------
+template <int S>
+__global__ void __launch_bounds__(256) k1_synthesis_f32(const double2 *__restrict__ states, long long sstride,
+                                                        Dims d, const float *__restrict__ pbar,
+                                                        const double *__restrict__ syn, float2 *__restrict__ f1) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2 *cf = reinterpret_cast<float2 *>(smem_raw);   // [rows][4]
+    const int T = d.T;
+    const int b = blockIdx.x;
+    const int m1 = blockIdx.y, m2 = T - blockIdx.y;
+    const int nn1 = T + 2 - m1;
+    const int nn2 = (m2 > m1) ? T + 2 - m2 : 0;
+    const int rows = nn1 + nn2;
+    const double2 *st = states + b * sstride;
+    const int nc = d.ncoef;
+    for (int r = threadIdx.x; r < rows; r += blockDim.x) {
+        const int m = (r < nn1) ? m1 : m2;
+        const int t = (r < nn1) ? r : r - nn1;
+        const int n = m + t;
+        const int off = order_offset(T, m);
+        const int e = ext_offset(T, m) + t;
+        auto ld = [&](int f, int k) -> float2 {
+            if (k < m || k > T) return make_float2(0.f, 0.f);
+            const double2 v = st[f * nc + off + k - m];
+            return make_float2(float(v.x), float(v.y));
+        };
+        const float2 z0 = ld(F_ZETA, n), zm = ld(F_ZETA, n - 1), zp = ld(F_ZETA, n + 1);
+        const float2 d0 = ld(F_DIV, n), dm = ld(F_DIV, n - 1), dp = ld(F_DIV, n + 1);
+        const float c0 = float(syn[3 * e]), c1 = float(syn[3 * e + 1]), c2 = float(syn[3 * e + 2]);
+        cf[r * 4 + G_ZETA] = z0;
+        cf[r * 4 + G_PHI] = ld(F_PHI, n);
+        cf[r * 4 + G_U] = make_float2(-c0 * d0.y - c1 * zm.x - c2 * zp.x, c0 * d0.x - c1 * zm.y - c2 * zp.y);
+        cf[r * 4 + G_V] = make_float2(-c0 * z0.y + c1 * dm.x + c2 * dp.x, c0 * z0.x + c1 * dm.y + c2 * dp.y);
+    }
+    __syncthreads();
+
+    const int part = threadIdx.x % S;
+    const int j0 = 4 * (threadIdx.x / S);
+    const bool active = j0 < d.J2;
+    const int jl = active ? j0 : 0;                      // idle lanes read a valid row and store nothing
+    for (int half = 0; half < 2; ++half) {
+        const int m = half ? m2 : m1;
+        const int nn = half ? nn2 : nn1;
+        if (nn == 0) break;
+        const float2 *c = cf + (half ? nn1 : 0) * 4;
+        float2 ae[4][4], ao[4][4];                       // [field][latitude]
+#pragma unroll
+        for (int f = 0; f < 4; ++f)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) ae[f][k] = ao[f][k] = make_float2(0.f, 0.f);
+        const float *prow = pbar + static_cast<size_t>(ext_offset(T, m)) * d.J2p + jl;
+        auto row = [&](int t) { return *reinterpret_cast<const float4 *>(prow + static_cast<size_t>(t) * d.J2p); };
+        auto accum = [&](float2 (&a)[4][4], const float4 pv4, int t) {
+            const float pv[4] = {pv4.x, pv4.y, pv4.z, pv4.w};
+#pragma unroll
+            for (int f = 0; f < 4; ++f) {
+                const float2 cc = c[t * 4 + f];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    a[f][k].x = fmaf(pv[k], cc.x, a[f][k].x);
+                    a[f][k].y = fmaf(pv[k], cc.y, a[f][k].y);
+                }
+            }
+        };
+        const int npairs = nn / 2;
+        int u = part;
+        for (; u + S < npairs; u += 2 * S) {
+            const int t0 = 2 * u, t1 = 2 * (u + S);
+            const float4 pe0 = row(t0), po0 = row(t0 + 1), pe1 = row(t1), po1 = row(t1 + 1);
+            accum(ae, pe0, t0);
+            accum(ao, po0, t0 + 1);
+            accum(ae, pe1, t1);
+            accum(ao, po1, t1 + 1);
+        }
+        if (u < npairs) {
+            const int t0 = 2 * u;
+            const float4 pe0 = row(t0), po0 = row(t0 + 1);
+            accum(ae, pe0, t0);
+            accum(ao, po0, t0 + 1);
+        }
+        if ((nn & 1) && part == (npairs % S)) accum(ae, row(nn - 1), nn - 1);
+#pragma unroll
+        for (int f = 0; f < 4; ++f)
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+#pragma unroll
+                for (int o = 1; o < S; o <<= 1) {
+                    ae[f][k].x += __shfl_xor_sync(0xffffffffu, ae[f][k].x, o);
+                    ae[f][k].y += __shfl_xor_sync(0xffffffffu, ae[f][k].y, o);
+                    ao[f][k].x += __shfl_xor_sync(0xffffffffu, ao[f][k].x, o);
+                    ao[f][k].y += __shfl_xor_sync(0xffffffffu, ao[f][k].y, o);
+                }
+        if (active && part == 0) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if (j0 + k >= d.J2) break;
+                float2 *o = f1 + (static_cast<size_t>(b) * d.J2 + j0 + k) * (4 * 2 * (T + 1)) + m;
+#pragma unroll
+                for (int f = 0; f < 4; ++f) {
+                    o[(f * 2 + 0) * (T + 1)] = ae[f][k];
+                    o[(f * 2 + 1) * (T + 1)] = ao[f][k];
+                }
+            }
+        }
+    }
+}
+
+// K3a (FP32): one block per (state, order pair m, T - m).  The W rows of
+// both orders (10 x J2 complex each) are staged in shared memory; a thread
+// group of kPrjParts neighbouring lanes owns a row quad (rows e, e+2, e+4,
+// e+6 of one group (m, p)), each lane every kPrjParts-th 4-latitude block,
+// 40 accumulators, summed with shuffles.  Per four latitudes a lane issues
+// four 16-byte table loads (neighbouring lanes: neighbouring 16 bytes of the
+// same row) and ten 16-byte shared loads for 160 FMAs.  VEC: J2 even, so
+// every W row starts on a 16-byte boundary.
+constexpr int kPrjParts = 4;
+template <bool VEC>
+__global__ void __launch_bounds__(512) k3_project_f32(const float2 *__restrict__ f2, Dims d,
+                                                      const float *__restrict__ pbar, float2 *__restrict__ y) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2 *ws = reinterpret_cast<float2 *>(smem_raw);   // [2][10][J2]
+    const int T = d.T, J2 = d.J2;
+    const int b = blockIdx.x;
+    const int m1 = blockIdx.y, m2 = T - blockIdx.y;
+    const int norders = (m2 > m1) ? 2 : 1;
+    for (int h = 0; h < norders; ++h) {
+        const float2 *src = f2 + (static_cast<size_t>(b) * (T + 1) + (h ? m2 : m1)) * 10 * J2;
+        for (int i = threadIdx.x; i < 10 * J2; i += blockDim.x) ws[h * 10 * J2 + i] = src[i];
+    }
+    __syncthreads();
+    // quads of (m1, p=0), (m1, p=1), (m2, p=0), (m2, p=1)
+    auto quads_of = [&](int m, int p) { return ((T + 3 - m - p) / 2 + 3) / 4; };
+    const int c1 = quads_of(m1, 0), c2 = c1 + quads_of(m1, 1);
+    const int c3 = c2 + (norders == 2 ? quads_of(m2, 0) : 0);
+    const int nqt = c3 + (norders == 2 ? quads_of(m2, 1) : 0);
+    const int part = threadIdx.x % kPrjParts;
+    const int per_pass = blockDim.x / kPrjParts;
+    for (int qb = 0; qb < nqt; qb += per_pass) {
+        const int qraw = qb + static_cast<int>(threadIdx.x) / kPrjParts;
+        const bool active = qraw < nqt;
+        const int qa = active ? qraw : nqt - 1;          // idle lanes compute a valid quad and store nothing
+        const int k = (qa < c1) ? 0 : (qa < c2) ? 1 : (qa < c3) ? 2 : 3;
+        const int qi = qa - ((k == 0) ? 0 : (k == 1) ? c1 : (k == 2) ? c2 : c3);
+        const int m = (k < 2) ? m1 : m2, p = k & 1, h = k >> 1;
+        const int R = (T + 3 - m - p) / 2;
+        const int q0 = 4 * qi, nr = min(4, R - q0);
+        const int e0 = ext_offset(T, m) + p + 2 * q0;
+        const float *pr[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) pr[r] = pbar + static_cast<size_t>(e0 + 2 * min(r, nr - 1)) * d.J2p;
+        const float2 *W = ws + h * 10 * J2 + p * J2;
+        float2 acc[4][5];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int g = 0; g < 5; ++g) acc[r][g] = make_float2(0.f, 0.f);
+        int jt = 0;                                      // first latitude of the scalar tail
+        if (VEC) {
+            jt = J2 & ~3;
+            for (int j = 4 * part; j < jt; j += 4 * kPrjParts) {
+                float pv[4][4];
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    const float4 v = *reinterpret_cast<const float4 *>(pr[r] + j);
+                    pv[r][0] = v.x; pv[r][1] = v.y; pv[r][2] = v.z; pv[r][3] = v.w;
+                }
+#pragma unroll
+                for (int g = 0; g < 5; ++g) {
+                    const float4 wa = *reinterpret_cast<const float4 *>(W + g * 2 * J2 + j);
+                    const float4 wb = *reinterpret_cast<const float4 *>(W + g * 2 * J2 + j + 2);
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) {
+                        acc[r][g].x = fmaf(pv[r][0], wa.x, acc[r][g].x);
+                        acc[r][g].y = fmaf(pv[r][0], wa.y, acc[r][g].y);
+                        acc[r][g].x = fmaf(pv[r][1], wa.z, acc[r][g].x);
+                        acc[r][g].y = fmaf(pv[r][1], wa.w, acc[r][g].y);
+                        acc[r][g].x = fmaf(pv[r][2], wb.x, acc[r][g].x);
+                        acc[r][g].y = fmaf(pv[r][2], wb.y, acc[r][g].y);
+                        acc[r][g].x = fmaf(pv[r][3], wb.z, acc[r][g].x);
+                        acc[r][g].y = fmaf(pv[r][3], wb.w, acc[r][g].y);
+                    }
+                }
+            }
+        }
+        for (int j = jt + part; j < J2; j += kPrjParts) {
+            float pv[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) pv[r] = pr[r][j];
+#pragma unroll
+            for (int g = 0; g < 5; ++g) {
+                const float2 w = W[g * 2 * J2 + j];
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    acc[r][g].x = fmaf(pv[r], w.x, acc[r][g].x);
+                    acc[r][g].y = fmaf(pv[r], w.y, acc[r][g].y);
+                }
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int g = 0; g < 5; ++g)
+#pragma unroll
+                for (int o = 1; o < kPrjParts; o <<= 1) {
+                    acc[r][g].x += __shfl_xor_sync(0xffffffffu, acc[r][g].x, o);
+                    acc[r][g].y += __shfl_xor_sync(0xffffffffu, acc[r][g].y, o);
+                }
+        if (active && part == 0) {
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                if (r >= nr) break;
+                float2 *o = y + (static_cast<size_t>(b) * d.next + e0 + 2 * r) * 5;
+#pragma unroll
+                for (int g = 0; g < 5; ++g) o[g] = acc[r][g];
+            }
+        }
+    }
+}
+
+// threads of a K3a (FP32) block: all row quads of the largest order pair,
+// kPrjParts lanes each, at most 512 (larger pairs take several passes)
+static int project_f32_threads(int T) {
+    int best = 0;
+    for (int m1 = 0; m1 <= T - m1; ++m1) {
+        int nq = 0;
+        for (int m : {m1, T - m1}) {
+            if (m == T - m1 && T - m1 == m1) break;
+            for (int p = 0; p < 2; ++p) nq += ((T + 3 - m - p) / 2 + 3) / 4;
+        }
+        best = best > nq ? best : nq;
+    }
+    const int t = (best * kPrjParts + 31) / 32 * 32;
+    return t < 512 ? t : 512;
+}
+
+// ---------------------------------------------------------------------------
 // K3b: per spectral mode (n, m), n = m..T (1/a folded in here):
 //   T_E(zeta)_n = -(1/a) [i m A^_n + n eps_{n+1} B^_{n+1} - (n+1) eps_n B^_{n-1}]
 //   T_E(div)_n  =  (1/a) [i m B^_n - n eps_{n+1} A^_{n+1} + (n+1) eps_n A^_{n-1}] + lambda_n E^_n
@@ -331,8 +578,13 @@ static cudaError_t configure(const Dims &d, const FftPlan &plan) {
     if (sm2 == 0) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(k2_ring<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k1_synthesis<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)(static_cast<size_t>(d.T + 4) * 4 * sizeof(V2<R>)));
+    e = cudaFuncSetAttribute(k1_synthesis<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(static_cast<size_t>(d.T + 4) * 4 * sizeof(V2<R>)));
+    if (e != cudaSuccess || sizeof(R) != sizeof(float)) return e;
+    const int smw = (int)(2 * 10 * static_cast<size_t>(d.J2) * sizeof(float2));
+    e = cudaFuncSetAttribute(k3_project_f32<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smw);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k3_project_f32<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smw);
 }
 
 template <typename R>
@@ -353,14 +605,22 @@ static cudaError_t launch_tendency_t(const Dims &d, const FftPlan &plan, int B, 
     if (timer) timer->mark(STAGE_SYNTH);
     if constexpr (sizeof(R) == sizeof(float)) {
         if (tc) {
-            // the prepared coefficients go through f3 (free until the projection)
-            cudaError_t e = launch_tc_synthesis(*tc, d, B, states, sstride, tb.syn, tb.row_m, f3, f1, s);
+            cudaError_t e = launch_tc_synthesis(*tc, d, B, states, sstride, tb.syn, tb.row_m, f1, s, launches);
             if (e != cudaSuccess) return e;
         } else {
-            k1_synthesis<R><<<g1, kK1Threads, sm1, s>>>(states, sstride, d, pbar, tb.syn, f1);
+            const int g4 = (d.J2 + 3) / 4;
+            const dim3 gs(B, (d.T + 2) / 2);
+            if (g4 <= 64)
+                k1_synthesis_f32<4><<<gs, (g4 * 4 + 31) / 32 * 32, sm1, s>>>(states, sstride, d, pbar, tb.syn, f1);
+            else if (g4 <= 128)
+                k1_synthesis_f32<2><<<gs, (g4 * 2 + 31) / 32 * 32, sm1, s>>>(states, sstride, d, pbar, tb.syn, f1);
+            else
+                k1_synthesis_f32<1><<<gs, (g4 + 31) / 32 * 32, sm1, s>>>(states, sstride, d, pbar, tb.syn, f1);
+            if (launches) ++*launches;
         }
     } else {
         k1_synthesis<R><<<g1, kK1Threads, sm1, s>>>(states, sstride, d, pbar, tb.syn, f1);
+        if (launches) ++*launches;
     }
     if (timer) timer->mark(STAGE_RING);
     k2_ring<R><<<dim3(d.J2, B), kK2Threads, sm2, s>>>(f1, f2, d, plan, tw, tb.mu, tb.w, nscratch,
@@ -368,19 +628,24 @@ static cudaError_t launch_tendency_t(const Dims &d, const FftPlan &plan, int B, 
     if (timer) timer->mark(STAGE_ANALYSIS);
     if constexpr (sizeof(R) == sizeof(float)) {
         if (tc) {
-            cudaError_t e = launch_tc_projection(*tc, d, B, f2, f3, s);
+            cudaError_t e = launch_tc_projection(*tc, d, B, f2, f3, s, launches);
             if (e != cudaSuccess) return e;
         } else {
-            k3_project<R><<<dim3((d.next + kK3Threads - 1) / kK3Threads, B), kK3Threads, 0, s>>>(f2, d, pbar,
-                                                                                                  tb.row_m, f3);
+            const dim3 g3(B, (d.T + 2) / 2);
+            const int nt = project_f32_threads(d.T);
+            const size_t smw = 2 * 10 * static_cast<size_t>(d.J2) * sizeof(float2);
+            if (d.J2 % 2 == 0) k3_project_f32<true><<<g3, nt, smw, s>>>(f2, d, pbar, f3);
+            else k3_project_f32<false><<<g3, nt, smw, s>>>(f2, d, pbar, f3);
+            if (launches) ++*launches;
         }
     } else {
         k3_project<R><<<dim3((d.next + kK3Threads - 1) / kK3Threads, B), kK3Threads, 0, s>>>(f2, d, pbar, tb.row_m,
                                                                                               f3);
+        if (launches) ++*launches;
     }
     if (timer) timer->mark(STAGE_EPILOGUE);
     k3_epilogue<R><<<dim3((d.ncoef + 127) / 128, B), 128, 0, s>>>(f3, d, tb.eps, tb.lam, tb.coef_m, tend, tstride);
-    if (launches) *launches += 4;
+    if (launches) *launches += 2;                  // ring + epilogue
     return cudaGetLastError();
 }
 

@@ -57,6 +57,25 @@ def test_mixed_tendency_accuracy(precision, T, J, L):
     assert np.all(rel_l2(one, ref) <= bound(precision, T))
 
 
+@pytest.mark.parametrize("precision", [1, 2])
+@pytest.mark.parametrize("J", [600, 1202])
+def test_mixed_tendency_many_latitudes(precision, J):
+    """Long latitude rows: the FP32 synthesis switches to fewer row splits per
+    latitude block (300 and 601 northern latitudes), the projection's K loop
+    and the tensor-core K chunks run much longer than at the bench size, and
+    601 is odd (scalar projection loads)."""
+    T, L = 21, 64
+    o = swe.SWE(sht.Grid(T, J, L), swe.default_physics())
+    wl = si.Workload("m", 2, T, J, L, 4, 3, 300.0, 1, 1, (100.0, 100.0))
+    u = swe.initial_state(wl, o)
+    ref = o.explicit(u)
+    s = _solver(T, J, L, 4, 3, 300.0, precision)
+    got = to_numpy(s.tendency(_cuda(np.stack([u, 2.0 * u]))))
+    s.sync()
+    assert np.all(rel_l2(got[0], ref) <= 2 * bound(precision, T)), rel_l2(got[0], ref)
+    assert np.all(rel_l2(got[1], o.explicit(2.0 * u)) <= 2 * bound(precision, T))
+
+
 @pytest.mark.parametrize("precision", [2, 3])
 def test_tensor_core_step_close_to_oracle(precision):
     T, J, L, M, K, dt = 42, 64, 128, 4, 5, 300.0
