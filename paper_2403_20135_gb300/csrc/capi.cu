@@ -61,6 +61,9 @@ struct sdc_ctx {
     int *row_m = nullptr, *coef_m = nullptr;
     double2 *tw = nullptr;
     float2 *tw32 = nullptr;
+    FftPlan plan16{};
+    float2 *twp32 = nullptr;
+    int ntwp = 0;
     // device workspaces
     double2 *un = nullptr, *U = nullptr, *E = nullptr, *E0 = nullptr;
     void *f1 = nullptr, *f2 = nullptr, *f3 = nullptr;
@@ -102,7 +105,7 @@ void free_ctx(sdc_ctx *c) {
     if (c->graph_retape) cudaGraphExecDestroy(c->graph_retape);
     if (c->graph_adjoint) cudaGraphExecDestroy(c->graph_adjoint);
     void *ptrs[] = {c->pbar, c->pbar32, c->eps, c->lam, c->mu2, c->w2, c->syn, c->row_m, c->coef_m, c->tw,
-                    c->tw32, c->un, c->U, c->E, c->E0, c->f1, c->f2, c->f3, c->resid_part, c->resid,
+                    c->tw32, c->twp32, c->un, c->U, c->E, c->E0, c->f1, c->f2, c->f3, c->resid_part, c->resid,
                     c->gstore, c->ub, c->eb, c->ubn, c->ubnext, c->eb0, c->snaps, c->phigrid, c->rgrid,
                     c->loss_part, c->loss_dev, c->tc_a3, c->tc_a1, c->tc_t3, c->tc_t1, c->tc_err, c->den,
                     c->tc_wb, c->tc_cb, c->tc_cboff};
@@ -137,6 +140,9 @@ DeviceTables tables(const sdc_ctx *c) {
     tb.syn = c->syn;
     tb.row_m = c->row_m;
     tb.coef_m = c->coef_m;
+    tb.plan16 = c->plan16;
+    tb.twp32 = c->twp32;
+    tb.ntwp = c->ntwp;
     return tb;
 }
 
@@ -163,6 +169,9 @@ cudaError_t tendency(sdc_ctx *c, int B, const double2 *states, long long sstride
     tb.syn = c->syn;
     tb.row_m = c->row_m;
     tb.coef_m = c->coef_m;
+    tb.plan16 = c->plan16;
+    tb.twp32 = c->twp32;
+    tb.ntwp = c->ntwp;
     Workspace ws{c->f1, c->f2, c->f3};
     const bool use_tc = c->precision == SDC_MIXED_BF16X3 || c->precision == SDC_MIXED_BF16X6;
     return launch_tendency(c->d, c->plan, fp32, B, states, sstride, tend, tstride, tb, ws, s, launches, timer,
@@ -547,6 +556,13 @@ int sdc_create(sdc_ctx **out, int T, int J, int L, int M, int K, double dt, cons
         for (size_t i = 0; i < table.size(); ++i) t32[i] = float(table[i]);
         SDC_TRY(upload(&c->pbar32, t32.data(), t32.size()));
         SDC_TRY(upload(&c->tw32, tw32.data(), tw32.size()));
+        if (!fft_plan16(L, c->plan16)) { free_ctx(c); return fail(SDC_EINVAL, "no FFT plan for nlon"); }
+        std::vector<double> pre, pim;
+        pass_twiddles(c->plan16, twr, twi, pre, pim);
+        std::vector<float2> twp(pre.size() + 1);           // never empty
+        for (size_t k = 0; k < pre.size(); ++k) twp[k] = make_float2(float(pre[k]), float(pim[k]));
+        c->ntwp = static_cast<int>(pre.size());
+        SDC_TRY(upload(&c->twp32, twp.data(), twp.size()));
         // the scalar helpers stay FP64
         SDC_TRY(upload(&c->pbar, table.data(), table.size()));
         SDC_TRY(upload(&c->tw, tw.data(), tw.size()));

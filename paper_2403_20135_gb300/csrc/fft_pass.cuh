@@ -1,0 +1,120 @@
+// Shared-memory Stockham FFT with radices up to 16 held in registers and a
+// padded layout (one spare element after every 16) that keeps the strided
+// reads and writes of every pass free of bank conflicts.  Used by the FP32
+// ring kernel, where the transforms are bound by shared-memory traffic: a
+// length-768 transform takes three passes (16, 16, 3) instead of five.
+//
+// Pass p of radix R over sequences of length L with Ns = R_0 ... R_{p-1}:
+//   v_r = in[j + r L/R] * w^(r k L/(Ns R)),  k = j mod Ns,  w = e^{-2 pi i / L}
+//   (v_0 .. v_{R-1}) <- R-point DFT,  out[(j - k) R + k + r Ns] = v_r.
+// The twiddles of each pass after the first are stored pass by pass as
+// [r - 1][k] (r = 1..R-1, k < Ns), so neighbouring threads read neighbouring
+// entries.  Inverse transforms conjugate every twiddle; both are unscaled.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "fft.cuh"
+
+namespace sdc {
+
+__host__ __device__ constexpr int fft_padded_len(int L) { return L + (L - 1) / 16 + 1; }
+__device__ __forceinline__ int fpad(int i) { return i + (i >> 4); }
+
+// e^{-2 pi i e / 16} for e = 0..15 (cos, -sin)
+__device__ __forceinline__ float2 w16(int e, bool inv) {
+    constexpr float c1 = 0.92387953251128675613f, s1 = 0.38268343236508977173f, h = 0.70710678118654752440f;
+    const float cs[16] = {1.f, c1, h, s1, 0.f, -s1, -h, -c1, -1.f, -c1, -h, -s1, 0.f, s1, h, c1};
+    const float sn[16] = {0.f, s1, h, c1, 1.f, c1, h, s1, 0.f, -s1, -h, -c1, -1.f, -c1, -h, -s1};
+    return make_float2(cs[e & 15], inv ? sn[e & 15] : -sn[e & 15]);
+}
+
+// In-register DFT of v[0..R-1], output in natural order.
+template <int R> __device__ __forceinline__ void dft(float2 *v, bool inv);
+
+template <> __device__ __forceinline__ void dft<2>(float2 *v, bool inv) { butterfly<float, 2>(v, inv); }
+template <> __device__ __forceinline__ void dft<3>(float2 *v, bool inv) { butterfly<float, 3>(v, inv); }
+template <> __device__ __forceinline__ void dft<4>(float2 *v, bool inv) { butterfly<float, 4>(v, inv); }
+
+// R = 4 R2: n = R2 n1 + n2, k = k1 + 4 k2.  4-point DFTs over n1, twiddle
+// w_R^(n2 k1), R2-point DFTs over n2.
+template <int R2>
+__device__ __forceinline__ void dft4x(float2 *v, bool inv) {
+    constexpr int R = 4 * R2;
+    float2 y[R2][4];
+#pragma unroll
+    for (int n2 = 0; n2 < R2; ++n2) {
+#pragma unroll
+        for (int n1 = 0; n1 < 4; ++n1) y[n2][n1] = v[R2 * n1 + n2];
+        dft<4>(y[n2], inv);
+#pragma unroll
+        for (int k1 = 1; k1 < 4; ++k1)
+            if (n2 * k1 != 0) y[n2][k1] = cmul<float>(y[n2][k1], w16(n2 * k1 * (16 / R), inv));
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) {
+        float2 z[R2];
+#pragma unroll
+        for (int n2 = 0; n2 < R2; ++n2) z[n2] = y[n2][k1];
+        dft<R2>(z, inv);
+#pragma unroll
+        for (int k2 = 0; k2 < R2; ++k2) v[k1 + 4 * k2] = z[k2];
+    }
+}
+template <> __device__ __forceinline__ void dft<8>(float2 *v, bool inv) { dft4x<2>(v, inv); }
+template <> __device__ __forceinline__ void dft<16>(float2 *v, bool inv) { dft4x<4>(v, inv); }
+
+// One pass over nb sequences (stride Lp) from src to dst.
+template <int R>
+__device__ __forceinline__ void fft_pass(const float2 *src, float2 *dst, int nb, int Lp, int L, int Ns,
+                                         const float2 *__restrict__ twp, bool inv) {
+    const int Lr = L / R;
+    const int total = nb * Lr;
+    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+        const int bb = t / Lr, j = t - bb * Lr;
+        const float2 *in = src + bb * Lp;
+        float2 *out = dst + bb * Lp;
+        const int k = j % Ns;
+        float2 v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = in[fpad(j + r * Lr)];
+        if (Ns > 1) {
+#pragma unroll
+            for (int r = 1; r < R; ++r) {
+                float2 w = twp[(r - 1) * Ns + k];
+                if (inv) w.y = -w.y;
+                v[r] = cmul<float>(v[r], w);
+            }
+        }
+        dft<R>(v, inv);
+        const int base = (j - k) * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) out[fpad(base + r * Ns)] = v[r];
+    }
+}
+
+// Transform nb padded sequences in a (scratch b, same size); returns the
+// buffer holding the result (a after an even number of passes, else b).
+__device__ inline float2 *fft_passes(float2 *a, float2 *b, int nb, int Lp, const FftPlan &plan,
+                                     const float2 *__restrict__ twp, bool inv) {
+    float2 *src = a, *dst = b;
+    int Ns = 1, toff = 0;
+    for (int p = 0; p < plan.nstages; ++p) {
+        const int R = plan.radix[p];
+        const float2 *tw = twp + toff;
+        switch (R) {
+            case 16: fft_pass<16>(src, dst, nb, Lp, plan.L, Ns, tw, inv); break;
+            case 8: fft_pass<8>(src, dst, nb, Lp, plan.L, Ns, tw, inv); break;
+            case 4: fft_pass<4>(src, dst, nb, Lp, plan.L, Ns, tw, inv); break;
+            case 2: fft_pass<2>(src, dst, nb, Lp, plan.L, Ns, tw, inv); break;
+            default: fft_pass<3>(src, dst, nb, Lp, plan.L, Ns, tw, inv); break;
+        }
+        __syncthreads();
+        if (Ns > 1) toff += (R - 1) * Ns;
+        Ns *= R;
+        float2 *t = src; src = dst; dst = t;
+    }
+    return src;
+}
+
+}  // namespace sdc

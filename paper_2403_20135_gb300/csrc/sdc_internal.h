@@ -98,6 +98,9 @@ struct DeviceTables {
     const double *syn;     // wind synthesis factors (c0, c1, c2) [next][3]
     const int *row_m;      // order m of each extended row [next]
     const int *coef_m;     // order m of each packed coefficient [ncoef]
+    FftPlan plan16;        // FP32 ring: passes of radix 16, then 8/4/2, then 3
+    const float2 *twp32;   // FP32 ring: per-pass twiddles of plan16 (after the first pass)
+    int ntwp;
 };
 
 // Transform workspaces (elements of the transform precision):
@@ -180,6 +183,10 @@ void epsilon_table(int T, std::vector<double> &eps);   // extended packing, eps_
 void synthesis_factors(int T, double radius, std::vector<double> &syn);   // [next][3]
 void order_maps(int T, std::vector<int> &row_m, std::vector<int> &coef_m);
 bool fft_plan(int L, FftPlan &plan);
+bool fft_plan16(int L, FftPlan &plan);
+// twiddles of every pass after the first, pass by pass as [r - 1][k < Ns]
+void pass_twiddles(const FftPlan &plan, const std::vector<double> &re, const std::vector<double> &im,
+                   std::vector<double> &pre, std::vector<double> &pim);
 void twiddles(int L, std::vector<double> &re, std::vector<double> &im);   // e^{-2 pi i k / L}
 
 // ---- kernel launchers (transforms.cu, sweep.cu) -------------------------

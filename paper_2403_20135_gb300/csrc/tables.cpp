@@ -313,6 +313,38 @@ bool fft_plan(int L, FftPlan &plan) {
     return rest == 1 && plan.nstages <= kMaxStages;
 }
 
+bool fft_plan16(int L, FftPlan &plan) {
+    plan.L = L;
+    plan.nstages = 0;
+    int rest = L;
+    while (rest % 16 == 0 && plan.nstages < kMaxStages) { plan.radix[plan.nstages++] = 16; rest /= 16; }
+    for (int r : {8, 4, 2})
+        if (rest % r == 0 && plan.nstages < kMaxStages) { plan.radix[plan.nstages++] = r; rest /= r; }
+    while (rest % 3 == 0) {
+        if (plan.nstages >= kMaxStages) return false;
+        plan.radix[plan.nstages++] = 3;
+        rest /= 3;
+    }
+    return rest == 1;
+}
+
+void pass_twiddles(const FftPlan &plan, const std::vector<double> &re, const std::vector<double> &im,
+                   std::vector<double> &pre, std::vector<double> &pim) {
+    pre.clear();
+    pim.clear();
+    int Ns = plan.radix[0];
+    for (int p = 1; p < plan.nstages; ++p) {
+        const int R = plan.radix[p];
+        const int tws = plan.L / (Ns * R);
+        for (int r = 1; r < R; ++r)
+            for (int k = 0; k < Ns; ++k) {
+                pre.push_back(re[static_cast<size_t>(r) * k * tws]);
+                pim.push_back(im[static_cast<size_t>(r) * k * tws]);
+            }
+        Ns *= R;
+    }
+}
+
 // e^{-2 pi i k / L}: the angle is folded into [0, pi/4] with exact integer
 // arithmetic before calling sin/cos.
 void twiddles(int L, std::vector<double> &re, std::vector<double> &im) {

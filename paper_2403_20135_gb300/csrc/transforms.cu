@@ -20,6 +20,7 @@
 #include <cuda_runtime.h>
 
 #include "fft.cuh"
+#include "fft_pass.cuh"
 #include "sdc_internal.h"
 
 namespace sdc {
@@ -217,6 +218,91 @@ __global__ void k2_ring(const V2<R> *__restrict__ f1, V2<R> *__restrict__ f2, Di
         V2<R> *o = f2 + ((static_cast<size_t>(b) * (T + 1) + m) * 5 + g) * 2 * d.J2 + j2;
         o[0] = cscale<R>(cadd<R>(gn, gs), wg);
         o[d.J2] = cscale<R>(csub<R>(gn, gs), wg);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// K2 (FP32): the ring kernel of k2_ring with the padded radix-16 passes of
+// fft_pass.cuh (shared-memory bound in FP32: fewer passes, no bank
+// conflicts, no copy-back).  X[5] and S[5] are both resident; the grid
+// fields land in X or S by the parity of the pass count, the products are
+// always written to X, the forward result again lands by parity.
+// ---------------------------------------------------------------------------
+__host__ __device__ inline size_t ring_f32_smem_bytes(int L, int ntw) {
+    return (10 * static_cast<size_t>(fft_padded_len(L)) + static_cast<size_t>(ntw)) * sizeof(float2);
+}
+
+__global__ void __launch_bounds__(256) k2_ring_f32(const float2 *__restrict__ f1, float2 *__restrict__ f2, Dims d,
+                                                   FftPlan plan, const float2 *__restrict__ twp, int ntw,
+                                                   const double *__restrict__ mu, const double *__restrict__ w,
+                                                   float2 *__restrict__ gstore) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int L = plan.L, Lp = fft_padded_len(L);
+    float2 *X = reinterpret_cast<float2 *>(smem_raw);   // [5][Lp]
+    float2 *S = X + 5 * Lp;                              // [5][Lp]
+    float2 *TW = S + 5 * Lp;                             // [ntw]
+    const int j2 = blockIdx.x;
+    const int b = blockIdx.y;
+    const int T = d.T;
+    const float2 *in = f1 + (static_cast<size_t>(b) * d.J2 + j2) * (4 * 2 * (T + 1));
+    for (int k = threadIdx.x; k < ntw; k += blockDim.x) TW[k] = twp[k];
+    const int gap = L - 2 * T - 1;
+    for (int i = threadIdx.x; i < 4 * gap; i += blockDim.x) {
+        const int f = i / gap, k = T + 1 + (i - f * gap);
+        X[f * Lp + fpad(k)] = make_float2(0.f, 0.f);
+    }
+    for (int i = threadIdx.x; i < 4 * (T + 1); i += blockDim.x) {
+        const int f = i / (T + 1), m = i - f * (T + 1);
+        float2 e = in[(f * 2 + 0) * (T + 1) + m];
+        float2 o = in[(f * 2 + 1) * (T + 1) + m];
+        if (m == 0) { e.y = 0.f; o.y = 0.f; }
+        const float2 n = cadd<float>(e, o), sv = csub<float>(e, o);
+        X[f * Lp + fpad(m)] = make_float2(n.x - sv.y, n.y + sv.x);                // n + i s
+        if (m > 0) X[f * Lp + fpad(L - m)] = make_float2(n.x + sv.y, -n.y + sv.x);   // conj(n) + i conj(s)
+    }
+    __syncthreads();
+    const float2 *G = fft_passes(X, S, 4, Lp, plan, TW, true);
+
+    const double mun = mu[j2];
+    const float cosl2 = float((1.0 - mun) * (1.0 + mun));
+    const float fN = float(d.two_omega * mun);
+    const float inv2c = 0.5f / cosl2;
+    float2 *gs = gstore ? gstore + (static_cast<size_t>(b) * d.J2 + j2) * 4 * L : nullptr;
+    for (int k = threadIdx.x; k < L; k += blockDim.x) {
+        const int kp = fpad(k);
+        const float2 zz = G[G_ZETA * Lp + kp], pp = G[G_PHI * Lp + kp];
+        const float2 uu = G[G_U * Lp + kp], vv = G[G_V * Lp + kp];
+        if (gs) {
+            gs[G_ZETA * L + k] = zz;
+            gs[G_PHI * L + k] = pp;
+            gs[G_U * L + k] = uu;
+            gs[G_V * L + k] = vv;
+        }
+        const float etaN = zz.x + fN, etaS = zz.y - fN;
+        X[P_A * Lp + kp] = make_float2(etaN * uu.x, etaS * uu.y);
+        X[P_B * Lp + kp] = make_float2(etaN * vv.x, etaS * vv.y);
+        X[P_C * Lp + kp] = make_float2(pp.x * uu.x, pp.y * uu.y);
+        X[P_D * Lp + kp] = make_float2(pp.x * vv.x, pp.y * vv.y);
+        X[P_E * Lp + kp] = make_float2((uu.x * uu.x + vv.x * vv.x) * inv2c, (uu.y * uu.y + vv.y * vv.y) * inv2c);
+    }
+    __syncthreads();
+    const float2 *Y = fft_passes(X, S, 5, Lp, plan, TW, false);
+
+    const double wj = w[j2];
+    const float wt = float(wj / ((1.0 - mun) * (1.0 + mun)));
+    const float wp = float(wj);
+    const float half_invL = 0.5f / float(L);
+    for (int i = threadIdx.x; i < 5 * (T + 1); i += blockDim.x) {
+        const int g = i / (T + 1), m = i - g * (T + 1);
+        const float2 y = Y[g * Lp + fpad(m)];
+        float2 yc = Y[g * Lp + fpad(m == 0 ? 0 : L - m)];
+        yc.y = -yc.y;
+        const float2 gn = cscale<float>(cadd<float>(y, yc), half_invL);
+        const float2 gsx = cscale<float>(mul_mi<float>(csub<float>(y, yc)), half_invL);
+        const float wg = (g == P_E) ? wp : wt;
+        float2 *o = f2 + ((static_cast<size_t>(b) * (T + 1) + m) * 5 + g) * 2 * d.J2 + j2;
+        o[0] = cscale<float>(cadd<float>(gn, gsx), wg);
+        o[d.J2] = cscale<float>(csub<float>(gn, gsx), wg);
     }
 }
 
@@ -581,6 +667,9 @@ static cudaError_t configure(const Dims &d, const FftPlan &plan) {
     e = cudaFuncSetAttribute(k1_synthesis<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(static_cast<size_t>(d.T + 4) * 4 * sizeof(V2<R>)));
     if (e != cudaSuccess || sizeof(R) != sizeof(float)) return e;
+    e = cudaFuncSetAttribute(k2_ring_f32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)ring_f32_smem_bytes(plan.L, plan.L));
+    if (e != cudaSuccess) return e;
     const int smw = (int)(2 * 10 * static_cast<size_t>(d.J2) * sizeof(float2));
     e = cudaFuncSetAttribute(k3_project_f32<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smw);
     if (e != cudaSuccess) return e;
@@ -623,8 +712,13 @@ static cudaError_t launch_tendency_t(const Dims &d, const FftPlan &plan, int B, 
         if (launches) ++*launches;
     }
     if (timer) timer->mark(STAGE_RING);
-    k2_ring<R><<<dim3(d.J2, B), kK2Threads, sm2, s>>>(f1, f2, d, plan, tw, tb.mu, tb.w, nscratch,
-                                                     static_cast<V2<R> *>(grid_store));
+    if constexpr (sizeof(R) == sizeof(float)) {
+        k2_ring_f32<<<dim3(d.J2, B), kK2Threads, ring_f32_smem_bytes(d.L, tb.ntwp), s>>>(
+            f1, f2, d, tb.plan16, tb.twp32, tb.ntwp, tb.mu, tb.w, static_cast<float2 *>(grid_store));
+    } else {
+        k2_ring<R><<<dim3(d.J2, B), kK2Threads, sm2, s>>>(f1, f2, d, plan, tw, tb.mu, tb.w, nscratch,
+                                                         static_cast<V2<R> *>(grid_store));
+    }
     if (timer) timer->mark(STAGE_ANALYSIS);
     if constexpr (sizeof(R) == sizeof(float)) {
         if (tc) {
