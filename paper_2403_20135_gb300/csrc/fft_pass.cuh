@@ -117,4 +117,77 @@ __device__ inline float2 *fft_passes(float2 *a, float2 *b, int nb, int Lp, const
     return src;
 }
 
+// ---------------------------------------------------------------------------
+// The same passes with the length, the pass radices and the batch fixed at
+// compile time (index arithmetic by shifts and multiplies) for the common
+// ring lengths.  plan16_radix reproduces the host factorisation: radix 16
+// while possible, then one of 8/4/2, then 3s.
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr int plan16_radix(int L, int p) {
+    int rest = L, q = 0;
+    while (rest % 16 == 0) {
+        if (q == p) return 16;
+        ++q;
+        rest /= 16;
+    }
+    const int rs[3] = {8, 4, 2};
+    for (int i = 0; i < 3; ++i)
+        if (rest % rs[i] == 0) {
+            if (q == p) return rs[i];
+            ++q;
+            rest /= rs[i];
+        }
+    while (rest % 3 == 0) {
+        if (q == p) return 3;
+        ++q;
+        rest /= 3;
+    }
+    return 0;
+}
+__host__ __device__ constexpr int plan16_npasses(int L) {
+    int p = 0;
+    while (plan16_radix(L, p) != 0) ++p;
+    return p;
+}
+
+template <int R, int L, int Ns, int NB>
+__device__ __forceinline__ void fft_pass_ct(const float2 *src, float2 *dst, const float2 *__restrict__ twp,
+                                            bool inv) {
+    constexpr int Lr = L / R, Lp = fft_padded_len(L), total = NB * Lr;
+    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+        const int bb = t / Lr, j = t - bb * Lr;
+        const float2 *in = src + bb * Lp;
+        float2 *out = dst + bb * Lp;
+        const int k = j % Ns;
+        float2 v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = in[fpad(j + r * Lr)];
+        if constexpr (Ns > 1) {
+#pragma unroll
+            for (int r = 1; r < R; ++r) {
+                float2 w = twp[(r - 1) * Ns + k];
+                if (inv) w.y = -w.y;
+                v[r] = cmul<float>(v[r], w);
+            }
+        }
+        dft<R>(v, inv);
+        const int base = (j - k) * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) out[fpad(base + r * Ns)] = v[r];
+    }
+}
+
+template <int L, int NB, int P = 0, int Ns = 1, int TOFF = 0>
+__device__ __forceinline__ float2 *fft_passes_ct(float2 *src, float2 *dst, const float2 *__restrict__ twp,
+                                                 bool inv) {
+    if constexpr (P == plan16_npasses(L)) {
+        return src;
+    } else {
+        constexpr int R = plan16_radix(L, P);
+        fft_pass_ct<R, L, Ns, NB>(src, dst, twp + TOFF, inv);
+        __syncthreads();
+        return fft_passes_ct<L, NB, P + 1, Ns * R, (Ns > 1 ? TOFF + (R - 1) * Ns : TOFF)>(dst, src, twp, inv);
+    }
+}
+
 }  // namespace sdc

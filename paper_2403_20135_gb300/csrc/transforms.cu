@@ -232,12 +232,14 @@ __host__ __device__ inline size_t ring_f32_smem_bytes(int L, int ntw) {
     return (10 * static_cast<size_t>(fft_padded_len(L)) + static_cast<size_t>(ntw)) * sizeof(float2);
 }
 
+// LC > 0: ring length fixed at compile time (LC == plan.L); 0: any length.
+template <int LC>
 __global__ void __launch_bounds__(256) k2_ring_f32(const float2 *__restrict__ f1, float2 *__restrict__ f2, Dims d,
                                                    FftPlan plan, const float2 *__restrict__ twp, int ntw,
                                                    const double *__restrict__ mu, const double *__restrict__ w,
                                                    float2 *__restrict__ gstore) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int L = plan.L, Lp = fft_padded_len(L);
+    const int L = LC > 0 ? LC : plan.L, Lp = fft_padded_len(L);
     float2 *X = reinterpret_cast<float2 *>(smem_raw);   // [5][Lp]
     float2 *S = X + 5 * Lp;                              // [5][Lp]
     float2 *TW = S + 5 * Lp;                             // [ntw]
@@ -261,7 +263,9 @@ __global__ void __launch_bounds__(256) k2_ring_f32(const float2 *__restrict__ f1
         if (m > 0) X[f * Lp + fpad(L - m)] = make_float2(n.x + sv.y, -n.y + sv.x);   // conj(n) + i conj(s)
     }
     __syncthreads();
-    const float2 *G = fft_passes(X, S, 4, Lp, plan, TW, true);
+    const float2 *G;
+    if constexpr (LC > 0) G = fft_passes_ct<LC, 4>(X, S, TW, true);
+    else G = fft_passes(X, S, 4, Lp, plan, TW, true);
 
     const double mun = mu[j2];
     const float cosl2 = float((1.0 - mun) * (1.0 + mun));
@@ -286,7 +290,9 @@ __global__ void __launch_bounds__(256) k2_ring_f32(const float2 *__restrict__ f1
         X[P_E * Lp + kp] = make_float2((uu.x * uu.x + vv.x * vv.x) * inv2c, (uu.y * uu.y + vv.y * vv.y) * inv2c);
     }
     __syncthreads();
-    const float2 *Y = fft_passes(X, S, 5, Lp, plan, TW, false);
+    const float2 *Y;
+    if constexpr (LC > 0) Y = fft_passes_ct<LC, 5>(X, S, TW, false);
+    else Y = fft_passes(X, S, 5, Lp, plan, TW, false);
 
     const double wj = w[j2];
     const float wt = float(wj / ((1.0 - mun) * (1.0 + mun)));
@@ -667,9 +673,13 @@ static cudaError_t configure(const Dims &d, const FftPlan &plan) {
     e = cudaFuncSetAttribute(k1_synthesis<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(static_cast<size_t>(d.T + 4) * 4 * sizeof(V2<R>)));
     if (e != cudaSuccess || sizeof(R) != sizeof(float)) return e;
-    e = cudaFuncSetAttribute(k2_ring_f32, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)ring_f32_smem_bytes(plan.L, plan.L));
-    if (e != cudaSuccess) return e;
+    const int smr = (int)ring_f32_smem_bytes(plan.L, plan.L);
+    for (const void *f : {(const void *)k2_ring_f32<0>, (const void *)k2_ring_f32<96>, (const void *)k2_ring_f32<192>,
+                          (const void *)k2_ring_f32<384>, (const void *)k2_ring_f32<768>,
+                          (const void *)k2_ring_f32<1536>}) {
+        e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smr);
+        if (e != cudaSuccess) return e;
+    }
     const int smw = (int)(2 * 10 * static_cast<size_t>(d.J2) * sizeof(float2));
     e = cudaFuncSetAttribute(k3_project_f32<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smw);
     if (e != cudaSuccess) return e;
@@ -713,8 +723,20 @@ static cudaError_t launch_tendency_t(const Dims &d, const FftPlan &plan, int B, 
     }
     if (timer) timer->mark(STAGE_RING);
     if constexpr (sizeof(R) == sizeof(float)) {
-        k2_ring_f32<<<dim3(d.J2, B), kK2Threads, ring_f32_smem_bytes(d.L, tb.ntwp), s>>>(
-            f1, f2, d, tb.plan16, tb.twp32, tb.ntwp, tb.mu, tb.w, static_cast<float2 *>(grid_store));
+        const dim3 g2(d.J2, B);
+        const size_t sm = ring_f32_smem_bytes(d.L, tb.ntwp);
+        float2 *gsr = static_cast<float2 *>(grid_store);
+#define SDC_RING_F32(LC) \
+    k2_ring_f32<LC><<<g2, kK2Threads, sm, s>>>(f1, f2, d, tb.plan16, tb.twp32, tb.ntwp, tb.mu, tb.w, gsr)
+        switch (d.L) {
+            case 96: SDC_RING_F32(96); break;
+            case 192: SDC_RING_F32(192); break;
+            case 384: SDC_RING_F32(384); break;
+            case 768: SDC_RING_F32(768); break;
+            case 1536: SDC_RING_F32(1536); break;
+            default: SDC_RING_F32(0); break;
+        }
+#undef SDC_RING_F32
     } else {
         k2_ring<R><<<dim3(d.J2, B), kK2Threads, sm2, s>>>(f1, f2, d, plan, tw, tb.mu, tb.w, nscratch,
                                                          static_cast<V2<R> *>(grid_store));
