@@ -610,6 +610,8 @@ static int project_f32_threads(int T) {
 //   T_E(div)_n  =  (1/a) [i m B^_n - n eps_{n+1} A^_{n+1} + (n+1) eps_n A^_{n-1}] + lambda_n E^_n
 //   T_E(Phi')_n = -(1/a) [i m C^_n + n eps_{n+1} D^_{n+1} - (n+1) eps_n D^_{n-1}]
 // ---------------------------------------------------------------------------
+// The arithmetic runs in R (FP32 in the mixed modes, like the rest of the
+// transform); the tendencies are stored in FP64.
 template <typename R>
 __global__ void k3_epilogue(const V2<R> *__restrict__ y, Dims d, const double *__restrict__ eps,
                             const double *__restrict__ lam, const int *__restrict__ coef_m,
@@ -623,33 +625,29 @@ __global__ void k3_epilogue(const V2<R> *__restrict__ y, Dims d, const double *_
     const int n = m + t;
     const int e = ext_offset(T, m) + t;
     const V2<R> *Y = y + static_cast<size_t>(b) * d.next * 5;
-    auto ld = [&](int row, int g) -> double2 {
-        const V2<R> v = Y[static_cast<size_t>(row) * 5 + g];
-        return make_double2(double(v.x), double(v.y));
-    };
-    const double2 z0 = make_double2(0.0, 0.0);
-    const double2 Ah = ld(e, P_A), Bh = ld(e, P_B), Ch = ld(e, P_C), Eh = ld(e, P_E);
-    const double2 Au = ld(e + 1, P_A), Bu = ld(e + 1, P_B), Du = ld(e + 1, P_D);
-    const double2 Al = t > 0 ? ld(e - 1, P_A) : z0;
-    const double2 Bl = t > 0 ? ld(e - 1, P_B) : z0;
-    const double2 Dl = t > 0 ? ld(e - 1, P_D) : z0;
-    const double cu = n * eps[e + 1];
-    const double cl = t > 0 ? (n + 1.0) * eps[e] : 0.0;
-    const double inv_a = 1.0 / d.a;
-    const double mm = m;
-    const double lm = lam[i];
-    double2 tz, td, tp;
+    auto ld = [&](int row, int g) -> V2<R> { return Y[static_cast<size_t>(row) * 5 + g]; };
+    const V2<R> z0 = mk<R>(0, 0);
+    const V2<R> Ah = ld(e, P_A), Bh = ld(e, P_B), Ch = ld(e, P_C), Eh = ld(e, P_E);
+    const V2<R> Au = ld(e + 1, P_A), Bu = ld(e + 1, P_B), Du = ld(e + 1, P_D);
+    const V2<R> Al = t > 0 ? ld(e - 1, P_A) : z0;
+    const V2<R> Bl = t > 0 ? ld(e - 1, P_B) : z0;
+    const V2<R> Dl = t > 0 ? ld(e - 1, P_D) : z0;
+    const R cu = R(n * eps[e + 1]);
+    const R cl = t > 0 ? R((n + 1.0) * eps[e]) : R(0);
+    const R inv_a = R(1.0 / d.a);
+    const R mm = R(m);
+    const R lm = R(lam[i]);
     // i m X = (-m X.y, m X.x)
-    tz.x = -inv_a * (-mm * Ah.y + cu * Bu.x - cl * Bl.x);
-    tz.y = -inv_a * (mm * Ah.x + cu * Bu.y - cl * Bl.y);
-    td.x = inv_a * (-mm * Bh.y - cu * Au.x + cl * Al.x) + lm * Eh.x;
-    td.y = inv_a * (mm * Bh.x - cu * Au.y + cl * Al.y) + lm * Eh.y;
-    tp.x = -inv_a * (-mm * Ch.y + cu * Du.x - cl * Dl.x);
-    tp.y = -inv_a * (mm * Ch.x + cu * Du.y - cl * Dl.y);
+    const R tzx = -inv_a * (-mm * Ah.y + cu * Bu.x - cl * Bl.x);
+    const R tzy = -inv_a * (mm * Ah.x + cu * Bu.y - cl * Bl.y);
+    const R tdx = inv_a * (-mm * Bh.y - cu * Au.x + cl * Al.x) + lm * Eh.x;
+    const R tdy = inv_a * (mm * Bh.x - cu * Au.y + cl * Al.y) + lm * Eh.y;
+    const R tpx = -inv_a * (-mm * Ch.y + cu * Du.x - cl * Dl.x);
+    const R tpy = -inv_a * (mm * Ch.x + cu * Du.y - cl * Dl.y);
     double2 *out = tend + b * tstride;
-    out[F_PHI * d.ncoef + i] = tp;
-    out[F_ZETA * d.ncoef + i] = tz;
-    out[F_DIV * d.ncoef + i] = td;
+    out[F_PHI * d.ncoef + i] = make_double2(double(tpx), double(tpy));
+    out[F_ZETA * d.ncoef + i] = make_double2(double(tzx), double(tzy));
+    out[F_DIV * d.ncoef + i] = make_double2(double(tdx), double(tdy));
 }
 
 // ---------------------------------------------------------------------------
