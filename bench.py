@@ -38,6 +38,13 @@ METRIC = "SDC steps/s at T255 M=4 K=5: FP64 vs mixed at fixed error; adjoint/fwd
 WORKLOAD = "t255"
 L2_FLUSH_BYTES = 512 << 20          # > 129 MB L2
 FP64_NOMINAL_TFLOPS = 1.25          # GB300 dense FP64 (nominal; no measured FP64 peak)
+# FP32 SIMT: 152 SMs x 128 FMA lanes x 2 flops x 2.07 GHz (maximum SM clock)
+FP32_SIMT_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# DRAM bytes (read + write) of one captured launch of the FP64 ring kernel with
+# a batch of 4 states at the bench workload (ncu capture summarised in
+# profiles/transforms_t255_fp64.md); the traffic is the batch's F1 input, so a
+# launch of b states moves b/4 of it.
+RING_FP64_TRAFFIC_B4 = 25.3e6 + 66.3e3
 
 
 def _peaks():
@@ -62,6 +69,15 @@ def stage_flops(wl, stage: str, batch: int) -> float:
     if stage == "ring":               # 9 complex FFTs (5 L log2 L) + products per ring pair
         return (9 * 5.0 * L * np.log2(L) + 60.0 * L) * J2 * batch
     raise ValueError(stage)
+
+
+def sweep_flops(wl) -> float:
+    """FP64 flops of one all-node sweep: per mode and node m the quadrature
+    (6 real components x M terms x 2 flops), the right side and the 2x2 solve
+    (about 24 flops), plus forming L_g u_j + T_E(u_j) (8 flops per node)."""
+    nc = (wl.T + 1) * (wl.T + 2) // 2
+    M = wl.nodes
+    return nc * (12.0 * M * M + 24.0 * M + 8.0 * M)
 
 
 def sweep_bytes(wl, all_nodes: bool) -> float:
@@ -306,9 +322,19 @@ def cuda_arm(args, rank: int, world: int):
     launches_per_step = prof[dom]["launches_per_step"]
     flops_per_launch = stage_flops(wl, dom, nodes_per_step) / launches_per_step
     achieved_tf = flops_per_launch / (prof[dom]["ms_per_launch"] * 1e-3) / 1e12
+    traffic = RING_FP64_TRAFFIC_B4 * (nodes_per_step / launches_per_step) / 4.0 if dom == "ring" else None
     roofline = {"bound": "alu", "achieved": achieved_tf, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved_tf / FP64_NOMINAL_TFLOPS, "traffic": None, "kernel": dom,
+                "frac": achieved_tf / FP64_NOMINAL_TFLOPS, "traffic": traffic, "kernel": dom,
                 "peak_kind": "nominal FP64 (no measured FP64 peak)"}
+    # the sweep kernel (FP64 in every mode): FP64 flops and the bytes it moves
+    sw_ms = prof["sweep"]["ms_per_launch"]
+    sw_all = (K - 1) / K          # share of sweeps that update all M nodes
+    sw_bytes = sw_all * sweep_bytes(wl, True) + (1 - sw_all) * sweep_bytes(wl, False)
+    sw_flops = sweep_flops(wl) * (sw_all + (1 - sw_all) / M)
+    roofline_sweep = {"bound": "alu", "achieved": sw_flops / (sw_ms * 1e-3) / 1e12, "peak": FP64_NOMINAL_TFLOPS,
+                      "unit": "TFLOP/s", "frac": sw_flops / (sw_ms * 1e-3) / 1e12 / FP64_NOMINAL_TFLOPS,
+                      "hbm_gbs": sw_bytes / (sw_ms * 1e-3) / 1e9, "hbm_peak_gbs": peaks["hbm_gbs"],
+                      "hbm_frac": sw_bytes / (sw_ms * 1e-3) / 1e9 / peaks["hbm_gbs"], "kernel": "sweep"}
 
     # end to end through host buffers
     host_state = u0.cpu().pin_memory()
@@ -351,11 +377,26 @@ def cuda_arm(args, rank: int, world: int):
             sm.run(am, nh)
             sm.sync()
             err = rel(am, a64)
+            mdom = max(("synthesis", "ring", "analysis"), key=lambda k: mprof[k]["ms_per_launch"])
+            mfl = stage_flops(wl, mdom, nodes_per_step) / mprof[mdom]["launches_per_step"]
+            mach = mfl / (mprof[mdom]["ms_per_launch"] * 1e-3) / 1e12
             mixed[name] = {"value": world * args.steps / (sum(tm) * 1e-3), "unit": "steps/s",
                            "ms_per_step": sum(tm) / args.steps, "stages": mprof,
                            "rel_l2_vs_fp64": dict(zip(fields, map(float, err))),
-                           "fixed_error": bool(np.all(err < edisc))}
+                           "fixed_error": bool(np.all(err < edisc)),
+                           "roofline": {"bound": "alu", "kernel": mdom, "achieved": mach,
+                                        "peak": FP32_SIMT_TFLOPS, "unit": "TFLOP/s",
+                                        "frac": mach / FP32_SIMT_TFLOPS,
+                                        "peak_kind": "nominal FP32 SIMT (algorithmic flops; the tensor-core "
+                                                     "modes count their contractions at this rate too)"}}
             sm.close()
+        ok = [k for k in ("fp32", "bf16x3", "bf16x6") if mixed[k]["fixed_error"]]
+        if ok:
+            best = max(ok, key=lambda k: mixed[k]["value"])
+            mixed["best_at_fixed_error"] = {"mode": best, "value": mixed[best]["value"], "unit": "steps/s",
+                                            "speedup_vs_fp64": mixed[best]["value"] / steps_per_s}
+        else:
+            mixed["best_at_fixed_error"] = None
 
     adjoint = None
     if not args.no_adjoint:
@@ -377,6 +418,7 @@ def cuda_arm(args, rank: int, world: int):
                        "l2": "flushed (512 MiB write) before every timed step",
                        "parallelism": f"replicas x{world}"},
             "e2e": e2e, "gpu_launches": int(l1 - l0), "clocks": clocks, "roofline": roofline,
+            "roofline_sweep": roofline_sweep,
             "stages": prof, "mixed": mixed,
             "adjoint_fwd_ratio": adjoint["t255"]["step_ratio"] if adjoint else None, "adjoint": adjoint,
             "cpu_baseline": cpu,
