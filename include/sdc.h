@@ -77,9 +77,25 @@ typedef enum {
      * The paper always runs K = M; for k > M the value is
      * SDC_QDELTA_CLAMPED (default): q(k) = min(k, M), or
      * SDC_QDELTA_LITERAL: q(k) = k. */
-    SDC_OPT_QDELTA_RULE = 1
+    SDC_OPT_QDELTA_RULE = 1,
+    /* The integrator sdc_step / sdc_run / sdc_profile_step advance with:
+     * SDC_METHOD_DSDC (default): diagonal IMEX SDC, Algorithm 2, Eq. (7);
+     * SDC_METHOD_SERIAL_SDC: serial IMEX SDC, Algorithm 1 with Eq. (6)
+     *   (same nodes, collocation matrix and K; node updates sequential, each
+     *   followed by one tendency evaluation: K M evaluations and K M solves
+     *   per step);
+     * SDC_METHOD_IMEX2: IMEX-o2 of Sec. 3.2, Strang splitting with
+     *   Crank-Nicolson half steps on L_g around one Heun step on T_E
+     *   (2 evaluations, 2 solves per step).
+     * The reference integrators run in the context's precision for T_E and FP64
+     * elsewhere; residual output and the adjoint calls (except
+     * sdc_tendency_adjoint) need SDC_METHOD_DSDC and return SDC_EUNSUPPORTED
+     * otherwise.  Selecting a reference integrator the first time allocates
+     * max(2 nodes, 4) extra states (SDC_ECUDA / SDC_ENOMEM on failure). */
+    SDC_OPT_METHOD = 2
 } sdc_option;
 enum { SDC_QDELTA_CLAMPED = 0, SDC_QDELTA_LITERAL = 1 };
+enum { SDC_METHOD_DSDC = 0, SDC_METHOD_SERIAL_SDC = 1, SDC_METHOD_IMEX2 = 2 };
 
 /* Create a solver for truncation T on an nlat x nlon Gauss grid with M
  * Radau-right collocation nodes (tau_M = 1, Sec. 4.2), K sweeps per step

@@ -46,6 +46,7 @@ struct sdc_ctx {
     int T = 0, J = 0, L = 0, M = 0, K = 0;
     int precision = SDC_FP64;
     int qdelta_rule = SDC_QDELTA_CLAMPED;
+    int method = SDC_METHOD_DSDC;
     double dt = 0.0;
     sdc_phys phys{};
     Dims d{};
@@ -89,6 +90,7 @@ struct sdc_ctx {
 
     cudaGraphExec_t graph[2] = {nullptr, nullptr};   // [with residuals]
     int graph_launches[2] = {0, 0};
+    double2 *alt = nullptr;              // reference integrators: extra node iterates
     cudaGraphExec_t graph_retape = nullptr, graph_adjoint = nullptr;
     int retape_launches = 0, adjoint_launches = 0;
     long long n_explicit = 0, n_solve = 0, n_launch = 0;
@@ -108,7 +110,7 @@ void free_ctx(sdc_ctx *c) {
                     c->tw32, c->twp32, c->un, c->U, c->E, c->E0, c->f1, c->f2, c->f3, c->resid_part, c->resid,
                     c->gstore, c->ub, c->eb, c->ubn, c->ubnext, c->eb0, c->snaps, c->phigrid, c->rgrid,
                     c->loss_part, c->loss_dev, c->tc_a3, c->tc_a1, c->tc_t3, c->tc_t1, c->tc_err, c->den,
-                    c->tc_wb, c->tc_cb, c->tc_cboff};
+                    c->tc_wb, c->tc_cb, c->tc_cboff, c->alt};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->cap) cudaStreamDestroy(c->cap);
@@ -178,11 +180,86 @@ cudaError_t tendency(sdc_ctx *c, int B, const double2 *states, long long sstride
                            grid_store, use_tc ? &c->tc : nullptr);
 }
 
-// Enqueue one step u_n -> u_n (in place on c->un), Algorithm 2.
+// Serial IMEX SDC step (Algorithm 1, Eq. (6)) in place on c->un: node by
+// node, each node update followed by the tendency of the new node state
+// (except after the last node of the last sweep).  Iterate 0 is u_n and
+// T_E(u_n) for every node; iterate k >= 1 lives in slot k % 2 (U/E, alt).
+cudaError_t enqueue_serial(sdc_ctx *c, cudaStream_t s, int *launches, StageTimer *timer) {
+    const long long se = c->state_elems();
+    const int M = c->M, K = c->K;
+    cudaError_t e = tendency(c, 1, c->un, se, c->E0, se, s, launches, timer);
+    if (e != cudaSuccess) return e;
+    SerialNodeParams p{};
+    p.un = c->un;
+    p.lam = c->lam;
+    p.ncoef = c->d.ncoef;
+    p.dt = c->dt;
+    p.phibar = c->phys.gravity * c->phys.mean_depth;
+    for (int j = 0; j < M; ++j) p.dtau[j] = c->tau[j] - (j > 0 ? c->tau[j - 1] : 0.0);
+    double2 *su[2] = {c->U, c->alt}, *sv[2] = {c->E, c->alt + M * se};
+    for (int k = 0; k < K; ++k) {
+        p.uk = k == 0 ? c->un : su[k % 2];
+        p.ek = k == 0 ? c->E0 : sv[k % 2];
+        p.kstride = k == 0 ? 0 : se;
+        double2 *nu = su[(k + 1) % 2], *ne = sv[(k + 1) % 2];
+        p.uk1 = nu;
+        p.ek1 = ne;
+        p.k1stride = se;
+        for (int m = 0; m < M; ++m) {
+            const bool final = (k == K - 1 && m == M - 1);
+            p.m = m;
+            for (int j = 0; j < M; ++j) p.Q[j] = c->Q[m * M + j];
+            p.out = final ? c->un : nu + m * se;
+            if (timer) timer->mark(STAGE_SWEEP);
+            e = launch_serial_node(p, M, s, launches);
+            if (e != cudaSuccess) return e;
+            if (!final) {
+                e = tendency(c, 1, nu + m * se, se, ne + m * se, se, s, launches, timer);
+                if (e != cudaSuccess) return e;
+            }
+        }
+    }
+    return cudaSuccess;
+}
+
+// IMEX-o2 step (Sec. 3.2) in place on c->un: CN half step, Heun step on
+// T_E, CN half step (a, b, T_E(a), T_E(b) in alt).
+cudaError_t enqueue_imex2(sdc_ctx *c, cudaStream_t s, int *launches, StageTimer *timer) {
+    const long long se = c->state_elems();
+    const int nc = c->d.ncoef;
+    const double phibar = c->phys.gravity * c->phys.mean_depth, h = 0.5 * c->dt;
+    double2 *a = c->alt, *b = c->alt + se, *ea = c->alt + 2 * se, *eb = c->alt + 3 * se;
+    if (timer) timer->mark(STAGE_SWEEP);
+    cudaError_t e = launch_imex2_cn(c->un, nullptr, nullptr, 0.0, h, c->lam, phibar, nc, a, s, launches);
+    if (e == cudaSuccess) e = tendency(c, 1, a, se, ea, se, s, launches, timer);
+    if (e == cudaSuccess && timer) timer->mark(STAGE_SWEEP);
+    if (e == cudaSuccess) e = launch_imex2_euler(a, ea, c->dt, nc, b, s, launches);
+    if (e == cudaSuccess) e = tendency(c, 1, b, se, eb, se, s, launches, timer);
+    if (e == cudaSuccess && timer) timer->mark(STAGE_SWEEP);
+    if (e == cudaSuccess) e = launch_imex2_cn(a, ea, eb, 0.5 * c->dt, h, c->lam, phibar, nc, c->un, s, launches);
+    return e;
+}
+
+// tendency evaluations and implicit solves of one step of the selected method
+long long evals_per_step(const sdc_ctx *c) {
+    if (c->method == SDC_METHOD_SERIAL_SDC) return static_cast<long long>(c->K) * c->M;
+    if (c->method == SDC_METHOD_IMEX2) return 2;
+    return 1 + static_cast<long long>(c->K - 1) * c->M;
+}
+long long solves_per_step(const sdc_ctx *c) {
+    if (c->method == SDC_METHOD_SERIAL_SDC) return static_cast<long long>(c->K) * c->M;
+    if (c->method == SDC_METHOD_IMEX2) return 2;
+    return static_cast<long long>(c->K - 1) * c->M + 1;
+}
+
+// Enqueue one step u_n -> u_n (in place on c->un), Algorithm 2 (or the
+// selected reference integrator).
 // With store_grid (the retape of the adjoint) every tendency evaluation also
 // records its grid fields: slot 0 for E0, slots 1 + k M + j for sweep k+1, node j.
 cudaError_t enqueue_step(sdc_ctx *c, cudaStream_t s, bool with_resid, int *launches,
                          StageTimer *timer = nullptr, bool store_grid = false) {
+    if (c->method == SDC_METHOD_SERIAL_SDC) return enqueue_serial(c, s, launches, timer);
+    if (c->method == SDC_METHOD_IMEX2) return enqueue_imex2(c, s, launches, timer);
     const long long se = c->state_elems();
     const int M = c->M, K = c->K;
     cudaError_t e;
@@ -453,8 +530,8 @@ int run_steps(sdc_ctx *c, int nsteps, bool with_resid) {
     int st = ensure_graph(c, with_resid);
     if (st != SDC_OK) return st;
     for (int i = 0; i < nsteps; ++i) SDC_CUDA(cudaGraphLaunch(c->graph[with_resid ? 1 : 0], c->stream));
-    c->n_explicit += static_cast<long long>(nsteps) * (1 + (c->K - 1) * c->M);
-    c->n_solve += static_cast<long long>(nsteps) * ((c->K - 1) * c->M + 1);
+    c->n_explicit += static_cast<long long>(nsteps) * evals_per_step(c);
+    c->n_solve += static_cast<long long>(nsteps) * solves_per_step(c);
     c->n_launch += static_cast<long long>(nsteps) * c->graph_launches[with_resid ? 1 : 0];
     return SDC_OK;
 }
@@ -679,6 +756,21 @@ int sdc_set_option(sdc_ctx *c, int key, int value) {
         }
         return SDC_OK;
     }
+    if (key == SDC_OPT_METHOD) {
+        if (value != SDC_METHOD_DSDC && value != SDC_METHOD_SERIAL_SDC && value != SDC_METHOD_IMEX2)
+            return fail(SDC_EINVAL, "bad method");
+        if (value != SDC_METHOD_DSDC && !c->alt) {
+            const size_t n = static_cast<size_t>(c->M > 2 ? 2 * c->M : 4) * c->state_elems();
+            SDC_CUDA(cudaMalloc(&c->alt, n * sizeof(double2)));
+        }
+        if (value != c->method) {
+            SDC_CUDA(cudaStreamSynchronize(c->stream));
+            c->method = value;
+            for (auto &g : c->graph)
+                if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+        }
+        return SDC_OK;
+    }
     return fail(SDC_EINVAL, "unknown option");
 }
 
@@ -686,6 +778,7 @@ int sdc_ncoef(const sdc_ctx *c) { return c ? c->d.ncoef : -1; }
 
 int sdc_step(sdc_ctx *c, const void *in, void *out, double *resid_out) {
     if (!c || !in || !out) return fail(SDC_EINVAL, "NULL argument");
+    if (resid_out && c->method != SDC_METHOD_DSDC) return fail(SDC_EUNSUPPORTED, "residuals need the dSDC method");
     const size_t sbytes = 3ULL * c->d.ncoef * sizeof(double2);
     SDC_CUDA(cudaMemcpyAsync(c->un, in, sbytes, cudaMemcpyDeviceToDevice, c->stream));
     int st = run_steps(c, 1, resid_out != nullptr);
@@ -785,6 +878,7 @@ int sdc_tendency_adjoint(sdc_ctx *c, const void *states, const void *abar, void 
 
 int sdc_step_adjoint(sdc_ctx *c, const void *state_n, const void *ubar_next, void *ubar_n) {
     if (!c || !state_n || !ubar_next || !ubar_n) return fail(SDC_EINVAL, "NULL argument");
+    if (c->method != SDC_METHOD_DSDC) return fail(SDC_EUNSUPPORTED, "the adjoint is built for the dSDC method");
     const size_t sbytes = 3ULL * c->d.ncoef * sizeof(double2);
     SDC_CUDA(cudaMemcpyAsync(c->un, state_n, sbytes, cudaMemcpyDeviceToDevice, c->stream));
     SDC_CUDA(cudaMemcpyAsync(c->ubnext, ubar_next, sbytes, cudaMemcpyDeviceToDevice, c->stream));
@@ -797,6 +891,7 @@ int sdc_step_adjoint(sdc_ctx *c, const void *state_n, const void *ubar_next, voi
 static int adjoint_common(sdc_ctx *c, const void *state0, int nsteps, int nsnapshots, const void *ubar_final,
                           const double *h_target, double *loss_out, void *ubar_initial) {
     if (!c || !state0 || !ubar_initial) return fail(SDC_EINVAL, "NULL argument");
+    if (c->method != SDC_METHOD_DSDC) return fail(SDC_EUNSUPPORTED, "the adjoint is built for the dSDC method");
     if (nsteps < 0 || nsteps > 4096) return fail(SDC_EINVAL, "nsteps must be in [0, 4096]");
     if (nsnapshots < 1 || nsnapshots > kMaxSnapshots) return fail(SDC_EINVAL, "nsnapshots must be in [1, 32]");
     const size_t sbytes = 3ULL * c->d.ncoef * sizeof(double2);
@@ -880,8 +975,8 @@ int sdc_profile_step(sdc_ctx *c, void *state, double *ms, int *launches) {
             ms[tm.cls[i]] += t;
             launches[tm.cls[i]] += 1;
         }
-        c->n_explicit += 1 + (c->K - 1) * c->M;
-        c->n_solve += (c->K - 1) * c->M + 1;
+        c->n_explicit += evals_per_step(c);
+        c->n_solve += solves_per_step(c);
         c->n_launch += nl;
     }
     for (int i = 0; i <= StageTimer::kMax; ++i) cudaEventDestroy(tm.ev[i]);

@@ -68,6 +68,23 @@ struct SweepParams {
     double alpha[kMaxNodes];      // dt * q^Delta_{m,m}
 };
 
+// One node update of serial IMEX SDC (Algorithm 1, Eq. (6)).
+struct SerialNodeParams {
+    const double2 *un;            // u_n
+    const double2 *uk, *ek;       // u_j^k, E_j^k at + j * kstride (kstride 0: every node is u_n)
+    long long kstride;
+    const double2 *uk1, *ek1;     // u_j^{k+1}, E_j^{k+1} for j < m at + j * k1stride
+    long long k1stride;
+    double2 *out;                 // u_m^{k+1}
+    const double *lam;            // n(n+1)/a^2 [ncoef]
+    int ncoef;
+    int m;
+    double dt;
+    double phibar;
+    double Q[kMaxNodes];          // row m of the collocation matrix
+    double dtau[kMaxNodes];       // tau_1, tau_2 - tau_1, ...
+};
+
 // Per-kernel CUDA-event timing of a directly launched (not graph) step:
 // mark(c) records an event and tags the kernel launched next with class c.
 enum {
@@ -229,6 +246,15 @@ cudaError_t launch_height_loss(const Dims &d, const FftPlan &plan, const double 
                                double inv_g, double H, double *rgrid, double *part, double *loss,
                                double2 *seed_phi, const double *pbar64, const double2 *tw64, double2 *fbuf,
                                cudaStream_t s);
+
+// ---- reference integrators (integrators.cu) ------------------------------
+cudaError_t launch_serial_node(const SerialNodeParams &p, int M, cudaStream_t s, int *launches);
+// out = CN(h) (a + s1 (e1 + e2)); e1, e2 nullable
+cudaError_t launch_imex2_cn(const double2 *a, const double2 *e1, const double2 *e2, double s1, double h,
+                            const double *lam, double phibar, int ncoef, double2 *out, cudaStream_t s,
+                            int *launches);
+cudaError_t launch_imex2_euler(const double2 *a, const double2 *e, double dt, int ncoef, double2 *b, cudaStream_t s,
+                               int *launches);
 
 size_t ring_smem_bytes(int L, int elem_bytes, int *scratch_arrays);
 cudaError_t configure_transform_kernels(const Dims &d, const FftPlan &plan, bool fp32);

@@ -26,7 +26,7 @@ class Solver:
     def __init__(self, T: int, nlat: int, nlon: int, nodes: int, sweeps: int, dt: float,
                  radius: float, omega: float, gravity: float, mean_depth: float,
                  precision: int = _lib.SDC_FP64, qdelta_rule: int = _lib.SDC_QDELTA_CLAMPED,
-                 stream: torch.cuda.Stream | None = None):
+                 method: int = _lib.SDC_METHOD_DSDC, stream: torch.cuda.Stream | None = None):
         self.lib = _lib.load()
         self.T, self.nlat, self.nlon, self.nodes, self.sweeps, self.dt = T, nlat, nlon, nodes, sweeps, dt
         self.phys = _lib.SdcPhys(radius, omega, gravity, mean_depth)
@@ -40,6 +40,14 @@ class Solver:
         if qdelta_rule != _lib.SDC_QDELTA_CLAMPED:
             _lib.check(self.lib.sdc_set_option(h, _lib.SDC_OPT_QDELTA_RULE, qdelta_rule), "sdc_set_option")
         self.ncoef = self.lib.sdc_ncoef(h)
+        self.method = _lib.SDC_METHOD_DSDC
+        if method != _lib.SDC_METHOD_DSDC:
+            self.set_method(method)
+
+    def set_method(self, method: int):
+        """Integrator for step/run: SDC_METHOD_DSDC, SDC_METHOD_SERIAL_SDC or SDC_METHOD_IMEX2."""
+        _lib.check(self.lib.sdc_set_option(self.h, _lib.SDC_OPT_METHOD, method), "sdc_set_option")
+        self.method = method
 
     @classmethod
     def for_workload(cls, wl, precision: int = _lib.SDC_FP64, **kw):
