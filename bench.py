@@ -431,6 +431,60 @@ def cuda_arm(args, rank: int, world: int):
 PRECISIONS = {"fp64": 0, "fp32": 1, "bf16x3": 2, "bf16x6": 3}
 
 
+def work_precision(hours: float):
+    """Synthetic work-precision study on the bench workload's grid and initial
+    state: error after a fixed simulated time against GPU time for dSDC (FP64,
+    FP32), serial IMEX SDC (FP64) and IMEX-o2 (FP64) over a time-step sweep.
+    Reference: dSDC FP64 at 1/8 of the smallest step.  One JSON line."""
+    import torch
+
+    from paper_2403_20135_gb300 import (SDC_FP64, SDC_METHOD_DSDC, SDC_METHOD_IMEX2, SDC_METHOD_SERIAL_SDC,
+                                        SDC_MIXED_FP32, Solver)
+    wl = si.WORKLOADS[WORKLOAD]
+    horizon = hours * 3600.0
+    cases = [("dsdc", SDC_METHOD_DSDC, SDC_FP64, (900.0, 600.0, 450.0, 300.0, 150.0, 75.0)),
+             ("dsdc", SDC_METHOD_DSDC, SDC_MIXED_FP32, (900.0, 600.0, 450.0, 300.0, 150.0, 75.0)),
+             ("serial_sdc", SDC_METHOD_SERIAL_SDC, SDC_FP64, (900.0, 600.0, 300.0, 150.0, 75.0)),
+             ("imex2", SDC_METHOD_IMEX2, SDC_FP64, (300.0, 150.0, 75.0, 37.5, 18.75))]
+
+    def make(dt, method, prec):
+        return Solver(wl.T, wl.nlat, wl.nlon, wl.nodes, wl.sweeps, dt, si.RADIUS, si.OMEGA, si.GRAVITY,
+                      si.MEAN_DEPTH, precision=prec, method=method)
+
+    s0 = make(wl.dt, SDC_METHOD_DSDC, SDC_FP64)
+    u0 = s0.initial_state(wl)
+    s0.close()
+    dt_ref = 75.0 / 8
+    sr = make(dt_ref, SDC_METHOD_DSDC, SDC_FP64)
+    ref = u0.clone()
+    sr.run(ref, int(round(horizon / dt_ref)))
+    sr.sync()
+    sr.close()
+    fields = ("phi", "zeta", "div")
+    rows = []
+    for name, method, prec, dts in cases:
+        for dt in dts:
+            n = int(round(horizon / dt))
+            s = make(dt, method, prec)
+            x = u0.clone()
+            s.run(x, 1)                       # graph capture and warm-up outside the timing
+            x = u0.clone()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            s.run(x, n)
+            e1.record()
+            torch.cuda.synchronize()
+            err = ((x - ref).abs().pow(2).sum(1) / ref.abs().pow(2).sum(1)).sqrt().cpu().numpy()
+            rows.append({"method": name, "precision": "fp64" if prec == SDC_FP64 else "fp32", "dt": dt,
+                         "steps": n, "gpu_ms": e0.elapsed_time(e1),
+                         "rel_l2": dict(zip(fields, map(float, err))),
+                         "finite": bool(np.all(np.isfinite(err)))})
+            s.close()
+    print(json.dumps({"work_precision": rows, "workload": wl.describe(), "simulated_hours": hours,
+                      "reference": f"dSDC FP64, dt = {dt_ref} s"}), flush=True)
+
+
 def profile_run(name: str, steps: int):
     """A few untimed steps of one precision mode (the command profilers wrap)."""
     from paper_2403_20135_gb300 import Solver
@@ -455,7 +509,12 @@ def main():
     ap.add_argument("--horizon", type=int, default=500, help="steps of the fixed-error comparison")
     ap.add_argument("--profile-run", choices=sorted(PRECISIONS), default=None,
                     help="only run --steps untimed steps of this precision (for profilers)")
+    ap.add_argument("--work-precision", type=float, default=None, metavar="HOURS",
+                    help="only run the work-precision study over this simulated time")
     args = ap.parse_args()
+    if args.work_precision:
+        work_precision(args.work_precision)
+        return
     if args.profile_run:
         profile_run(args.profile_run, args.steps)
         return
