@@ -142,6 +142,7 @@ DeviceTables tables(const sdc_ctx *c) {
     tb.syn = c->syn;
     tb.row_m = c->row_m;
     tb.coef_m = c->coef_m;
+    tb.err = c->tc_err;
     tb.plan16 = c->plan16;
     tb.twp32 = c->twp32;
     tb.ntwp = c->ntwp;
@@ -171,6 +172,7 @@ cudaError_t tendency(sdc_ctx *c, int B, const double2 *states, long long sstride
     tb.syn = c->syn;
     tb.row_m = c->row_m;
     tb.coef_m = c->coef_m;
+    tb.err = c->tc_err;
     tb.plan16 = c->plan16;
     tb.twp32 = c->twp32;
     tb.ntwp = c->ntwp;
@@ -644,6 +646,8 @@ int sdc_create(sdc_ctx **out, int T, int J, int L, int M, int K, double dt, cons
         SDC_TRY(upload(&c->pbar, table.data(), table.size()));
         SDC_TRY(upload(&c->tw, tw.data(), tw.size()));
     }
+    SDC_TRY(cudaMalloc(&c->tc_err, sizeof(int)));
+    SDC_TRY(cudaMemset(c->tc_err, 0, sizeof(int)));
     if (precision == SDC_MIXED_BF16X3 || precision == SDC_MIXED_BF16X6) {
         std::vector<uint16_t> a3, a1;
         std::vector<TcTile3> t3;
@@ -655,8 +659,6 @@ int sdc_create(sdc_ctx **out, int T, int J, int L, int M, int K, double dt, cons
         SDC_TRY(upload(&c->tc_a1, a1.data(), a1.size()));
         SDC_TRY(upload(&c->tc_t3, t3.data(), t3.size()));
         SDC_TRY(upload(&c->tc_t1, t1.data(), t1.size()));
-        SDC_TRY(cudaMalloc(&c->tc_err, sizeof(int)));
-        SDC_TRY(cudaMemset(c->tc_err, 0, sizeof(int)));
         SDC_TRY(configure_tc_kernels());
         c->tc.a3 = c->tc_a3;
         c->tc.a1 = c->tc_a1;

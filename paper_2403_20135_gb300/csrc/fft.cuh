@@ -70,11 +70,16 @@ __device__ __forceinline__ void fft_stage(const V2<R> *src, V2<R> *dst, int nb, 
             const int k = pow2 ? (j & (Ns - 1)) : (j % Ns);
             V2<R> v[RADIX];
             v[0] = in[j];
+            if (Ns == 1) {                       // first stage: every twiddle is 1
 #pragma unroll
-            for (int r = 1; r < RADIX; ++r) {
-                V2<R> w = tw[r * k * tws];
-                if (inv) w.y = -w.y;
-                v[r] = cmul<R>(in[j + r * Lr], w);
+                for (int r = 1; r < RADIX; ++r) v[r] = in[j + r * Lr];
+            } else {
+#pragma unroll
+                for (int r = 1; r < RADIX; ++r) {
+                    V2<R> w = tw[r * k * tws];
+                    if (inv) w.y = -w.y;
+                    v[r] = cmul<R>(in[j + r * Lr], w);
+                }
             }
             butterfly<R, RADIX>(v, inv);
             const int base = (j - k) * RADIX + k;

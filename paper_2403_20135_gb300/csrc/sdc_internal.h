@@ -115,6 +115,7 @@ struct DeviceTables {
     const double *syn;     // wind synthesis factors (c0, c1, c2) [next][3]
     const int *row_m;      // order m of each extended row [next]
     const int *coef_m;     // order m of each packed coefficient [ncoef]
+    int *err;              // device flag set by a kernel whose bounded wait expired
     FftPlan plan16;        // FP32 ring: passes of radix 16, then 8/4/2, then 3
     const float2 *twp32;   // FP32 ring: per-pass twiddles of plan16 (after the first pass)
     int ntwp;
@@ -152,7 +153,7 @@ struct SweepAdjParams {
 // BF16 pieces, tile by tile and chunk by chunk in the canonical K-major
 // shared-memory layout (8 x 8 core matrices, [row block][k block][8][8]), so
 // one chunk of one piece is one contiguous bulk copy.
-constexpr int kTcChunkKB = 8;     // k blocks (of 8 elements) per chunk
+constexpr int kTcChunkKB = 4;     // k blocks (of 8 elements) per chunk
 struct TcTile3 {                  // analysis: rows q0..q0+nrows of group (m, p), K = latitudes
     int m, p, q0, nrows, nrb;
     long long aoff;               // element offset of chunk 0 in each piece table

@@ -23,6 +23,7 @@
 
 #include <cstdint>
 
+#include "async_copy.cuh"
 #include "sdc_internal.h"
 
 namespace sdc {
@@ -30,13 +31,7 @@ namespace sdc {
 namespace {
 
 constexpr int kTcThreads = 128;
-constexpr int kTcMaxPieces = 3;
 constexpr int kTileRows = 128;                       // M of every MMA
-constexpr uint32_t kWaitLimit = 1u << 22;
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
 
 // Shared-memory matrix descriptor (tcgen05), no swizzle: start address,
 // leading byte offset = distance of core matrices along K, stride byte offset
@@ -64,32 +59,6 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t ad, uint64_t bd
 __device__ __forceinline__ void mma_commit(uint64_t *mbar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
         smem_u32(mbar)));
-}
-
-__device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t phase) {
-    uint32_t done = 0;
-    for (uint32_t it = 0; it < kWaitLimit && !done; ++it) {
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(done)
-            : "r"(smem_u32(mbar)), "r"(phase));
-    }
-    return done != 0;
-}
-
-__device__ __forceinline__ void bulk_copy(void *dst, const void *src, uint32_t bytes, uint64_t *mbar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(smem_u32(mbar))
-        : "memory");
-}
-
-__device__ __forceinline__ void expect_tx(uint64_t *mbar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)), "r"(bytes)
-                 : "memory");
 }
 
 // x = h_0 + h_1 (+ h_2): each piece the BF16 rounding of the remaining FP32
@@ -131,7 +100,7 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float *v) {
 // partial tile hold stale finite data: they only feed accumulator rows the
 // epilogue never reads.  K padding is zero in both operands' global copies.
 struct TcSmem {
-    uint64_t mbar_ld;
+    uint64_t mbar_ld[2];
     uint64_t mbar_mma;
     uint32_t tmem;
     int abort;
@@ -141,9 +110,11 @@ constexpr size_t kCtrlBytes = 128;
 
 __host__ __device__ inline int b_elems(int nbc) { return nbc * kTcChunkKB * 64; }
 
-size_t tc_smem_bytes(int np, int nbc) {
-    return kCtrlBytes + static_cast<size_t>(np) * (kAElems + b_elems(nbc)) * sizeof(__nv_bfloat16);
+// two operand stages of NP pieces each
+__host__ __device__ inline size_t tc_stage_elems(int np, int nbc) {
+    return static_cast<size_t>(np) * (kAElems + b_elems(nbc));
 }
+size_t tc_smem_bytes(int np, int nbc) { return kCtrlBytes + 2 * tc_stage_elems(np, nbc) * sizeof(__nv_bfloat16); }
 
 // The MMAs of one chunk: kbc k-blocks, K step 16 (two core matrices).
 template <int NP>
@@ -165,52 +136,104 @@ __device__ __forceinline__ void issue_chunk(const __nv_bfloat16 *abase, const __
     }
 }
 
-// Thread 0 only: for every chunk of kb_total k blocks, bulk-copy the NP
-// pieces of the A chunk (a_rb row blocks, chunks of a_rb * kbc core
-// matrices back to back from a_src) and of the B chunk (the first nbc col
-// blocks of a chunk of b_cb col blocks from b_src), then issue its MMAs and
-// wait for them before the next copy overwrites the operands.  Returns false
-// (flag set) if a bounded wait expired; it then waits once more, bounded,
-// for work still in flight.
+// Operands of one tile: A chunks (a_rb row blocks, chunks of a_rb * kbc core
+// matrices back to back from a_src, pieces a_piece apart) and B chunks (the
+// first nbc col blocks of chunks of b_cb col blocks from b_src, pieces
+// b_piece apart), kb_total k blocks in chunks of kTcChunkKB.
+struct TileOperands {
+    const uint16_t *a_src;
+    long long a_piece;
+    int a_rb;
+    const uint16_t *b_src;
+    long long b_piece;
+    int b_cb, nbc, N, kb_total;
+};
+
+// Thread 0: bulk-copy chunk c into operand stage st (mbar_ld[st]).
 template <int NP>
-__device__ bool run_chunks(TcSmem &sm, __nv_bfloat16 *sa, __nv_bfloat16 *sb, int belems, const uint16_t *a_src,
-                           long long a_piece, int a_rb, const uint16_t *b_src, long long b_piece, int b_cb, int nbc,
-                           int N, int kb_total, int *err, int code) {
-    int chunk = 0;
-    for (int c0 = 0; c0 < kb_total; c0 += kTcChunkKB, ++chunk) {
-        const int kbc = min(kTcChunkKB, kb_total - c0);
-        const uint32_t abytes = static_cast<uint32_t>(a_rb) * kbc * 128;
-        const uint32_t bbytes = static_cast<uint32_t>(nbc) * kbc * 128;
-        expect_tx(&sm.mbar_ld, NP * (abytes + bbytes));
+__device__ void copy_chunk(TcSmem &sm, __nv_bfloat16 *stage0, size_t stage_elems, int belems, const TileOperands &o,
+                           int c, int st) {
+    const int c0 = c * kTcChunkKB, kbc = min(kTcChunkKB, o.kb_total - c0);
+    __nv_bfloat16 *sa = stage0 + st * stage_elems, *sb = sa + NP * kAElems;
+    const uint32_t abytes = static_cast<uint32_t>(o.a_rb) * kbc * 128;
+    const uint32_t bbytes = static_cast<uint32_t>(o.nbc) * kbc * 128;
+    expect_tx(&sm.mbar_ld[st], NP * (abytes + bbytes));
 #pragma unroll
-        for (int i = 0; i < NP; ++i) {
-            bulk_copy(sa + i * kAElems, a_src + i * a_piece + static_cast<long long>(a_rb) * 64 * c0, abytes,
-                      &sm.mbar_ld);
-            bulk_copy(sb + i * belems, b_src + i * b_piece + static_cast<long long>(b_cb) * 64 * c0, bbytes,
-                      &sm.mbar_ld);
+    for (int i = 0; i < NP; ++i) {
+        bulk_copy(sa + i * kAElems, o.a_src + i * o.a_piece + static_cast<long long>(o.a_rb) * 64 * c0, abytes,
+                  &sm.mbar_ld[st]);
+        bulk_copy(sb + i * belems, o.b_src + i * o.b_piece + static_cast<long long>(o.b_cb) * 64 * c0, bbytes,
+                  &sm.mbar_ld[st]);
+    }
+}
+
+// The chunks of one tile, two operand stages deep: chunk c + 2 is copied while
+// the block finishes chunk c + 1.  Every chunk's MMAs start a fresh TMEM
+// accumulator (the tensor core's own accumulation spans at most kTcChunkKB k
+// blocks along K) that the block adds into acc in FP32 registers (row =
+// thread, columns 8 cb + u) before the next chunk's MMAs.  Bounded waits: on
+// expiry the flag gets `code`, thread 0 waits once more (bounded) for copies
+// and MMAs in flight and the tile is abandoned (returns false).
+template <int NP, int NBC>
+__device__ bool tile_chunks(TcSmem &sm, __nv_bfloat16 *stage0, int belems, const TileOperands &o, int *err,
+                            int code, float (&acc)[NBC][8]) {
+    const int warp = threadIdx.x >> 5;
+    const size_t stage_elems = tc_stage_elems(NP, o.nbc);
+#pragma unroll
+    for (int cb = 0; cb < NBC; ++cb)
+#pragma unroll
+        for (int u = 0; u < 8; ++u) acc[cb][u] = 0.f;
+    const int nch = (o.kb_total + kTcChunkKB - 1) / kTcChunkKB;
+    if (threadIdx.x == 0) {
+        copy_chunk<NP>(sm, stage0, stage_elems, belems, o, 0, 0);
+        if (nch > 1) copy_chunk<NP>(sm, stage0, stage_elems, belems, o, 1, 1);
+    }
+    for (int c = 0; c < nch; ++c) {
+        const int st = c & 1;
+        if (threadIdx.x == 0) {
+            const bool landed = mbar_wait(&sm.mbar_ld[st], (c >> 1) & 1);
+            bool done = false;
+            if (landed) {
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                const __nv_bfloat16 *sa = stage0 + st * stage_elems;
+                issue_chunk<NP>(sa, sa + NP * kAElems, belems, sm.tmem,
+                                min(kTcChunkKB, o.kb_total - c * kTcChunkKB), o.N, true);
+                mma_commit(&sm.mbar_mma);
+                done = mbar_wait(&sm.mbar_mma, c & 1);
+            }
+            if (done && c + 2 < nch) copy_chunk<NP>(sm, stage0, stage_elems, belems, o, c + 2, st);
+            if (!done) {                        // let work in flight land (bounded) and give up the tile
+                atomicExch(err, landed ? code + 1 : code);
+                sm.abort = 1;
+                if (landed) mbar_wait(&sm.mbar_mma, c & 1);
+                else mbar_wait(&sm.mbar_ld[st], (c >> 1) & 1);
+                if (c + 1 < nch) mbar_wait(&sm.mbar_ld[st ^ 1], ((c + 1) >> 1) & 1);
+            }
         }
-        if (!mbar_wait(&sm.mbar_ld, chunk & 1)) {
-            atomicExch(err, code);
-            mbar_wait(&sm.mbar_ld, chunk & 1);
-            return false;
-        }
+        __syncthreads();
+        if (sm.abort) return false;
         asm volatile("tcgen05.fence::after_thread_sync;");
-        issue_chunk<NP>(sa, sb, belems, sm.tmem, kbc, N, chunk == 0);
-        mma_commit(&sm.mbar_mma);
-        if (!mbar_wait(&sm.mbar_mma, chunk & 1)) {
-            atomicExch(err, code + 1);
-            mbar_wait(&sm.mbar_mma, chunk & 1);
-            return false;
+#pragma unroll
+        for (int cb = 0; cb < NBC; ++cb) {
+            if (cb < o.nbc) {
+                float v[8];
+                tmem_ld8(sm.tmem + (static_cast<uint32_t>(warp * 32) << 16) + cb * 8, v);
+#pragma unroll
+                for (int u = 0; u < 8; ++u) acc[cb][u] += v[u];
+            }
         }
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncthreads();                        // TMEM read before the next chunk overwrites it
     }
     return true;
 }
 
 __device__ __forceinline__ void tc_prologue(TcSmem &sm, uint32_t ncols) {
     if (threadIdx.x == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&sm.mbar_ld)));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&sm.mbar_mma)));
-        asm volatile("fence.mbarrier_init.release.cluster;");
+        mbar_init(&sm.mbar_ld[0], 1);
+        mbar_init(&sm.mbar_ld[1], 1);
+        mbar_init(&sm.mbar_mma, 1);
+        mbar_init_fence();
         sm.abort = 0;
     }
     if (threadIdx.x < 32) {
@@ -244,39 +267,29 @@ __global__ void __launch_bounds__(kTcThreads) k3_tc(TcTables tc, Dims d, int B, 
     const int N = (ncols + 15) / 16 * 16;
     const int nbc = N / 8;                      // column blocks
     const int belems = b_elems(nbc);
-    __nv_bfloat16 *sa = reinterpret_cast<__nv_bfloat16 *>(smem_raw + kCtrlBytes);
-    __nv_bfloat16 *sb = sa + NP * kAElems;
+    __nv_bfloat16 *stage0 = reinterpret_cast<__nv_bfloat16 *>(smem_raw + kCtrlBytes);
     const uint32_t tcols = N <= 32 ? 32u : (N <= 64 ? 64u : 128u);
     const int T = d.T;
     const int kjb = tc.kj / 8;
     tc_prologue(sm, tcols);
-    if (threadIdx.x == 0) {
-        const long long gbase = static_cast<long long>(2 * t.m + t.p) * kNbc3 * kjb * 64;
-        if (!run_chunks<NP>(sm, sa, sb, belems, tc.a3 + t.aoff, tc.elems3, t.nrb, tc.wb + gbase, tc.wb_elems,
-                            kNbc3, nbc, N, kjb, tc.err, 1))
-            sm.abort = 1;
-    }
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;");
-
-    if (!sm.abort) {
-        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-        const int r = warp * 32 + lane;
+    const long long gbase = static_cast<long long>(2 * t.m + t.p) * kNbc3 * kjb * 64;
+    const TileOperands o{tc.a3 + t.aoff, tc.elems3, t.nrb, tc.wb + gbase, tc.wb_elems, kNbc3, nbc, N, kjb};
+    float acc[kNbc3][8];
+    if (tile_chunks<NP, kNbc3>(sm, stage0, belems, o, tc.err, 1, acc)) {
+        const int r = threadIdx.x;
         const int q = t.q0 + r;
         const int e = ext_offset(T, t.m) + t.p + 2 * q;
-        float v[8];
-        for (int cb = 0; cb < nbc; ++cb) {
-            tmem_ld8(sm.tmem + (static_cast<uint32_t>(warp * 32) << 16) + cb * 8, v);
-            if (r < t.nrows) {
+        if (r < t.nrows) {
+#pragma unroll
+            for (int cb = 0; cb < kNbc3; ++cb)
 #pragma unroll
                 for (int u = 0; u < 8; u += 2) {
                     const int c = cb * 8 + u;
-                    if (c < ncols) {
+                    if (cb < nbc && c < ncols) {
                         const int b = c / 10, g = (c - b * 10) / 2;
-                        y[(static_cast<size_t>(b) * d.next + e) * 5 + g] = make_float2(v[u], v[u + 1]);
+                        y[(static_cast<size_t>(b) * d.next + e) * 5 + g] = make_float2(acc[cb][u], acc[cb][u + 1]);
                     }
                 }
-            }
         }
     }
     tc_epilogue_free(sm, tcols);
@@ -297,31 +310,25 @@ __global__ void __launch_bounds__(kTcThreads) k1_tc(TcTables tc, Dims d, int B, 
     const int N = (ncols + 15) / 16 * 16;
     const int nbc = N / 8;
     const int belems = b_elems(nbc);
-    __nv_bfloat16 *sa = reinterpret_cast<__nv_bfloat16 *>(smem_raw + kCtrlBytes);
-    __nv_bfloat16 *sb = sa + NP * kAElems;
+    __nv_bfloat16 *stage0 = reinterpret_cast<__nv_bfloat16 *>(smem_raw + kCtrlBytes);
     const uint32_t tcols = N <= 32 ? 32u : 64u;
     const int T = d.T;
     const int m = t.m;
     tc_prologue(sm, tcols);
-    if (threadIdx.x == 0) {
-        if (!run_chunks<NP>(sm, sa, sb, belems, tc.a1 + t.aoff, tc.elems1, t.njb, tc.cb + tc.cb_off[2 * m + t.p],
-                            tc.cb_elems, kNbc1, nbc, N, t.KR / 8, tc.err, 3))
-            sm.abort = 1;
-    }
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;");
-
-    if (!sm.abort) {
-        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-        const int r = warp * 32 + lane;
+    const TileOperands o{tc.a1 + t.aoff, tc.elems1, t.njb, tc.cb + tc.cb_off[2 * m + t.p], tc.cb_elems, kNbc1, nbc, N,
+                         t.KR / 8};
+    float acc[kNbc1][8];
+    if (tile_chunks<NP, kNbc1>(sm, stage0, belems, o, tc.err, 3, acc)) {
+        const int r = threadIdx.x;
         const int j = t.j0 + r;
-        float v[8];
-        for (int cb = 0; cb < nbc; ++cb) {
-            tmem_ld8(sm.tmem + (static_cast<uint32_t>(warp * 32) << 16) + cb * 8, v);
-            if (r < t.nj && cb < B) {
-                float2 *o = f1 + (static_cast<size_t>(cb) * d.J2 + j) * 8 * (T + 1) + t.p * (T + 1) + m;
+        if (r < t.nj) {
 #pragma unroll
-                for (int f = 0; f < 4; ++f) o[f * 2 * (T + 1)] = make_float2(v[2 * f], v[2 * f + 1]);
+            for (int cb = 0; cb < kNbc1; ++cb) {
+                if (cb < B) {
+                    float2 *o = f1 + (static_cast<size_t>(cb) * d.J2 + j) * 8 * (T + 1) + t.p * (T + 1) + m;
+#pragma unroll
+                    for (int f = 0; f < 4; ++f) o[f * 2 * (T + 1)] = make_float2(acc[cb][2 * f], acc[cb][2 * f + 1]);
+                }
             }
         }
     }

@@ -21,6 +21,7 @@
 
 #include "fft.cuh"
 #include "fft_pass.cuh"
+#include "async_copy.cuh"
 #include "sdc_internal.h"
 
 namespace sdc {
@@ -362,26 +363,72 @@ __global__ void __launch_bounds__(64) k3_project(const V2<R> *__restrict__ f2, D
 // are bound by GB300's FP64 rate; in FP32 the same loops would be bound by
 // load issue and latency).
 //
-// K1 (FP32): one block per (state, order pair), all latitudes.  A thread
-// owns four consecutive latitudes and keeps the even/odd sums of the four
-// fields for all four in registers; S neighbouring lanes split the rows and
-// are summed with shuffles at the end (S = 4, 2, 1 keeps a block at <= 256
-// threads for up to 256, 512, 1024 northern latitudes).  Each step issues the table
-// loads of two row pairs before their 128 FMAs.  The coefficients are
-// prepared in FP32 (the precision of this path).
+// K1 (FP32): one block per (state, order pair), all latitudes.  The table
+// rows of the two orders (contiguous in the table) stream through a ring of
+// shared-memory stages, kSynRows rows per bulk copy, issued nstages chunks
+// ahead by one thread (bounded mbarrier waits; on expiry the block sets the
+// error flag and stops).  A thread owns four consecutive latitudes and keeps
+// the even/odd sums of the four fields for all four in registers; S
+// neighbouring lanes split the row pairs of each chunk and are summed with
+// shuffles at the end of each order (S = 2 or 1 keeps a block at <= 256
+// threads).  The coefficients are prepared in FP32 (the precision of this
+// path) while the first copies are in flight.
 // ---------------------------------------------------------------------------
+constexpr int kSynRows = 8;
+constexpr int kMaxSynStages = 8;
+constexpr size_t kSynCtrlBytes = 128;
+
+__host__ inline int synthesis_f32_stages(int J2p) {
+    const int per = kSynRows * J2p * static_cast<int>(sizeof(float));
+    int ns = (48 * 1024) / per;
+    return ns < 2 ? 2 : (ns > 6 ? 6 : ns);
+}
+__host__ inline size_t synthesis_f32_smem(const Dims &d, int nstages) {
+    return kSynCtrlBytes + static_cast<size_t>(nstages) * kSynRows * d.J2p * sizeof(float) +
+           static_cast<size_t>(d.T + 4) * 4 * sizeof(float2);
+}
+
 template <int S>
 __global__ void __launch_bounds__(256) k1_synthesis_f32(const double2 *__restrict__ states, long long sstride,
                                                         Dims d, const float *__restrict__ pbar,
-                                                        const double *__restrict__ syn, float2 *__restrict__ f1) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    float2 *cf = reinterpret_cast<float2 *>(smem_raw);   // [rows][4]
+                                                        const double *__restrict__ syn, float2 *__restrict__ f1,
+                                                        int nstages, int *err) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem_raw);                 // [kMaxSynStages]
+    float *stage = reinterpret_cast<float *>(smem_raw + kSynCtrlBytes);      // [nstages][kSynRows][J2p]
+    const size_t stage_elems = static_cast<size_t>(kSynRows) * d.J2p;
+    float2 *cf = reinterpret_cast<float2 *>(stage + nstages * stage_elems);  // [rows][4]
     const int T = d.T;
     const int b = blockIdx.x;
     const int m1 = blockIdx.y, m2 = T - blockIdx.y;
     const int nn1 = T + 2 - m1;
     const int nn2 = (m2 > m1) ? T + 2 - m2 : 0;
     const int rows = nn1 + nn2;
+    const int nch1 = (nn1 + kSynRows - 1) / kSynRows;
+    const int nch = nch1 + (nn2 + kSynRows - 1) / kSynRows;
+    // chunk c: order, first row t0 within the order, row count
+    auto chunk = [&](int c, int &m, int &t0, int &cnt) {
+        const bool second = c >= nch1;
+        m = second ? m2 : m1;
+        t0 = (second ? c - nch1 : c) * kSynRows;
+        cnt = min(kSynRows, (second ? nn2 : nn1) - t0);
+    };
+    auto issue = [&](int c) {
+        int m, t0, cnt;
+        chunk(c, m, t0, cnt);
+        const uint32_t bytes = static_cast<uint32_t>(cnt) * d.J2p * sizeof(float);
+        uint64_t *bar = &mbar[c % nstages];
+        expect_tx(bar, bytes);
+        bulk_copy(stage + (c % nstages) * stage_elems, pbar + static_cast<size_t>(ext_offset(T, m) + t0) * d.J2p,
+                  bytes, bar);
+    };
+    int issued = 0;
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < nstages; ++k) mbar_init(&mbar[k], 1);
+        mbar_init_fence();
+        for (; issued < min(nstages, nch); ++issued) issue(issued);
+    }
+
     const double2 *st = states + b * sstride;
     const int nc = d.ncoef;
     for (int r = threadIdx.x; r < rows; r += blockDim.x) {
@@ -408,71 +455,80 @@ __global__ void __launch_bounds__(256) k1_synthesis_f32(const double2 *__restric
     const int part = threadIdx.x % S;
     const int j0 = 4 * (threadIdx.x / S);
     const bool active = j0 < d.J2;
-    const int jl = active ? j0 : 0;                      // idle lanes read a valid row and store nothing
-    for (int half = 0; half < 2; ++half) {
-        const int m = half ? m2 : m1;
-        const int nn = half ? nn2 : nn1;
-        if (nn == 0) break;
-        const float2 *c = cf + (half ? nn1 : 0) * 4;
-        float2 ae[4][4], ao[4][4];                       // [field][latitude]
+    const int jl = active ? j0 : 0;                      // idle lanes read a valid column and store nothing
+    float2 ae[4][4], ao[4][4];                           // [field][latitude]
+    auto reset = [&]() {
 #pragma unroll
         for (int f = 0; f < 4; ++f)
 #pragma unroll
             for (int k = 0; k < 4; ++k) ae[f][k] = ao[f][k] = make_float2(0.f, 0.f);
-        const float *prow = pbar + static_cast<size_t>(ext_offset(T, m)) * d.J2p + jl;
-        auto row = [&](int t) { return *reinterpret_cast<const float4 *>(prow + static_cast<size_t>(t) * d.J2p); };
-        auto accum = [&](float2 (&a)[4][4], const float4 pv4, int t) {
-            const float pv[4] = {pv4.x, pv4.y, pv4.z, pv4.w};
+    };
+    auto accum = [&](float2 (&a)[4][4], const float4 pv4, const float2 *c) {
+        const float pv[4] = {pv4.x, pv4.y, pv4.z, pv4.w};
 #pragma unroll
-            for (int f = 0; f < 4; ++f) {
-                const float2 cc = c[t * 4 + f];
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    a[f][k].x = fmaf(pv[k], cc.x, a[f][k].x);
-                    a[f][k].y = fmaf(pv[k], cc.y, a[f][k].y);
-                }
-            }
-        };
-        const int npairs = nn / 2;
-        int u = part;
-        for (; u + S < npairs; u += 2 * S) {
-            const int t0 = 2 * u, t1 = 2 * (u + S);
-            const float4 pe0 = row(t0), po0 = row(t0 + 1), pe1 = row(t1), po1 = row(t1 + 1);
-            accum(ae, pe0, t0);
-            accum(ao, po0, t0 + 1);
-            accum(ae, pe1, t1);
-            accum(ao, po1, t1 + 1);
-        }
-        if (u < npairs) {
-            const int t0 = 2 * u;
-            const float4 pe0 = row(t0), po0 = row(t0 + 1);
-            accum(ae, pe0, t0);
-            accum(ao, po0, t0 + 1);
-        }
-        if ((nn & 1) && part == (npairs % S)) accum(ae, row(nn - 1), nn - 1);
-#pragma unroll
-        for (int f = 0; f < 4; ++f)
-#pragma unroll
-            for (int k = 0; k < 4; ++k)
-#pragma unroll
-                for (int o = 1; o < S; o <<= 1) {
-                    ae[f][k].x += __shfl_xor_sync(0xffffffffu, ae[f][k].x, o);
-                    ae[f][k].y += __shfl_xor_sync(0xffffffffu, ae[f][k].y, o);
-                    ao[f][k].x += __shfl_xor_sync(0xffffffffu, ao[f][k].x, o);
-                    ao[f][k].y += __shfl_xor_sync(0xffffffffu, ao[f][k].y, o);
-                }
-        if (active && part == 0) {
+        for (int f = 0; f < 4; ++f) {
+            const float2 cc = c[f];
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                if (j0 + k >= d.J2) break;
-                float2 *o = f1 + (static_cast<size_t>(b) * d.J2 + j0 + k) * (4 * 2 * (T + 1)) + m;
-#pragma unroll
-                for (int f = 0; f < 4; ++f) {
-                    o[(f * 2 + 0) * (T + 1)] = ae[f][k];
-                    o[(f * 2 + 1) * (T + 1)] = ao[f][k];
-                }
+                a[f][k].x = fmaf(pv[k], cc.x, a[f][k].x);
+                a[f][k].y = fmaf(pv[k], cc.y, a[f][k].y);
             }
         }
+    };
+    reset();
+    int c = 0;
+    for (; c < nch; ++c) {
+        int m, t0, cnt;
+        chunk(c, m, t0, cnt);
+        const bool late = !mbar_wait(&mbar[c % nstages], (c / nstages) & 1);
+        if (__syncthreads_or(late)) {                    // the block agrees before anyone leaves
+            if (threadIdx.x == 0) atomicExch(err, 5);
+            break;
+        }
+        const float *P = stage + (c % nstages) * stage_elems + jl;
+        const float2 *cc = cf + ((c >= nch1 ? nn1 : 0) + t0) * 4;
+        for (int u = part; 2 * u < cnt; u += S) {
+            const int i0 = 2 * u;
+            const float4 pe = *reinterpret_cast<const float4 *>(P + i0 * d.J2p);
+            if (i0 + 1 < cnt) {
+                const float4 po = *reinterpret_cast<const float4 *>(P + (i0 + 1) * d.J2p);
+                accum(ae, pe, cc + i0 * 4);
+                accum(ao, po, cc + (i0 + 1) * 4);
+            } else {
+                accum(ae, pe, cc + i0 * 4);
+            }
+        }
+        if (c == nch1 - 1 || c == nch - 1) {             // end of an order: reduce and store
+#pragma unroll
+            for (int f = 0; f < 4; ++f)
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+#pragma unroll
+                    for (int o = 1; o < S; o <<= 1) {
+                        ae[f][k].x += __shfl_xor_sync(0xffffffffu, ae[f][k].x, o);
+                        ae[f][k].y += __shfl_xor_sync(0xffffffffu, ae[f][k].y, o);
+                        ao[f][k].x += __shfl_xor_sync(0xffffffffu, ao[f][k].x, o);
+                        ao[f][k].y += __shfl_xor_sync(0xffffffffu, ao[f][k].y, o);
+                    }
+            if (active && part == 0) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    if (j0 + k >= d.J2) break;
+                    float2 *o = f1 + (static_cast<size_t>(b) * d.J2 + j0 + k) * (4 * 2 * (T + 1)) + m;
+#pragma unroll
+                    for (int f = 0; f < 4; ++f) {
+                        o[(f * 2 + 0) * (T + 1)] = ae[f][k];
+                        o[(f * 2 + 1) * (T + 1)] = ao[f][k];
+                    }
+                }
+            }
+            reset();
+        }
+        __syncthreads();                                 // every read of this stage is done
+        if (threadIdx.x == 0 && issued < nch) issue(issued++);
+    }
+    if (c < nch && threadIdx.x == 0) {                   // stopped early: let issued copies land (bounded)
+        for (int k = c; k < issued; ++k) mbar_wait(&mbar[k % nstages], (k / nstages) & 1);
     }
 }
 
@@ -678,6 +734,11 @@ static cudaError_t configure(const Dims &d, const FftPlan &plan) {
         e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smr);
         if (e != cudaSuccess) return e;
     }
+    const int sms = (int)synthesis_f32_smem(d, synthesis_f32_stages(d.J2p));
+    e = cudaFuncSetAttribute(k1_synthesis_f32<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sms);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k1_synthesis_f32<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sms);
+    if (e != cudaSuccess) return e;
     const int smw = (int)(2 * 10 * static_cast<size_t>(d.J2) * sizeof(float2));
     e = cudaFuncSetAttribute(k3_project_f32<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smw);
     if (e != cudaSuccess) return e;
@@ -707,12 +768,14 @@ static cudaError_t launch_tendency_t(const Dims &d, const FftPlan &plan, int B, 
         } else {
             const int g4 = (d.J2 + 3) / 4;
             const dim3 gs(B, (d.T + 2) / 2);
-            if (g4 <= 64)
-                k1_synthesis_f32<4><<<gs, (g4 * 4 + 31) / 32 * 32, sm1, s>>>(states, sstride, d, pbar, tb.syn, f1);
-            else if (g4 <= 128)
-                k1_synthesis_f32<2><<<gs, (g4 * 2 + 31) / 32 * 32, sm1, s>>>(states, sstride, d, pbar, tb.syn, f1);
+            const int ns = synthesis_f32_stages(d.J2p);
+            const size_t smk = synthesis_f32_smem(d, ns);
+            if (g4 <= 128)
+                k1_synthesis_f32<2><<<gs, (g4 * 2 + 31) / 32 * 32, smk, s>>>(states, sstride, d, pbar, tb.syn, f1,
+                                                                           ns, tb.err);
             else
-                k1_synthesis_f32<1><<<gs, (g4 + 31) / 32 * 32, sm1, s>>>(states, sstride, d, pbar, tb.syn, f1);
+                k1_synthesis_f32<1><<<gs, (g4 + 31) / 32 * 32, smk, s>>>(states, sstride, d, pbar, tb.syn, f1, ns,
+                                                                       tb.err);
             if (launches) ++*launches;
         }
     } else {
