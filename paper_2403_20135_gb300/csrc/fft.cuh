@@ -4,6 +4,8 @@
 
 #include <cuda_runtime.h>
 
+#include <cstring>
+
 #include "sdc_internal.h"
 
 namespace sdc {
@@ -20,6 +22,21 @@ template <typename R> __device__ __forceinline__ V2<R> cmul(V2<R> a, V2<R> b) {
     return mk<R>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 template <typename R> __device__ __forceinline__ V2<R> cscale(V2<R> a, R s) { return mk<R>(a.x * s, a.y * s); }
+// Packed FP32 pair FMA (two IEEE round-to-nearest FMAs in one instruction):
+// (a.x * b.x + c.x, a.y * b.y + c.y).
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
+    unsigned long long ra, rb, rc, rd;
+    memcpy(&ra, &a, 8);
+    memcpy(&rb, &b, 8);
+    memcpy(&rc, &c, 8);
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(rd) : "l"(ra), "l"(rb), "l"(rc));
+    float2 d;
+    memcpy(&d, &rd, 8);
+    return d;
+}
+// c + s * z for a real s and a complex z, as one packed FMA
+__device__ __forceinline__ float2 caxpy(float s, float2 z, float2 c) { return ffma2(make_float2(s, s), z, c); }
+
 // multiply by +i or -i
 template <typename R> __device__ __forceinline__ V2<R> mul_i(V2<R> a) { return mk<R>(-a.y, a.x); }
 template <typename R> __device__ __forceinline__ V2<R> mul_mi(V2<R> a) { return mk<R>(a.y, -a.x); }

@@ -469,10 +469,7 @@ __global__ void __launch_bounds__(256) k1_synthesis_f32(const double2 *__restric
         for (int f = 0; f < 4; ++f) {
             const float2 cc = c[f];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                a[f][k].x = fmaf(pv[k], cc.x, a[f][k].x);
-                a[f][k].y = fmaf(pv[k], cc.y, a[f][k].y);
-            }
+            for (int k = 0; k < 4; ++k) a[f][k] = caxpy(pv[k], cc, a[f][k]);
         }
     };
     reset();
@@ -597,14 +594,10 @@ __global__ void __launch_bounds__(512) k3_project_f32(const float2 *__restrict__
                     const float4 wb = *reinterpret_cast<const float4 *>(W + g * 2 * J2 + j + 2);
 #pragma unroll
                     for (int r = 0; r < 4; ++r) {
-                        acc[r][g].x = fmaf(pv[r][0], wa.x, acc[r][g].x);
-                        acc[r][g].y = fmaf(pv[r][0], wa.y, acc[r][g].y);
-                        acc[r][g].x = fmaf(pv[r][1], wa.z, acc[r][g].x);
-                        acc[r][g].y = fmaf(pv[r][1], wa.w, acc[r][g].y);
-                        acc[r][g].x = fmaf(pv[r][2], wb.x, acc[r][g].x);
-                        acc[r][g].y = fmaf(pv[r][2], wb.y, acc[r][g].y);
-                        acc[r][g].x = fmaf(pv[r][3], wb.z, acc[r][g].x);
-                        acc[r][g].y = fmaf(pv[r][3], wb.w, acc[r][g].y);
+                        acc[r][g] = caxpy(pv[r][0], make_float2(wa.x, wa.y), acc[r][g]);
+                        acc[r][g] = caxpy(pv[r][1], make_float2(wa.z, wa.w), acc[r][g]);
+                        acc[r][g] = caxpy(pv[r][2], make_float2(wb.x, wb.y), acc[r][g]);
+                        acc[r][g] = caxpy(pv[r][3], make_float2(wb.z, wb.w), acc[r][g]);
                     }
                 }
             }
