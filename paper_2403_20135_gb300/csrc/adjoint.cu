@@ -51,7 +51,7 @@ __global__ void k3t_epilogue(const double2 *__restrict__ abar, long long astride
     auto ld = [&](int f, int k) -> double2 {
         return (k >= m && k <= T) ? ab[f * nc + off + k - m] : make_double2(0.0, 0.0);
     };
-    const double inv_a = 1.0 / d.a;
+    const double inv_a = d.inv_a;
     const double cu = (t >= 1) ? (n - 1.0) * eps[e] * inv_a : 0.0;
     const double cl = (n + 1 <= T) ? (n + 2.0) * eps[e + 1] * inv_a : 0.0;
     const double mi = double(m) * inv_a;

@@ -58,7 +58,8 @@ struct sdc_ctx {
     // device tables
     double *pbar = nullptr;
     float *pbar32 = nullptr;
-    double *eps = nullptr, *lam = nullptr, *mu2 = nullptr, *w2 = nullptr, *syn = nullptr;
+    double *eps = nullptr, *lam = nullptr, *mu2 = nullptr, *w2 = nullptr, *syn = nullptr, *ring64 = nullptr;
+    float *ring32 = nullptr, *epi32 = nullptr;
     int *row_m = nullptr, *coef_m = nullptr;
     double2 *tw = nullptr;
     float2 *tw32 = nullptr;
@@ -106,7 +107,7 @@ void free_ctx(sdc_ctx *c) {
         if (g) cudaGraphExecDestroy(g);
     if (c->graph_retape) cudaGraphExecDestroy(c->graph_retape);
     if (c->graph_adjoint) cudaGraphExecDestroy(c->graph_adjoint);
-    void *ptrs[] = {c->pbar, c->pbar32, c->eps, c->lam, c->mu2, c->w2, c->syn, c->row_m, c->coef_m, c->tw,
+    void *ptrs[] = {c->pbar, c->pbar32, c->ring64, c->ring32, c->epi32, c->eps, c->lam, c->mu2, c->w2, c->syn, c->row_m, c->coef_m, c->tw,
                     c->tw32, c->twp32, c->un, c->U, c->E, c->E0, c->f1, c->f2, c->f3, c->resid_part, c->resid,
                     c->gstore, c->ub, c->eb, c->ubn, c->ubnext, c->eb0, c->snaps, c->phigrid, c->rgrid,
                     c->loss_part, c->loss_dev, c->tc_a3, c->tc_a1, c->tc_t3, c->tc_t1, c->tc_err, c->den,
@@ -143,6 +144,9 @@ DeviceTables tables(const sdc_ctx *c) {
     tb.row_m = c->row_m;
     tb.coef_m = c->coef_m;
     tb.err = c->tc_err;
+    tb.ring64 = c->ring64;
+    tb.ring32 = c->ring32;
+    tb.epi32 = c->epi32;
     tb.plan16 = c->plan16;
     tb.twp32 = c->twp32;
     tb.ntwp = c->ntwp;
@@ -173,6 +177,9 @@ cudaError_t tendency(sdc_ctx *c, int B, const double2 *states, long long sstride
     tb.row_m = c->row_m;
     tb.coef_m = c->coef_m;
     tb.err = c->tc_err;
+    tb.ring64 = c->ring64;
+    tb.ring32 = c->ring32;
+    tb.epi32 = c->epi32;
     tb.plan16 = c->plan16;
     tb.twp32 = c->twp32;
     tb.ntwp = c->ntwp;
@@ -586,6 +593,7 @@ int sdc_create(sdc_ctx **out, int T, int J, int L, int M, int K, double dt, cons
     d.ncoef = (T + 1) * (T + 2) / 2;
     d.next = (T + 1) * (T + 4) / 2;
     d.a = phys->radius;
+    d.inv_a = 1.0 / phys->radius;
     d.two_omega = 2.0 * phys->omega;
     if (!fft_plan(L, c->plan)) { free_ctx(c); return fail(SDC_EINVAL, "no FFT plan for nlon"); }
     const int elem = precision == SDC_FP64 ? (int)sizeof(double2) : (int)sizeof(float2);
@@ -698,6 +706,29 @@ int sdc_create(sdc_ctx **out, int T, int J, int L, int M, int K, double dt, cons
     SDC_TRY(upload(&c->coef_m, coef_m.data(), coef_m.size()));
     SDC_TRY(upload(&c->lam, lam.data(), lam.size()));
     SDC_TRY(upload(&c->mu2, c->mu.data(), d.J2));
+    {
+        // per-latitude ring constants and FP32 epilogue factors
+        std::vector<double> r64(4 * static_cast<size_t>(d.J2));
+        std::vector<float> r32(r64.size());
+        for (int j = 0; j < d.J2; ++j) {
+            const double mu = c->mu[j], c2 = (1.0 - mu) * (1.0 + mu);
+            const double v[4] = {d.two_omega * mu, 0.5 / c2, c->w[j] / c2, c->w[j]};
+            for (int k = 0; k < 4; ++k) { r64[4 * j + k] = v[k]; r32[4 * j + k] = float(v[k]); }
+        }
+        SDC_TRY(upload(&c->ring64, r64.data(), r64.size()));
+        SDC_TRY(upload(&c->ring32, r32.data(), r32.size()));
+        std::vector<float> e32(4 * static_cast<size_t>(d.ncoef));
+        for (int m = 0; m <= T; ++m)
+            for (int n = m; n <= T; ++n) {
+                const size_t i = static_cast<size_t>(order_offset(T, m) + n - m);
+                const int e = ext_offset(T, m) + n - m;
+                e32[4 * i + 0] = float(n * eps[e + 1]);
+                e32[4 * i + 1] = float(n > m ? (n + 1.0) * eps[e] : 0.0);
+                e32[4 * i + 2] = float(lam[i]);
+                e32[4 * i + 3] = 0.f;
+            }
+        SDC_TRY(upload(&c->epi32, e32.data(), e32.size()));
+    }
     SDC_TRY(upload(&c->w2, c->w.data(), d.J2));
 
     const size_t sbytes = 3ULL * d.ncoef * sizeof(double2);

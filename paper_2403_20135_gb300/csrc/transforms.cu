@@ -147,8 +147,8 @@ size_t ring_smem_bytes(int L, int elem_bytes, int *scratch_arrays) {
 // ---------------------------------------------------------------------------
 template <typename R>
 __global__ void k2_ring(const V2<R> *__restrict__ f1, V2<R> *__restrict__ f2, Dims d, FftPlan plan,
-                        const V2<R> *__restrict__ tw, const double *__restrict__ mu,
-                        const double *__restrict__ w, int nscratch, V2<R> *__restrict__ gstore) {
+                        const V2<R> *__restrict__ tw, const R *__restrict__ rw, int nscratch,
+                        V2<R> *__restrict__ gstore) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V2<R> *X = reinterpret_cast<V2<R> *>(smem_raw);   // [5][L]
     V2<R> *S = X + 5 * plan.L;                          // [nscratch][L]
@@ -176,10 +176,7 @@ __global__ void k2_ring(const V2<R> *__restrict__ f1, V2<R> *__restrict__ f2, Di
     __syncthreads();
     fft_inplace<R>(X, S, nscratch, 4, plan, TW, true);
 
-    const double mun = mu[j2];
-    const R cosl2 = R((1.0 - mun) * (1.0 + mun));
-    const R fN = R(d.two_omega * mun);
-    const R inv2c = R(0.5) / cosl2;
+    const R fN = rw[4 * j2], inv2c = rw[4 * j2 + 1];
     // optional record of the grid fields (north ring .x, south ring .y) for
     // the adjoint: gstore[b][j2][field][L]
     V2<R> *gs = gstore ? gstore + (static_cast<size_t>(b) * d.J2 + j2) * 4 * L : nullptr;
@@ -203,9 +200,7 @@ __global__ void k2_ring(const V2<R> *__restrict__ f1, V2<R> *__restrict__ f2, Di
     __syncthreads();
     fft_inplace<R>(X, S, nscratch, 5, plan, TW, false);
 
-    const double wj = w[j2];
-    const R wt = R(wj / ((1.0 - mun) * (1.0 + mun)));
-    const R wp = R(wj);
+    const R wt = rw[4 * j2 + 2], wp = rw[4 * j2 + 3];
     const R invL = R(1.0) / R(L);
     for (int i = threadIdx.x; i < 5 * (T + 1); i += blockDim.x) {
         const int g = i / (T + 1), m = i - g * (T + 1);
@@ -237,8 +232,7 @@ __host__ __device__ inline size_t ring_f32_smem_bytes(int L, int ntw) {
 template <int LC>
 __global__ void __launch_bounds__(256) k2_ring_f32(const float2 *__restrict__ f1, float2 *__restrict__ f2, Dims d,
                                                    FftPlan plan, const float2 *__restrict__ twp, int ntw,
-                                                   const double *__restrict__ mu, const double *__restrict__ w,
-                                                   float2 *__restrict__ gstore) {
+                                                   const float *__restrict__ rw, float2 *__restrict__ gstore) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int L = LC > 0 ? LC : plan.L, Lp = fft_padded_len(L);
     float2 *X = reinterpret_cast<float2 *>(smem_raw);   // [5][Lp]
@@ -268,10 +262,7 @@ __global__ void __launch_bounds__(256) k2_ring_f32(const float2 *__restrict__ f1
     if constexpr (LC > 0) G = fft_passes_ct<LC, 4>(X, S, TW, true);
     else G = fft_passes(X, S, 4, Lp, plan, TW, true);
 
-    const double mun = mu[j2];
-    const float cosl2 = float((1.0 - mun) * (1.0 + mun));
-    const float fN = float(d.two_omega * mun);
-    const float inv2c = 0.5f / cosl2;
+    const float fN = rw[4 * j2], inv2c = rw[4 * j2 + 1];
     float2 *gs = gstore ? gstore + (static_cast<size_t>(b) * d.J2 + j2) * 4 * L : nullptr;
     for (int k = threadIdx.x; k < L; k += blockDim.x) {
         const int kp = fpad(k);
@@ -295,9 +286,7 @@ __global__ void __launch_bounds__(256) k2_ring_f32(const float2 *__restrict__ f1
     if constexpr (LC > 0) Y = fft_passes_ct<LC, 5>(X, S, TW, false);
     else Y = fft_passes(X, S, 5, Lp, plan, TW, false);
 
-    const double wj = w[j2];
-    const float wt = float(wj / ((1.0 - mun) * (1.0 + mun)));
-    const float wp = float(wj);
+    const float wt = rw[4 * j2 + 2], wp = rw[4 * j2 + 3];
     const float half_invL = 0.5f / float(L);
     for (int i = threadIdx.x; i < 5 * (T + 1); i += blockDim.x) {
         const int g = i / (T + 1), m = i - g * (T + 1);
@@ -660,11 +649,12 @@ static int project_f32_threads(int T) {
 //   T_E(Phi')_n = -(1/a) [i m C^_n + n eps_{n+1} D^_{n+1} - (n+1) eps_n D^_{n-1}]
 // ---------------------------------------------------------------------------
 // The arithmetic runs in R (FP32 in the mixed modes, like the rest of the
-// transform); the tendencies are stored in FP64.
+// transform, with the per-mode factors from an FP32 table); the tendencies
+// are stored in FP64.
 template <typename R>
 __global__ void k3_epilogue(const V2<R> *__restrict__ y, Dims d, const double *__restrict__ eps,
-                            const double *__restrict__ lam, const int *__restrict__ coef_m,
-                            double2 *__restrict__ tend, long long tstride) {
+                            const double *__restrict__ lam, const float *__restrict__ epi32,
+                            const int *__restrict__ coef_m, double2 *__restrict__ tend, long long tstride) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int b = blockIdx.y;
     if (i >= d.ncoef) return;
@@ -681,11 +671,19 @@ __global__ void k3_epilogue(const V2<R> *__restrict__ y, Dims d, const double *_
     const V2<R> Al = t > 0 ? ld(e - 1, P_A) : z0;
     const V2<R> Bl = t > 0 ? ld(e - 1, P_B) : z0;
     const V2<R> Dl = t > 0 ? ld(e - 1, P_D) : z0;
-    const R cu = R(n * eps[e + 1]);
-    const R cl = t > 0 ? R((n + 1.0) * eps[e]) : R(0);
-    const R inv_a = R(1.0 / d.a);
+    R cu, cl, lm;
+    if constexpr (sizeof(R) == sizeof(float)) {
+        const float4 f = reinterpret_cast<const float4 *>(epi32)[i];
+        cu = f.x;
+        cl = f.y;
+        lm = f.z;
+    } else {
+        cu = n * eps[e + 1];
+        cl = t > 0 ? (n + 1.0) * eps[e] : 0.0;
+        lm = lam[i];
+    }
+    const R inv_a = R(d.inv_a);
     const R mm = R(m);
-    const R lm = R(lam[i]);
     // i m X = (-m X.y, m X.x)
     const R tzx = -inv_a * (-mm * Ah.y + cu * Bu.x - cl * Bl.x);
     const R tzy = -inv_a * (mm * Ah.x + cu * Bu.y - cl * Bl.y);
@@ -781,7 +779,7 @@ static cudaError_t launch_tendency_t(const Dims &d, const FftPlan &plan, int B, 
         const size_t sm = ring_f32_smem_bytes(d.L, tb.ntwp);
         float2 *gsr = static_cast<float2 *>(grid_store);
 #define SDC_RING_F32(LC) \
-    k2_ring_f32<LC><<<g2, kK2Threads, sm, s>>>(f1, f2, d, tb.plan16, tb.twp32, tb.ntwp, tb.mu, tb.w, gsr)
+    k2_ring_f32<LC><<<g2, kK2Threads, sm, s>>>(f1, f2, d, tb.plan16, tb.twp32, tb.ntwp, tb.ring32, gsr)
         switch (d.L) {
             case 96: SDC_RING_F32(96); break;
             case 192: SDC_RING_F32(192); break;
@@ -792,7 +790,7 @@ static cudaError_t launch_tendency_t(const Dims &d, const FftPlan &plan, int B, 
         }
 #undef SDC_RING_F32
     } else {
-        k2_ring<R><<<dim3(d.J2, B), kK2Threads, sm2, s>>>(f1, f2, d, plan, tw, tb.mu, tb.w, nscratch,
+        k2_ring<R><<<dim3(d.J2, B), kK2Threads, sm2, s>>>(f1, f2, d, plan, tw, tb.ring64, nscratch,
                                                          static_cast<V2<R> *>(grid_store));
     }
     if (timer) timer->mark(STAGE_ANALYSIS);
@@ -814,7 +812,8 @@ static cudaError_t launch_tendency_t(const Dims &d, const FftPlan &plan, int B, 
         if (launches) ++*launches;
     }
     if (timer) timer->mark(STAGE_EPILOGUE);
-    k3_epilogue<R><<<dim3((d.ncoef + 127) / 128, B), 128, 0, s>>>(f3, d, tb.eps, tb.lam, tb.coef_m, tend, tstride);
+    k3_epilogue<R><<<dim3((d.ncoef + 127) / 128, B), 128, 0, s>>>(f3, d, tb.eps, tb.lam, tb.epi32, tb.coef_m, tend,
+                                                                  tstride);
     if (launches) *launches += 2;                  // ring + epilogue
     return cudaGetLastError();
 }
