@@ -363,7 +363,7 @@ __global__ void __launch_bounds__(64) k3_project(const V2<R> *__restrict__ f2, D
 // threads).  The coefficients are prepared in FP32 (the precision of this
 // path) while the first copies are in flight.
 // ---------------------------------------------------------------------------
-constexpr int kSynRows = 8;
+constexpr int kSynRows = 24;
 constexpr int kMaxSynStages = 8;
 constexpr size_t kSynCtrlBytes = 128;
 
@@ -473,6 +473,7 @@ __global__ void __launch_bounds__(256) k1_synthesis_f32(const double2 *__restric
         }
         const float *P = stage + (c % nstages) * stage_elems + jl;
         const float2 *cc = cf + ((c >= nch1 ? nn1 : 0) + t0) * 4;
+#pragma unroll 4
         for (int u = part; 2 * u < cnt; u += S) {
             const int i0 = 2 * u;
             const float4 pe = *reinterpret_cast<const float4 *>(P + i0 * d.J2p);
