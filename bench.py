@@ -42,7 +42,7 @@ FP64_NOMINAL_TFLOPS = 1.25          # GB300 dense FP64 (nominal; no measured FP6
 FP32_SIMT_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # DRAM bytes (read + write) of one captured launch of the FP64 ring kernel with
 # a batch of 4 states at the bench workload (ncu capture summarised in
-# profiles/transforms_t255_fp64.md); the traffic is the batch's F1 input, so a
+# profiles/kernels_t255_fp64.md); the traffic is the batch's F1 input, so a
 # launch of b states moves b/4 of it.
 RING_FP64_TRAFFIC_B4 = 25.3e6 + 66.3e3
 
