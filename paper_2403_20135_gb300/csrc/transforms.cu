@@ -528,18 +528,40 @@ __global__ void __launch_bounds__(256) k1_synthesis_f32(const double2 *__restric
 // same row) and ten 16-byte shared loads for 160 FMAs.  VEC: J2 even, so
 // every W row starts on a 16-byte boundary.
 constexpr int kPrjParts = 4;
-template <bool VEC>
+constexpr int kPrjDepth = 4;          // per-thread cp.async stages of the table rows (ASYNC)
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// ASYNC: each lane streams its own four rows through kPrjDepth private
+// shared-memory stages with cp.async (16 bytes per row and 4-latitude
+// block), kPrjDepth - 1 blocks ahead of the FMAs; no block barrier is
+// involved because a lane only reads what it copied.
+template <bool VEC, bool ASYNC>
 __global__ void __launch_bounds__(512) k3_project_f32(const float2 *__restrict__ f2, Dims d,
                                                       const float *__restrict__ pbar, float2 *__restrict__ y) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2 *ws = reinterpret_cast<float2 *>(smem_raw);   // [2][10][J2]
+    float4 *pst = reinterpret_cast<float4 *>(ws + 2 * 10 * d.J2);   // [kPrjDepth][4 rows][blockDim] (ASYNC)
     const int T = d.T, J2 = d.J2;
     const int b = blockIdx.x;
     const int m1 = blockIdx.y, m2 = T - blockIdx.y;
     const int norders = (m2 > m1) ? 2 : 1;
     for (int h = 0; h < norders; ++h) {
         const float2 *src = f2 + (static_cast<size_t>(b) * (T + 1) + (h ? m2 : m1)) * 10 * J2;
-        for (int i = threadIdx.x; i < 10 * J2; i += blockDim.x) ws[h * 10 * J2 + i] = src[i];
+        if (VEC) {                                        // 10 J2 float2 = 5 J2 16-byte pieces, asynchronous
+            for (int i = threadIdx.x; i < 5 * J2; i += blockDim.x) cp_async16(ws + h * 10 * J2 + 2 * i, src + 2 * i);
+        } else {
+            for (int i = threadIdx.x; i < 10 * J2; i += blockDim.x) ws[h * 10 * J2 + i] = src[i];
+        }
+    }
+    if (VEC) {
+        cp_async_commit();
+        cp_async_wait<0>();
     }
     __syncthreads();
     // quads of (m1, p=0), (m1, p=1), (m2, p=0), (m2, p=1)
@@ -571,11 +593,29 @@ __global__ void __launch_bounds__(512) k3_project_f32(const float2 *__restrict__
         int jt = 0;                                      // first latitude of the scalar tail
         if (VEC) {
             jt = J2 & ~3;
-            for (int j = 4 * part; j < jt; j += 4 * kPrjParts) {
+            const int nit = jt > 4 * part ? (jt - 4 * part + 4 * kPrjParts - 1) / (4 * kPrjParts) : 0;
+            auto stage_ptr = [&](int it, int r) { return pst + ((it % kPrjDepth) * 4 + r) * blockDim.x + threadIdx.x; };
+            auto issue = [&](int it) {
+                if (it < nit) {
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) cp_async16(stage_ptr(it, r), pr[r] + 4 * part + 4 * kPrjParts * it);
+                }
+                cp_async_commit();                       // one group per block index, possibly empty
+            };
+            if (ASYNC) {
+#pragma unroll
+                for (int it = 0; it < kPrjDepth - 1; ++it) issue(it);
+            }
+            for (int it = 0; it < nit; ++it) {
+                const int j = 4 * part + 4 * kPrjParts * it;
                 float pv[4][4];
+                if (ASYNC) {
+                    issue(it + kPrjDepth - 1);
+                    cp_async_wait<kPrjDepth - 1>();      // block index it has landed
+                }
 #pragma unroll
                 for (int r = 0; r < 4; ++r) {
-                    const float4 v = *reinterpret_cast<const float4 *>(pr[r] + j);
+                    const float4 v = ASYNC ? *stage_ptr(it, r) : *reinterpret_cast<const float4 *>(pr[r] + j);
                     pv[r][0] = v.x; pv[r][1] = v.y; pv[r][2] = v.z; pv[r][3] = v.w;
                 }
 #pragma unroll
@@ -625,6 +665,16 @@ __global__ void __launch_bounds__(512) k3_project_f32(const float2 *__restrict__
             }
         }
     }
+}
+
+// shared memory of a K3a (FP32) block; the per-lane cp.async stages are
+// used when the W rows leave room for them (and J2 is even)
+static bool project_f32_async(const Dims &d, int nthreads, size_t *bytes) {
+    const size_t w = 2 * 10 * static_cast<size_t>(d.J2) * sizeof(float2);
+    const size_t st = static_cast<size_t>(kPrjDepth) * 4 * nthreads * sizeof(float4);
+    const bool async = d.J2 % 2 == 0 && w + st <= 200 * 1024;
+    *bytes = async ? w + st : w;
+    return async;
 }
 
 // threads of a K3a (FP32) block: all row quads of the largest order pair,
@@ -731,10 +781,14 @@ static cudaError_t configure(const Dims &d, const FftPlan &plan) {
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k1_synthesis_f32<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sms);
     if (e != cudaSuccess) return e;
-    const int smw = (int)(2 * 10 * static_cast<size_t>(d.J2) * sizeof(float2));
-    e = cudaFuncSetAttribute(k3_project_f32<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smw);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k3_project_f32<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smw);
+    size_t smp = 0;
+    project_f32_async(d, project_f32_threads(d.T), &smp);
+    for (const void *f : {(const void *)k3_project_f32<true, true>, (const void *)k3_project_f32<true, false>,
+                          (const void *)k3_project_f32<false, false>}) {
+        e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smp);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 template <typename R>
@@ -802,9 +856,11 @@ static cudaError_t launch_tendency_t(const Dims &d, const FftPlan &plan, int B, 
         } else {
             const dim3 g3(B, (d.T + 2) / 2);
             const int nt = project_f32_threads(d.T);
-            const size_t smw = 2 * 10 * static_cast<size_t>(d.J2) * sizeof(float2);
-            if (d.J2 % 2 == 0) k3_project_f32<true><<<g3, nt, smw, s>>>(f2, d, pbar, f3);
-            else k3_project_f32<false><<<g3, nt, smw, s>>>(f2, d, pbar, f3);
+            size_t smp = 0;
+            const bool async = project_f32_async(d, nt, &smp);
+            if (d.J2 % 2 != 0) k3_project_f32<false, false><<<g3, nt, smp, s>>>(f2, d, pbar, f3);
+            else if (async) k3_project_f32<true, true><<<g3, nt, smp, s>>>(f2, d, pbar, f3);
+            else k3_project_f32<true, false><<<g3, nt, smp, s>>>(f2, d, pbar, f3);
             if (launches) ++*launches;
         }
     } else {
