@@ -248,14 +248,27 @@ __global__ void __launch_bounds__(256) k2_ring_f32(const float2 *__restrict__ f1
         const int f = i / gap, k = T + 1 + (i - f * gap);
         X[f * Lp + fpad(k)] = make_float2(0.f, 0.f);
     }
-    for (int i = threadIdx.x; i < 4 * (T + 1); i += blockDim.x) {
-        const int f = i / (T + 1), m = i - f * (T + 1);
-        float2 e = in[(f * 2 + 0) * (T + 1) + m];
-        float2 o = in[(f * 2 + 1) * (T + 1) + m];
-        if (m == 0) { e.y = 0.f; o.y = 0.f; }
-        const float2 n = cadd<float>(e, o), sv = csub<float>(e, o);
-        X[f * Lp + fpad(m)] = make_float2(n.x - sv.y, n.y + sv.x);                // n + i s
-        if (m > 0) X[f * Lp + fpad(L - m)] = make_float2(n.x + sv.y, -n.y + sv.x);   // conj(n) + i conj(s)
+    // four (field, order) items per thread and pass, all loads first
+    for (int i0 = threadIdx.x; i0 < 4 * (T + 1); i0 += 4 * blockDim.x) {
+        float2 ev[4], ov[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int i = min(i0 + u * static_cast<int>(blockDim.x), 4 * (T + 1) - 1);
+            const int f = i / (T + 1), m = i - f * (T + 1);
+            ev[u] = in[(f * 2 + 0) * (T + 1) + m];
+            ov[u] = in[(f * 2 + 1) * (T + 1) + m];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int i = i0 + u * blockDim.x;
+            if (i >= 4 * (T + 1)) break;
+            const int f = i / (T + 1), m = i - f * (T + 1);
+            float2 e = ev[u], o = ov[u];
+            if (m == 0) { e.y = 0.f; o.y = 0.f; }
+            const float2 n = cadd<float>(e, o), sv = csub<float>(e, o);
+            X[f * Lp + fpad(m)] = make_float2(n.x - sv.y, n.y + sv.x);                // n + i s
+            if (m > 0) X[f * Lp + fpad(L - m)] = make_float2(n.x + sv.y, -n.y + sv.x);   // conj(n) + i conj(s)
+        }
     }
     __syncthreads();
     const float2 *G;
@@ -364,13 +377,14 @@ __global__ void __launch_bounds__(64) k3_project(const V2<R> *__restrict__ f2, D
 // path) while the first copies are in flight.
 // ---------------------------------------------------------------------------
 constexpr int kSynRows = 24;
-constexpr int kMaxSynStages = 8;
+constexpr int kMaxSynStages = 6;
 constexpr size_t kSynCtrlBytes = 128;
+static_assert(8 * kMaxSynStages <= static_cast<int>(kSynCtrlBytes), "mbarriers fit the control block");
 
 __host__ inline int synthesis_f32_stages(int J2p) {
     const int per = kSynRows * J2p * static_cast<int>(sizeof(float));
     int ns = (48 * 1024) / per;
-    return ns < 2 ? 2 : (ns > 6 ? 6 : ns);
+    return ns < 2 ? 2 : (ns > kMaxSynStages ? kMaxSynStages : ns);
 }
 __host__ inline size_t synthesis_f32_smem(const Dims &d, int nstages) {
     return kSynCtrlBytes + static_cast<size_t>(nstages) * kSynRows * d.J2p * sizeof(float) +
@@ -382,7 +396,7 @@ __global__ void __launch_bounds__(256) k1_synthesis_f32(const double2 *__restric
                                                         Dims d, const float *__restrict__ pbar,
                                                         const double *__restrict__ syn, float2 *__restrict__ f1,
                                                         int nstages, int *err) {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     uint64_t *mbar = reinterpret_cast<uint64_t *>(smem_raw);                 // [kMaxSynStages]
     float *stage = reinterpret_cast<float *>(smem_raw + kSynCtrlBytes);      // [nstages][kSynRows][J2p]
     const size_t stage_elems = static_cast<size_t>(kSynRows) * d.J2p;
