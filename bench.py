@@ -194,6 +194,20 @@ def reference_arm(args, rank: int, world: int):
 # ---------------------------------------------------------------------------
 # the CUDA arm
 # ---------------------------------------------------------------------------
+def job_rate(local_ms: float, steps: int, world: int, device: str = "cpu"):
+    """Whole-job throughput of `world` replicas that each ran `steps` steps:
+    the slowest rank's time (MAX over ranks) bounds the job, and every rank
+    processed `steps` units.  Returns (max_ms, steps/s of the whole job)."""
+    total_ms = local_ms
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([local_ms], device=device, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return total_ms, world * steps / (total_ms * 1e-3)
+
+
 def time_device(s, state, steps: int, flush):
     """Sum of CUDA-event times of `steps` single-step graph replays, L2 flushed before each."""
     import torch
@@ -305,12 +319,7 @@ def cuda_arm(args, rank: int, world: int):
     with ClockSampler(dev) as clk:
         times = time_device(s, state, args.steps, flush)
     ev1, _, l1 = s.counters()
-    total_ms = float(sum(times))
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    steps_per_s = world * args.steps / (total_ms * 1e-3)
+    total_ms, steps_per_s = job_rate(float(sum(times)), args.steps, world, "cuda")
     clocks = clk.summary()
 
     # kernel-by-kernel profile of the same step (CUDA events between launches)
