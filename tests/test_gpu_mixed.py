@@ -104,3 +104,22 @@ def test_tensor_core_modes_order_of_accuracy():
         s.sync()
     assert e[3] * 10 <= e[2], e
     assert e[3] <= 2 * e[1], e
+
+
+@pytest.mark.parametrize("precision", [1, 3])
+def test_mixed_adjoint_close_to_fp64_adjoint(precision):
+    """The discrete adjoint in a mixed mode (the retape records FP32 grid fields,
+    the transposed transforms run in FP32; sweeps and solves stay FP64): loss
+    and gradient of a 3-step height misfit against the FP64 context's."""
+    T, J, L, M, K, dt = 42, 64, 128, 4, 4, 300.0
+    o = swe.SWE(sht.Grid(T, J, L), swe.default_physics())
+    wl = si.Workload("m", 2, T, J, L, M, K, dt, 1, 1, (100.0, 100.0))
+    u = swe.initial_state(wl, o)
+    rng = np.random.default_rng(5)
+    target = torch.from_numpy(o.height_grid(u) + rng.standard_normal((J, L))).to("cuda")
+    ref_loss, ref_g = _solver(T, J, L, M, K, dt, 0).adjoint_run(_cuda(u), 3, target, nsnapshots=2)
+    loss, g = _solver(T, J, L, M, K, dt, precision).adjoint_run(_cuda(u), 3, target, nsnapshots=2)
+    assert abs(loss - ref_loss) <= 1e-5 * abs(ref_loss), (loss, ref_loss)
+    err = rel_l2(to_numpy(g), to_numpy(ref_g))
+    print(f"precision {precision}: gradient rel L2 vs FP64 adjoint {err}")
+    assert np.all(err <= 1e-5), err
