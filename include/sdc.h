@@ -103,7 +103,8 @@ enum { SDC_METHOD_DSDC = 0, SDC_METHOD_SERIAL_SDC = 1, SDC_METHOD_IMEX2 = 2 };
  * Requirements (else SDC_EINVAL): 1 <= T <= 1023; nlat even, nlat >= (3T+1)/2
  * (alias-free quadratic products), nlat <= 2048; nlon = 2^a 3^b with
  * nlon >= 3T + 1 and nlon <= 2304 (one latitude ring pair's FFTs live in
- * shared memory); 1 <= nodes <= 8; 1 <= sweeps <= 64;
+ * shared memory; SDC_FP64 contexts return SDC_EUNSUPPORTED above 2048
+ * longitudes); 1 <= nodes <= 8; 1 <= sweeps <= 64;
  * dt > 0; phys non-NULL with radius, gravity, mean_depth > 0; precision one of
  * sdc_precision.  cuda_stream is a cudaStream_t (NULL = legacy default
  * stream) used by every later call.  On success *out owns all device memory

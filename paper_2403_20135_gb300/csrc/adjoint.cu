@@ -466,6 +466,7 @@ __global__ void k_scalar_synth_adjoint(const double2 *__restrict__ in, Dims d, c
 template <typename R>
 static cudaError_t configure_adj(const Dims &d, const FftPlan &plan) {
     const size_t sm2 = ring_smem_bytes(plan.L, sizeof(V2<R>), nullptr);
+    if (sm2 == 0) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(k2t_ring<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2);
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(k3t_synth<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -596,6 +596,10 @@ int sdc_create(sdc_ctx **out, int T, int J, int L, int M, int K, double dt, cons
     d.inv_a = 1.0 / phys->radius;
     d.two_omega = 2.0 * phys->omega;
     if (!fft_plan(L, c->plan)) { free_ctx(c); return fail(SDC_EINVAL, "no FFT plan for nlon"); }
+    if (precision == SDC_FP64 && ring_smem_bytes(L, sizeof(double2), nullptr) == 0) {
+        free_ctx(c);
+        return fail(SDC_EUNSUPPORTED, "nlon too long for the FP64 ring kernel (at most 2048 longitudes in FP64)");
+    }
     const int elem = precision == SDC_FP64 ? (int)sizeof(double2) : (int)sizeof(float2);
     if (ring_smem_bytes(L, elem, nullptr) == 0) { free_ctx(c); return fail(SDC_EINVAL, "nlon too large"); }
 

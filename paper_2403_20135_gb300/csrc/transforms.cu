@@ -776,9 +776,11 @@ constexpr int kK3Threads = 64;
 
 template <typename R>
 static cudaError_t configure(const Dims &d, const FftPlan &plan) {
+    // the Stockham ring of this precision (used in FP64 mode) may not fit for the
+    // longest rings; sdc_create refuses FP64 contexts in that case
     const size_t sm2 = ring_smem_bytes(plan.L, sizeof(V2<R>), nullptr);
-    if (sm2 == 0) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(k2_ring<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2);
+    cudaError_t e = cudaSuccess;
+    if (sm2 != 0) e = cudaFuncSetAttribute(k2_ring<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k1_synthesis<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(static_cast<size_t>(d.T + 4) * 4 * sizeof(V2<R>)));
