@@ -272,13 +272,19 @@ cudaError_t enqueue_step(sdc_ctx *c, cudaStream_t s, bool with_resid, int *launc
     const long long se = c->state_elems();
     const int M = c->M, K = c->K;
     cudaError_t e;
-    // E0 = T_E(u_n)
-    e = tendency(c, 1, c->un, se, c->E0, se, s, launches, timer, store_grid ? grid_slot(c, 0) : nullptr);
+    // E0 = T_E(u_n): the transforms here, the vector epilogue inside the first sweep
+    e = tendency(c, 1, c->un, se, nullptr, se, s, launches, timer, store_grid ? grid_slot(c, 0) : nullptr);
     if (e != cudaSuccess) return e;
 
+    const DeviceTables tb = tables(c);
     SweepParams p{};
     p.un = c->un;
     p.lam = c->lam;
+    p.y = c->f3;
+    p.dims = c->d;
+    p.eps = tb.eps;
+    p.epi32 = tb.epi32;
+    p.coef_m = tb.coef_m;
     p.ncoef = c->d.ncoef;
     p.T = c->T;
     p.dt = c->dt;
@@ -291,8 +297,7 @@ cudaError_t enqueue_step(sdc_ctx *c, cudaStream_t s, bool with_resid, int *launc
         const bool first = (k == 0), last = (k == K - 1);
         p.ubase = first ? c->un : c->U;
         p.ustride = first ? 0 : se;
-        p.ebase = first ? c->E0 : c->E;
-        p.estride = first ? 0 : se;
+        p.ybatch = first ? 1 : M;
         const double den = qdelta_den(c, k + 1);
         for (int m = 0; m < M; ++m) p.alpha[m] = c->dt * c->tau[m] / den;
         p.den = c->den + static_cast<size_t>(k) * M * c->d.ncoef;
@@ -307,7 +312,7 @@ cudaError_t enqueue_step(sdc_ctx *c, cudaStream_t s, bool with_resid, int *launc
             p.out = c->U;
             p.ostride = se;
         }
-        e = launch_sweep(p, M, s, launches, timer);
+        e = launch_sweep(p, M, c->precision != SDC_FP64, s, launches, timer);
         if (e != cudaSuccess) return e;
         if (with_resid) {
             e = launch_resid_reduce(c->resid_part, c->sweep_nblocks, M, p.m0, p.m1, c->resid + 3 * k, s, launches,
@@ -315,7 +320,7 @@ cudaError_t enqueue_step(sdc_ctx *c, cudaStream_t s, bool with_resid, int *launc
             if (e != cudaSuccess) return e;
         }
         if (!last) {
-            e = tendency(c, M, c->U, se, c->E, se, s, launches, timer,
+            e = tendency(c, M, c->U, se, nullptr, se, s, launches, timer,
                          store_grid ? grid_slot(c, 1 + k * M) : nullptr);
             if (e != cudaSuccess) return e;
         }

@@ -49,12 +49,18 @@ struct Dims {
 };
 
 // Parameters of the fused quadrature + implicit solve + residual kernel.
+// The explicit tendencies of the nodes come as the projections Y of the
+// preceding tendency batch (the vector epilogue runs inside the sweep).
 struct SweepParams {
     const double2 *un;            // u_n, [3][ncoef]
     const double2 *ubase;         // node j iterate at ubase + j * ustride
     long long ustride;            // 0 on the first sweep (u_j^0 = u_n)
-    const double2 *ebase;         // node j explicit tendency at ebase + j * estride
-    long long estride;
+    const void *y;                // projections [ybatch][next][5] in the transform precision
+    int ybatch;                   // 1: every node takes Y[0] (the first sweep), else M
+    Dims dims;
+    const double *eps;            // epilogue factors (FP64 transforms)
+    const float *epi32;           // epilogue factors (FP32 transforms)
+    const int *coef_m;
     double2 *out;                 // node m result at out + (m - m0) * ostride
     long long ostride;
     const double *lam;            // n(n+1)/a^2 per packed coefficient
@@ -214,6 +220,8 @@ void twiddles(int L, std::vector<double> &re, std::vector<double> &im);   // e^{
 // ---- kernel launchers (transforms.cu, sweep.cu) -------------------------
 // Explicit tendency of B states (K1 -> K2 -> K3a -> K3b).  With tc (FP32
 // transforms only) the two Legendre contractions run on the tensor cores.
+// With tend == nullptr the epilogue is left to the caller, which reads the
+// projections from ws.f3 ([B][next][5] in the transform precision).
 cudaError_t launch_tendency(const Dims &d, const FftPlan &plan, bool fp32, int B, const double2 *states,
                             long long sstride, double2 *tend, long long tstride, const DeviceTables &tb,
                             const Workspace &ws, cudaStream_t s, int *launches, StageTimer *timer = nullptr,
@@ -224,7 +232,7 @@ cudaError_t launch_tc_synthesis(const TcTables &tc, const Dims &d, int B, const 
 cudaError_t launch_tc_projection(const TcTables &tc, const Dims &d, int B, const float2 *f2, float2 *y,
                                  cudaStream_t s, int *launches);
 cudaError_t configure_tc_kernels();
-cudaError_t launch_sweep(const SweepParams &p, int M, cudaStream_t s, int *launches,
+cudaError_t launch_sweep(const SweepParams &p, int M, bool fp32, cudaStream_t s, int *launches,
                          StageTimer *timer = nullptr);
 cudaError_t launch_resid_reduce(const double *part, int nblocks, int M, int m0, int m1,
                                 double *out3, cudaStream_t s, int *launches,

@@ -12,9 +12,12 @@
 //     Phi' = (rhs_Phi - alpha Phibar rhs_div) / (1 + alpha^2 Phibar lambda_n)
 //     div  = rhs_div + alpha lambda_n Phi',  zeta = rhs_zeta
 //   residual R_m - u_m^k accumulated as sum w |r|^2 (w = 1 at m = 0, else 2).
-// All arithmetic is FP64.
+// T_E(u_j^k) is formed here from the projections of the preceding tendency
+// batch by the vector epilogue (epilogue.cuh, in the transform precision);
+// all other arithmetic is FP64.
 #include <cuda_runtime.h>
 
+#include "epilogue.cuh"
 #include "sdc_internal.h"
 
 namespace sdc {
@@ -23,7 +26,7 @@ constexpr int kSweepThreads = 64;
 
 int sweep_blocks(int ncoef) { return (ncoef + kSweepThreads - 1) / kSweepThreads; }
 
-template <int M, bool RESID>
+template <int M, bool RESID, typename R>
 __global__ void __launch_bounds__(kSweepThreads) k4_sweep(SweepParams p) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int nc = p.ncoef;
@@ -34,19 +37,24 @@ __global__ void __launch_bounds__(kSweepThreads) k4_sweep(SweepParams p) {
     if (i < nc) {
         const double lam = p.lam[i];
         const double wgt = (i <= p.T) ? 1.0 : 2.0;      // order m = 0 occupies indices 0..T
+        const int mo = p.coef_m[i];
+        const V2<R> *Y = static_cast<const V2<R> *>(p.y);
         const double2 un_p = p.un[F_PHI * nc + i];
         const double2 un_z = p.un[F_ZETA * nc + i];
         const double2 un_d = p.un[F_DIV * nc + i];
         double2 Fp[M], Fz[M], Fd[M];
         double2 up[M], uz[M], ud[M];
+        double2 ep, ez, ed;                               // T_E of node j (of u_n when ybatch == 1)
+        if (p.ybatch == 1) vector_epilogue<R>(Y, p.dims, i, mo, p.eps, p.lam, p.epi32, ep, ez, ed);
 #pragma unroll
         for (int j = 0; j < M; ++j) {
             const double2 *u = p.ubase + j * p.ustride;
-            const double2 *e = p.ebase + j * p.estride;
             up[j] = u[F_PHI * nc + i];
             uz[j] = u[F_ZETA * nc + i];
             ud[j] = u[F_DIV * nc + i];
-            const double2 ep = e[F_PHI * nc + i], ez = e[F_ZETA * nc + i], ed = e[F_DIV * nc + i];
+            if (p.ybatch != 1)
+                vector_epilogue<R>(Y + static_cast<size_t>(j) * p.dims.next * 5, p.dims, i, mo, p.eps, p.lam,
+                                   p.epi32, ep, ez, ed);
             Fp[j] = make_double2(ep.x - p.phibar * ud[j].x, ep.y - p.phibar * ud[j].y);
             Fz[j] = ez;
             Fd[j] = make_double2(ed.x + lam * up[j].x, ed.y + lam * up[j].y);
@@ -134,13 +142,13 @@ __global__ void k5_resid_reduce(const double *__restrict__ part, int nblocks, in
     }
 }
 
-cudaError_t launch_sweep(const SweepParams &p, int M, cudaStream_t s, int *launches, StageTimer *timer) {
+template <typename R>
+static cudaError_t launch_sweep_t(const SweepParams &p, int M, cudaStream_t s) {
     const int nb = sweep_blocks(p.ncoef);
-    if (timer) timer->mark(STAGE_SWEEP);
-#define SDC_SWEEP_CASE(MM)                                                        \
-    case MM:                                                                      \
-        if (p.resid_part) k4_sweep<MM, true><<<nb, kSweepThreads, 0, s>>>(p);     \
-        else k4_sweep<MM, false><<<nb, kSweepThreads, 0, s>>>(p);                 \
+#define SDC_SWEEP_CASE(MM)                                                           \
+    case MM:                                                                         \
+        if (p.resid_part) k4_sweep<MM, true, R><<<nb, kSweepThreads, 0, s>>>(p);     \
+        else k4_sweep<MM, false, R><<<nb, kSweepThreads, 0, s>>>(p);                 \
         break;
     switch (M) {
         SDC_SWEEP_CASE(1) SDC_SWEEP_CASE(2) SDC_SWEEP_CASE(3) SDC_SWEEP_CASE(4)
@@ -148,8 +156,14 @@ cudaError_t launch_sweep(const SweepParams &p, int M, cudaStream_t s, int *launc
         default: return cudaErrorInvalidValue;
     }
 #undef SDC_SWEEP_CASE
-    if (launches) *launches += 1;
     return cudaGetLastError();
+}
+
+cudaError_t launch_sweep(const SweepParams &p, int M, bool fp32, cudaStream_t s, int *launches, StageTimer *timer) {
+    if (timer) timer->mark(STAGE_SWEEP);
+    const cudaError_t e = fp32 ? launch_sweep_t<float>(p, M, s) : launch_sweep_t<double>(p, M, s);
+    if (launches) *launches += 1;
+    return e;
 }
 
 cudaError_t launch_resid_reduce(const double *part, int nblocks, int M, int m0, int m1, double *out3,

@@ -22,6 +22,7 @@
 #include "fft.cuh"
 #include "fft_pass.cuh"
 #include "async_copy.cuh"
+#include "epilogue.cuh"
 #include "sdc_internal.h"
 
 namespace sdc {
@@ -708,14 +709,8 @@ static int project_f32_threads(int T) {
 }
 
 // ---------------------------------------------------------------------------
-// K3b: per spectral mode (n, m), n = m..T (1/a folded in here):
-//   T_E(zeta)_n = -(1/a) [i m A^_n + n eps_{n+1} B^_{n+1} - (n+1) eps_n B^_{n-1}]
-//   T_E(div)_n  =  (1/a) [i m B^_n - n eps_{n+1} A^_{n+1} + (n+1) eps_n A^_{n-1}] + lambda_n E^_n
-//   T_E(Phi')_n = -(1/a) [i m C^_n + n eps_{n+1} D^_{n+1} - (n+1) eps_n D^_{n-1}]
+// K3b: per spectral mode (n, m), the vector epilogue of epilogue.cuh.
 // ---------------------------------------------------------------------------
-// The arithmetic runs in R (FP32 in the mixed modes, like the rest of the
-// transform, with the per-mode factors from an FP32 table); the tendencies
-// are stored in FP64.
 template <typename R>
 __global__ void k3_epilogue(const V2<R> *__restrict__ y, Dims d, const double *__restrict__ eps,
                             const double *__restrict__ lam, const float *__restrict__ epi32,
@@ -723,43 +718,12 @@ __global__ void k3_epilogue(const V2<R> *__restrict__ y, Dims d, const double *_
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int b = blockIdx.y;
     if (i >= d.ncoef) return;
-    const int T = d.T;
-    const int m = coef_m[i];
-    const int t = i - order_offset(T, m);
-    const int n = m + t;
-    const int e = ext_offset(T, m) + t;
-    const V2<R> *Y = y + static_cast<size_t>(b) * d.next * 5;
-    auto ld = [&](int row, int g) -> V2<R> { return Y[static_cast<size_t>(row) * 5 + g]; };
-    const V2<R> z0 = mk<R>(0, 0);
-    const V2<R> Ah = ld(e, P_A), Bh = ld(e, P_B), Ch = ld(e, P_C), Eh = ld(e, P_E);
-    const V2<R> Au = ld(e + 1, P_A), Bu = ld(e + 1, P_B), Du = ld(e + 1, P_D);
-    const V2<R> Al = t > 0 ? ld(e - 1, P_A) : z0;
-    const V2<R> Bl = t > 0 ? ld(e - 1, P_B) : z0;
-    const V2<R> Dl = t > 0 ? ld(e - 1, P_D) : z0;
-    R cu, cl, lm;
-    if constexpr (sizeof(R) == sizeof(float)) {
-        const float4 f = reinterpret_cast<const float4 *>(epi32)[i];
-        cu = f.x;
-        cl = f.y;
-        lm = f.z;
-    } else {
-        cu = n * eps[e + 1];
-        cl = t > 0 ? (n + 1.0) * eps[e] : 0.0;
-        lm = lam[i];
-    }
-    const R inv_a = R(d.inv_a);
-    const R mm = R(m);
-    // i m X = (-m X.y, m X.x)
-    const R tzx = -inv_a * (-mm * Ah.y + cu * Bu.x - cl * Bl.x);
-    const R tzy = -inv_a * (mm * Ah.x + cu * Bu.y - cl * Bl.y);
-    const R tdx = inv_a * (-mm * Bh.y - cu * Au.x + cl * Al.x) + lm * Eh.x;
-    const R tdy = inv_a * (mm * Bh.x - cu * Au.y + cl * Al.y) + lm * Eh.y;
-    const R tpx = -inv_a * (-mm * Ch.y + cu * Du.x - cl * Dl.x);
-    const R tpy = -inv_a * (mm * Ch.x + cu * Du.y - cl * Dl.y);
+    double2 tp, tz, td;
+    vector_epilogue<R>(y + static_cast<size_t>(b) * d.next * 5, d, i, coef_m[i], eps, lam, epi32, tp, tz, td);
     double2 *out = tend + b * tstride;
-    out[F_PHI * d.ncoef + i] = make_double2(double(tpx), double(tpy));
-    out[F_ZETA * d.ncoef + i] = make_double2(double(tzx), double(tzy));
-    out[F_DIV * d.ncoef + i] = make_double2(double(tdx), double(tdy));
+    out[F_PHI * d.ncoef + i] = tp;
+    out[F_ZETA * d.ncoef + i] = tz;
+    out[F_DIV * d.ncoef + i] = td;
 }
 
 // ---------------------------------------------------------------------------
@@ -884,10 +848,12 @@ static cudaError_t launch_tendency_t(const Dims &d, const FftPlan &plan, int B, 
                                                                                               f3);
         if (launches) ++*launches;
     }
-    if (timer) timer->mark(STAGE_EPILOGUE);
-    k3_epilogue<R><<<dim3((d.ncoef + 127) / 128, B), 128, 0, s>>>(f3, d, tb.eps, tb.lam, tb.epi32, tb.coef_m, tend,
-                                                                  tstride);
-    if (launches) *launches += 2;                  // ring + epilogue
+    if (tend) {
+        if (timer) timer->mark(STAGE_EPILOGUE);
+        k3_epilogue<R><<<dim3((d.ncoef + 127) / 128, B), 128, 0, s>>>(f3, d, tb.eps, tb.lam, tb.epi32, tb.coef_m,
+                                                                      tend, tstride);
+    }
+    if (launches) *launches += tend ? 2 : 1;       // ring (+ epilogue)
     return cudaGetLastError();
 }
 

@@ -198,7 +198,7 @@ def test_zero_steps_and_counters():
     e1, s1, l1 = s.counters()
     assert e1 - e0 == 3 * (1 + (K - 1) * M)          # Table 1
     assert s1 - s0 == 3 * ((K - 1) * M + 1)
-    assert s.launches_per_step() == 5 * K             # K tendencies x 4 kernels + K sweep kernels
+    assert s.launches_per_step() == 4 * K             # K tendency batches x 3 kernels + K sweeps (epilogue inside)
 
 
 def test_invalid_shapes_raise():
