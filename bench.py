@@ -71,20 +71,24 @@ def stage_flops(wl, stage: str, batch: int) -> float:
     raise ValueError(stage)
 
 
-def sweep_flops(wl) -> float:
-    """FP64 flops of one all-node sweep: per mode and node m the quadrature
-    (6 real components x M terms x 2 flops), the right side and the 2x2 solve
-    (about 24 flops), plus forming L_g u_j + T_E(u_j) (8 flops per node)."""
+def sweep_flops(wl, ybatch: int, nupdated: int) -> float:
+    """FP64-mode flops of one sweep kernel per mode: for each updated node the
+    quadrature (6 real components x M terms x 2 flops), the right side and the
+    2x2 solve (about 24 flops); forming L_g u_j + T_E(u_j) (8 flops per node);
+    the vector epilogue of the ybatch projected states (about 36 flops each)."""
     nc = (wl.T + 1) * (wl.T + 2) // 2
     M = wl.nodes
-    return nc * (12.0 * M * M + 24.0 * M + 8.0 * M)
+    return nc * ((12.0 * M + 24.0) * nupdated + 8.0 * M + 36.0 * ybatch)
 
 
-def sweep_bytes(wl, all_nodes: bool) -> float:
+def sweep_bytes(wl, all_nodes: bool, ybatch: int, y_elem: int = 16) -> float:
+    """Bytes one sweep kernel moves per launch: u_n, the M node states, the
+    projections (10 complex values per mode and projected state) and the
+    states it writes (M, or 1 in the last sweep)."""
     nc = (wl.T + 1) * (wl.T + 2) // 2
     M = wl.nodes
-    states = (1 + 2 * M + M) if all_nodes else (1 + 2 * M + 1)
-    return states * 3 * nc * 16.0
+    states = 1 + M + (M if all_nodes else 1)
+    return nc * (states * 3 * 16.0 + ybatch * 10 * y_elem)
 
 
 # ---------------------------------------------------------------------------
@@ -337,9 +341,10 @@ def cuda_arm(args, rank: int, world: int):
                 "peak_kind": "nominal FP64 (no measured FP64 peak)"}
     # the sweep kernel (FP64 in every mode): FP64 flops and the bytes it moves
     sw_ms = prof["sweep"]["ms_per_launch"]
-    sw_all = (K - 1) / K          # share of sweeps that update all M nodes
-    sw_bytes = sw_all * sweep_bytes(wl, True) + (1 - sw_all) * sweep_bytes(wl, False)
-    sw_flops = sweep_flops(wl) * (sw_all + (1 - sw_all) / M)
+    # K sweeps per step: the first reads the projections of one state, the
+    # others of M; sweeps 1..K-1 update all M nodes, the last one node
+    sw_bytes = (sweep_bytes(wl, True, 1) + (K - 2) * sweep_bytes(wl, True, M) + sweep_bytes(wl, False, M)) / K
+    sw_flops = (sweep_flops(wl, 1, M) + (K - 2) * sweep_flops(wl, M, M) + sweep_flops(wl, M, 1)) / K
     roofline_sweep = {"bound": "alu", "achieved": sw_flops / (sw_ms * 1e-3) / 1e12, "peak": FP64_NOMINAL_TFLOPS,
                       "unit": "TFLOP/s", "frac": sw_flops / (sw_ms * 1e-3) / 1e12 / FP64_NOMINAL_TFLOPS,
                       "hbm_gbs": sw_bytes / (sw_ms * 1e-3) / 1e9, "hbm_peak_gbs": peaks["hbm_gbs"],
