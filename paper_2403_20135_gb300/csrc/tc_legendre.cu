@@ -350,21 +350,29 @@ __global__ void k2_split_w(TcTables tc, Dims d, int B, int nbc, const float2 *__
     const int m = g >> 1, p = g & 1;
     const int T = d.T, J2 = d.J2;
     const int c0 = kb / kTcChunkKB * kTcChunkKB, kbc = min(kTcChunkKB, kjb - c0);
-    float v[8][8];                              // [column in block][latitude in k block]
+    // all 32 loads first (clamped to valid addresses), then the zeros of
+    // missing states and latitudes: nothing waits between the loads
+    float2 w[4][8];
+    bool live[4];
 #pragma unroll
     for (int cp = 0; cp < 4; ++cp) {
         const int c = cb * 8 + 2 * cp;          // even: (re, im) of one (b, g) pair
         const int b = c / 10;
-        const float2 *src = nullptr;
-        if (b < B) src = f2 + ((static_cast<size_t>(b) * (T + 1) + m) * 5 + (c - 10 * b) / 2) * 2 * J2 + p * J2;
+        live[cp] = b < B;
+        const int bb = live[cp] ? b : 0, gg = live[cp] ? (c - 10 * b) / 2 : 0;
+        const float2 *src = f2 + ((static_cast<size_t>(bb) * (T + 1) + m) * 5 + gg) * 2 * J2 + p * J2;
+#pragma unroll
+        for (int kr = 0; kr < 8; ++kr) w[cp][kr] = src[min(kb * 8 + kr, J2 - 1)];
+    }
+    float v[8][8];                              // [column in block][latitude in k block]
+#pragma unroll
+    for (int cp = 0; cp < 4; ++cp)
 #pragma unroll
         for (int kr = 0; kr < 8; ++kr) {
-            const int j = kb * 8 + kr;
-            const float2 w = (src && j < J2) ? src[j] : make_float2(0.f, 0.f);
-            v[2 * cp][kr] = w.x;
-            v[2 * cp + 1][kr] = w.y;
+            const bool ok = live[cp] && kb * 8 + kr < J2;
+            v[2 * cp][kr] = ok ? w[cp][kr].x : 0.f;
+            v[2 * cp + 1][kr] = ok ? w[cp][kr].y : 0.f;
         }
-    }
     uint16_t *dst = tc.wb + static_cast<long long>(g) * kNbc3 * kjb * 64 + static_cast<long long>(c0) * kNbc3 * 64 +
                     (cb * kbc + kb - c0) * 64;
 #pragma unroll
@@ -391,13 +399,17 @@ __global__ void k1_prep_split(TcTables tc, const double2 *__restrict__ states, l
     const int n = m + ne;
     const int off = order_offset(T, m);
     const double2 *st = states + b * sstride;
-    auto ld = [&](int f, int k) -> double2 {
-        return (k >= m && k <= T) ? st[f * nc + off + k - m] : make_double2(0.0, 0.0);
-    };
-    const double2 z0 = ld(F_ZETA, n), zm = ld(F_ZETA, n - 1), zp = ld(F_ZETA, n + 1);
-    const double2 d0 = ld(F_DIV, n), dm = ld(F_DIV, n - 1), dp = ld(F_DIV, n + 1);
-    const double2 p0 = ld(F_PHI, n);
+    // loads from clamped degrees first, then zeros outside m..T: no load waits on a branch
+    auto ldc = [&](int f, int k) { return st[f * nc + off + min(max(k, m), T) - m]; };
+    auto in = [&](int k) { return k >= m && k <= T; };
+    double2 z0 = ldc(F_ZETA, n), zm = ldc(F_ZETA, n - 1), zp = ldc(F_ZETA, n + 1);
+    double2 d0 = ldc(F_DIV, n), dm = ldc(F_DIV, n - 1), dp = ldc(F_DIV, n + 1);
+    double2 p0 = ldc(F_PHI, n);
     const double c0 = syn[3 * e], c1 = syn[3 * e + 1], c2 = syn[3 * e + 2];
+    const double2 zero = make_double2(0.0, 0.0);
+    if (!in(n)) z0 = d0 = p0 = zero;
+    if (!in(n - 1)) zm = dm = zero;
+    if (!in(n + 1)) zp = dp = zero;
     const float x[8] = {float(z0.x),
                         float(z0.y),
                         float(p0.x),
