@@ -339,6 +339,12 @@ def cuda_arm(args, rank: int, world: int):
     roofline = {"bound": "alu", "achieved": achieved_tf, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved_tf / FP64_NOMINAL_TFLOPS, "traffic": traffic, "kernel": dom,
                 "peak_kind": "nominal FP64 (no measured FP64 peak)"}
+    # the whole step: algorithmic flops of every stage over the step time
+    step_flops = sum(stage_flops(wl, k, nodes_per_step) for k in ("synthesis", "ring", "analysis"))
+    step_flops += (sweep_flops(wl, 1, M) + (K - 2) * sweep_flops(wl, M, M) + sweep_flops(wl, M, 1))
+    step_tf = step_flops / (total_ms / args.steps * 1e-3) / 1e12
+    roofline_step = {"bound": "alu", "achieved": step_tf, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                     "frac": step_tf / FP64_NOMINAL_TFLOPS, "flops_per_step": step_flops}
     # the sweep kernel (FP64 in every mode): FP64 flops and the bytes it moves
     sw_ms = prof["sweep"]["ms_per_launch"]
     # K sweeps per step: the first reads the projections of one state, the
@@ -432,7 +438,7 @@ def cuda_arm(args, rank: int, world: int):
                        "l2": "flushed (512 MiB write) before every timed step",
                        "parallelism": f"replicas x{world}"},
             "e2e": e2e, "gpu_launches": int(l1 - l0), "clocks": clocks, "roofline": roofline,
-            "roofline_sweep": roofline_sweep,
+            "roofline_sweep": roofline_sweep, "roofline_step": roofline_step,
             "stages": prof, "mixed": mixed,
             "adjoint_fwd_ratio": adjoint["t255"]["step_ratio"] if adjoint else None, "adjoint": adjoint,
             "cpu_baseline": cpu,
