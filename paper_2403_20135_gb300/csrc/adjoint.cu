@@ -20,6 +20,7 @@
 #include <cuda_runtime.h>
 
 #include "fft.cuh"
+#include "fft_pass.cuh"
 #include "sdc_internal.h"
 
 namespace sdc {
@@ -209,6 +210,84 @@ __global__ void k2t_ring(const V2<R> *__restrict__ wbar, const V2<R> *__restrict
         const V2<R> fs = cscale<R>(mul_mi<R>(csub<R>(y, yc)), wm);
         V2<R> se = cadd<R>(fn, fs), so = csub<R>(fn, fs);
         if (m == 0) { se.y = 0; so.y = 0; }
+        o[(f * 2 + 0) * (T + 1) + m] = se;
+        o[(f * 2 + 1) * (T + 1) + m] = so;
+    }
+}
+
+// K2^T in FP32 on the padded radix-16 passes of fft_pass.cuh (as the FP32
+// forward ring): LC > 0 fixes the ring length at compile time.
+template <int LC>
+__global__ void __launch_bounds__(256) k2t_ring_f32(const float2 *__restrict__ wbar, const float2 *__restrict__ gbase,
+                                                    float2 *__restrict__ f1bar, Dims d, FftPlan plan,
+                                                    const float2 *__restrict__ twp, int ntw,
+                                                    const float *__restrict__ rw) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int L = LC > 0 ? LC : plan.L, Lp = fft_padded_len(L);
+    float2 *X = reinterpret_cast<float2 *>(smem_raw);   // [5][Lp]
+    float2 *S = X + 5 * Lp;                              // [5][Lp]
+    float2 *TW = S + 5 * Lp;                             // [ntw]
+    const int j2 = blockIdx.x;
+    const int b = blockIdx.y;
+    const int T = d.T, J2 = d.J2;
+    for (int k = threadIdx.x; k < ntw; k += blockDim.x) TW[k] = twp[k];
+    const float fN = rw[4 * j2], ic2 = 2.f * rw[4 * j2 + 1], wt = rw[4 * j2 + 2], wp = rw[4 * j2 + 3];
+    const float invL = 1.f / float(L);
+    for (int i = threadIdx.x; i < 5 * L; i += blockDim.x) {
+        const int g = i / L, k = i - g * L;
+        float2 z = make_float2(0.f, 0.f);
+        int m = -1;
+        bool conj = false;
+        if (k <= T) m = k;
+        else if (k >= L - T) { m = L - k; conj = true; }
+        if (m >= 0) {
+            const float2 *src = wbar + ((static_cast<size_t>(b) * (T + 1) + m) * 5 + g) * 2 * J2 + j2;
+            const float2 ws = src[0], wa = src[J2];
+            const float wg = (g == P_E) ? wp : wt;
+            const float sc = wg * ((m == 0) ? invL : 0.5f * invL);
+            float2 gn = cscale<float>(cadd<float>(ws, wa), sc), gsth = cscale<float>(csub<float>(ws, wa), sc);
+            if (m == 0) { gn.y = 0.f; gsth.y = 0.f; }
+            if (conj) { gn.y = -gn.y; gsth.y = -gsth.y; }
+            z = make_float2(gn.x - gsth.y, gn.y + gsth.x);   // north + i south
+        }
+        X[g * Lp + fpad(k)] = z;
+    }
+    __syncthreads();
+    const float2 *G;
+    if constexpr (LC > 0) G = fft_passes_ct<LC, 5>(X, S, TW, true);
+    else G = fft_passes(X, S, 5, Lp, plan, TW, true);
+
+    const float2 *gb = gbase + (static_cast<size_t>(b) * J2 + j2) * 4 * L;
+    for (int k = threadIdx.x; k < L; k += blockDim.x) {
+        const int kp = fpad(k);
+        const float2 zz = gb[G_ZETA * L + k], pp = gb[G_PHI * L + k];
+        const float2 uu = gb[G_U * L + k], vv = gb[G_V * L + k];
+        const float2 Ab = G[P_A * Lp + kp], Bb = G[P_B * Lp + kp], Cb = G[P_C * Lp + kp];
+        const float2 Db = G[P_D * Lp + kp], Eb = G[P_E * Lp + kp];
+        const float etaN = zz.x + fN, etaS = zz.y - fN;
+        X[G_ZETA * Lp + kp] = make_float2(Ab.x * uu.x + Bb.x * vv.x, Ab.y * uu.y + Bb.y * vv.y);
+        X[G_PHI * Lp + kp] = make_float2(Cb.x * uu.x + Db.x * vv.x, Cb.y * uu.y + Db.y * vv.y);
+        X[G_U * Lp + kp] = make_float2(Ab.x * etaN + Cb.x * pp.x + Eb.x * uu.x * ic2,
+                                       Ab.y * etaS + Cb.y * pp.y + Eb.y * uu.y * ic2);
+        X[G_V * Lp + kp] = make_float2(Bb.x * etaN + Db.x * pp.x + Eb.x * vv.x * ic2,
+                                       Bb.y * etaS + Db.y * pp.y + Eb.y * vv.y * ic2);
+    }
+    __syncthreads();
+    const float2 *Y;
+    if constexpr (LC > 0) Y = fft_passes_ct<LC, 4>(X, S, TW, false);
+    else Y = fft_passes(X, S, 4, Lp, plan, TW, false);
+
+    float2 *o = f1bar + (static_cast<size_t>(b) * J2 + j2) * 8 * (T + 1);
+    for (int i = threadIdx.x; i < 4 * (T + 1); i += blockDim.x) {
+        const int f = i / (T + 1), m = i - f * (T + 1);
+        const float2 y = Y[f * Lp + fpad(m)];
+        float2 yc = Y[f * Lp + fpad(m == 0 ? 0 : L - m)];
+        yc.y = -yc.y;
+        const float wm = (m == 0) ? 0.5f : 1.f;            // w_m / 2
+        const float2 fn = cscale<float>(cadd<float>(y, yc), wm);
+        const float2 fs = cscale<float>(mul_mi<float>(csub<float>(y, yc)), wm);
+        float2 se = cadd<float>(fn, fs), so = csub<float>(fn, fs);
+        if (m == 0) { se.y = 0.f; so.y = 0.f; }
         o[(f * 2 + 0) * (T + 1) + m] = se;
         o[(f * 2 + 1) * (T + 1) + m] = so;
     }
@@ -465,10 +544,21 @@ __global__ void k_scalar_synth_adjoint(const double2 *__restrict__ in, Dims d, c
 // ---------------------------------------------------------------------------
 template <typename R>
 static cudaError_t configure_adj(const Dims &d, const FftPlan &plan) {
-    const size_t sm2 = ring_smem_bytes(plan.L, sizeof(V2<R>), nullptr);
-    if (sm2 == 0) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(k2t_ring<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2);
-    if (e != cudaSuccess) return e;
+    cudaError_t e = cudaSuccess;
+    if constexpr (sizeof(R) == sizeof(float)) {
+        const int smr = (int)ring_f32_smem_bytes(plan.L, plan.L);
+        for (const void *f : {(const void *)k2t_ring_f32<0>, (const void *)k2t_ring_f32<96>,
+                              (const void *)k2t_ring_f32<192>, (const void *)k2t_ring_f32<384>,
+                              (const void *)k2t_ring_f32<768>, (const void *)k2t_ring_f32<1536>}) {
+            e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smr);
+            if (e != cudaSuccess) return e;
+        }
+    } else {
+        const size_t sm2 = ring_smem_bytes(plan.L, sizeof(V2<R>), nullptr);
+        if (sm2 == 0) return cudaErrorInvalidValue;
+        e = cudaFuncSetAttribute(k2t_ring<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2);
+        if (e != cudaSuccess) return e;
+    }
     return cudaFuncSetAttribute(k3t_synth<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)(static_cast<size_t>(d.T + 4) * 5 * sizeof(V2<R>)));
 }
@@ -494,12 +584,34 @@ static cudaError_t launch_tendency_adjoint_t(const Dims &d, const FftPlan &plan,
     k3t_epilogue<R><<<dim3(rows_blocks, B), kAdjThreads, 0, s>>>(abar, astride, d, tb.eps, tb.row_m, f3);
     k3t_synth<R><<<dim3((d.T + 2) / 2, B, (d.J2 + 63) / 64), 64, static_cast<size_t>(d.T + 4) * 5 * sizeof(V2<R>),
                    s>>>(f3, d, pbar, f2);
-    int nscratch = 0;
-    const size_t sm2 = ring_smem_bytes(plan.L, sizeof(V2<R>), &nscratch);
-    if (sm2 == 0) return cudaErrorInvalidValue;
-    k2t_ring<R><<<dim3(d.J2, B), 256, sm2, s>>>(f2, static_cast<const V2<R> *>(grid_base), f1, d, plan, tw, tb.mu,
-                                               tb.w, nscratch);
-    k1t_project<R><<<dim3(rows_blocks, B), kAdjThreads, 0, s>>>(f1, d, pbar, tb.row_m, f3);
+    if constexpr (sizeof(R) == sizeof(float)) {
+        const dim3 g2(d.J2, B);
+        const size_t sm = ring_f32_smem_bytes(d.L, tb.ntwp);
+        const float2 *gr = static_cast<const float2 *>(grid_base);
+#define SDC_RING_T_F32(LC) \
+    k2t_ring_f32<LC><<<g2, 256, sm, s>>>(f2, gr, f1, d, tb.plan16, tb.twp32, tb.ntwp, tb.ring32)
+        switch (d.L) {
+            case 96: SDC_RING_T_F32(96); break;
+            case 192: SDC_RING_T_F32(192); break;
+            case 384: SDC_RING_T_F32(384); break;
+            case 768: SDC_RING_T_F32(768); break;
+            case 1536: SDC_RING_T_F32(1536); break;
+            default: SDC_RING_T_F32(0); break;
+        }
+#undef SDC_RING_T_F32
+    } else {
+        int nscratch = 0;
+        const size_t sm2 = ring_smem_bytes(plan.L, sizeof(V2<R>), &nscratch);
+        if (sm2 == 0) return cudaErrorInvalidValue;
+        k2t_ring<R><<<dim3(d.J2, B), 256, sm2, s>>>(f2, static_cast<const V2<R> *>(grid_base), f1, d, plan, tw,
+                                                   tb.mu, tb.w, nscratch);
+    }
+    if constexpr (sizeof(R) == sizeof(float)) {
+        const cudaError_t e = launch_synthesis_transpose_f32(d, B, f1, pbar, f3, s);
+        if (e != cudaSuccess) return e;
+    } else {
+        k1t_project<R><<<dim3(rows_blocks, B), kAdjThreads, 0, s>>>(f1, d, pbar, tb.row_m, f3);
+    }
     k1t_epilogue<R><<<dim3((d.ncoef + 127) / 128, B), 128, 0, s>>>(f3, d, tb.syn, tb.coef_m, ubar, ustride);
     if (launches) *launches += 5;
     return cudaGetLastError();

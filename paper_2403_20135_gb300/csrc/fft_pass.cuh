@@ -19,6 +19,10 @@
 namespace sdc {
 
 __host__ __device__ constexpr int fft_padded_len(int L) { return L + (L - 1) / 16 + 1; }
+// shared memory of an FP32 ring kernel: X[5] and S[5] padded, ntw twiddles
+__host__ __device__ inline size_t ring_f32_smem_bytes(int L, int ntw) {
+    return (10 * static_cast<size_t>(fft_padded_len(L)) + static_cast<size_t>(ntw)) * sizeof(float2);
+}
 __device__ __forceinline__ int fpad(int i) { return i + (i >> 4); }
 
 // e^{-2 pi i e / 16} for e = 0..15 (cos, -sin)

@@ -246,6 +246,11 @@ cudaError_t launch_grid_to_spec(const Dims &d, const FftPlan &plan, const double
                                 double2 *spec, const double *pbar, const double *w,
                                 const double2 *tw, double2 *f2, cudaStream_t s);
 
+// Transpose of the FP32 synthesis (adjoint): Z-bar[b][e][4] = sum_j Pbar_e(mu_j)
+// F1-bar[b][j][f][parity(e)][m(e)], with the register-tiled projection kernel.
+cudaError_t launch_synthesis_transpose_f32(const Dims &d, int B, const float2 *f1bar, const float *pbar, float2 *zbar,
+                                           cudaStream_t s);
+
 // ---- adjoint (adjoint.cu) ------------------------------------------------
 cudaError_t configure_adjoint_kernels(const Dims &d, const FftPlan &plan, bool fp32);
 // u-bar (accumulated) += J_E^T a-bar for B states whose forward ring kernel

@@ -225,9 +225,6 @@ __global__ void k2_ring(const V2<R> *__restrict__ f1, V2<R> *__restrict__ f2, Di
 // fields land in X or S by the parity of the pass count, the products are
 // always written to X, the forward result again lands by parity.
 // ---------------------------------------------------------------------------
-__host__ __device__ inline size_t ring_f32_smem_bytes(int L, int ntw) {
-    return (10 * static_cast<size_t>(fft_padded_len(L)) + static_cast<size_t>(ntw)) * sizeof(float2);
-}
 
 // LC > 0: ring length fixed at compile time (LC == plan.L); 0: any length.
 template <int LC>
@@ -548,6 +545,9 @@ constexpr int kPrjDepth = 4;          // per-thread cp.async stages of the table
 __device__ __forceinline__ void cp_async16(void *dst, const void *src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
 }
+__device__ __forceinline__ void cp_async8(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
@@ -556,25 +556,39 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 // shared-memory stages with cp.async (16 bytes per row and 4-latitude
 // block), kPrjDepth - 1 blocks ahead of the FMAs; no block barrier is
 // involved because a lane only reads what it copied.
-template <bool VEC, bool ASYNC>
-__global__ void __launch_bounds__(512) k3_project_f32(const float2 *__restrict__ f2, Dims d,
+// NF = 5: the analysis projection, W = F2[b][m][g][parity][j] (contiguous per
+// order), Y[b][e][g].  NF = 4: the transpose of the synthesis in the adjoint,
+// W = F1-bar[b][j][f][parity][m] gathered per order into the same
+// [f][parity][j] arrangement, Z-bar[b][e][f].
+template <bool VEC, bool ASYNC, int NF>
+__global__ void __launch_bounds__(512) k3_project_f32(const float2 *__restrict__ src, Dims d,
                                                       const float *__restrict__ pbar, float2 *__restrict__ y) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float2 *ws = reinterpret_cast<float2 *>(smem_raw);   // [2][10][J2]
-    float4 *pst = reinterpret_cast<float4 *>(ws + 2 * 10 * d.J2);   // [kPrjDepth][4 rows][blockDim] (ASYNC)
+    float2 *ws = reinterpret_cast<float2 *>(smem_raw);   // [2][2 NF][J2]
+    float4 *pst = reinterpret_cast<float4 *>(ws + 2 * 2 * NF * d.J2);   // [kPrjDepth][4 rows][blockDim] (ASYNC)
     const int T = d.T, J2 = d.J2;
     const int b = blockIdx.x;
     const int m1 = blockIdx.y, m2 = T - blockIdx.y;
     const int norders = (m2 > m1) ? 2 : 1;
     for (int h = 0; h < norders; ++h) {
-        const float2 *src = f2 + (static_cast<size_t>(b) * (T + 1) + (h ? m2 : m1)) * 10 * J2;
-        if (VEC) {                                        // 10 J2 float2 = 5 J2 16-byte pieces, asynchronous
-            for (int i = threadIdx.x; i < 5 * J2; i += blockDim.x) cp_async16(ws + h * 10 * J2 + 2 * i, src + 2 * i);
-        } else {
-            for (int i = threadIdx.x; i < 10 * J2; i += blockDim.x) ws[h * 10 * J2 + i] = src[i];
+        float2 *dst = ws + h * 2 * NF * J2;
+        const int mh = h ? m2 : m1;
+        if constexpr (NF == 5) {
+            const float2 *w = src + (static_cast<size_t>(b) * (T + 1) + mh) * 10 * J2;
+            if (VEC) {                                    // 10 J2 float2 = 5 J2 16-byte pieces, asynchronous
+                for (int i = threadIdx.x; i < 5 * J2; i += blockDim.x) cp_async16(dst + 2 * i, w + 2 * i);
+            } else {
+                for (int i = threadIdx.x; i < 10 * J2; i += blockDim.x) dst[i] = w[i];
+            }
+        } else {                                          // gather (f, parity) columns of order mh, 8 bytes each
+            const float2 *w = src + static_cast<size_t>(b) * J2 * 8 * (T + 1) + mh;
+            for (int i = threadIdx.x; i < 8 * J2; i += blockDim.x) {
+                const int fp = i / J2, j = i - fp * J2;
+                cp_async8(dst + i, w + (static_cast<size_t>(j) * 8 + fp) * (T + 1));
+            }
         }
     }
-    if (VEC) {
+    if (VEC || NF != 5) {
         cp_async_commit();
         cp_async_wait<0>();
     }
@@ -599,12 +613,12 @@ __global__ void __launch_bounds__(512) k3_project_f32(const float2 *__restrict__
         const float *pr[4];
 #pragma unroll
         for (int r = 0; r < 4; ++r) pr[r] = pbar + static_cast<size_t>(e0 + 2 * min(r, nr - 1)) * d.J2p;
-        const float2 *W = ws + h * 10 * J2 + p * J2;
-        float2 acc[4][5];
+        const float2 *W = ws + h * 2 * NF * J2 + p * J2;
+        float2 acc[4][NF];
 #pragma unroll
         for (int r = 0; r < 4; ++r)
 #pragma unroll
-            for (int g = 0; g < 5; ++g) acc[r][g] = make_float2(0.f, 0.f);
+            for (int g = 0; g < NF; ++g) acc[r][g] = make_float2(0.f, 0.f);
         int jt = 0;                                      // first latitude of the scalar tail
         if (VEC) {
             jt = J2 & ~3;
@@ -634,7 +648,7 @@ __global__ void __launch_bounds__(512) k3_project_f32(const float2 *__restrict__
                     pv[r][0] = v.x; pv[r][1] = v.y; pv[r][2] = v.z; pv[r][3] = v.w;
                 }
 #pragma unroll
-                for (int g = 0; g < 5; ++g) {
+                for (int g = 0; g < NF; ++g) {
                     const float4 wa = *reinterpret_cast<const float4 *>(W + g * 2 * J2 + j);
                     const float4 wb = *reinterpret_cast<const float4 *>(W + g * 2 * J2 + j + 2);
 #pragma unroll
@@ -652,7 +666,7 @@ __global__ void __launch_bounds__(512) k3_project_f32(const float2 *__restrict__
 #pragma unroll
             for (int r = 0; r < 4; ++r) pv[r] = pr[r][j];
 #pragma unroll
-            for (int g = 0; g < 5; ++g) {
+            for (int g = 0; g < NF; ++g) {
                 const float2 w = W[g * 2 * J2 + j];
 #pragma unroll
                 for (int r = 0; r < 4; ++r) {
@@ -664,7 +678,7 @@ __global__ void __launch_bounds__(512) k3_project_f32(const float2 *__restrict__
 #pragma unroll
         for (int r = 0; r < 4; ++r)
 #pragma unroll
-            for (int g = 0; g < 5; ++g)
+            for (int g = 0; g < NF; ++g)
 #pragma unroll
                 for (int o = 1; o < kPrjParts; o <<= 1) {
                     acc[r][g].x += __shfl_xor_sync(0xffffffffu, acc[r][g].x, o);
@@ -674,9 +688,9 @@ __global__ void __launch_bounds__(512) k3_project_f32(const float2 *__restrict__
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
                 if (r >= nr) break;
-                float2 *o = y + (static_cast<size_t>(b) * d.next + e0 + 2 * r) * 5;
+                float2 *o = y + (static_cast<size_t>(b) * d.next + e0 + 2 * r) * NF;
 #pragma unroll
-                for (int g = 0; g < 5; ++g) o[g] = acc[r][g];
+                for (int g = 0; g < NF; ++g) o[g] = acc[r][g];
             }
         }
     }
@@ -684,8 +698,8 @@ __global__ void __launch_bounds__(512) k3_project_f32(const float2 *__restrict__
 
 // shared memory of a K3a (FP32) block; the per-lane cp.async stages are
 // used when the W rows leave room for them (and J2 is even)
-static bool project_f32_async(const Dims &d, int nthreads, size_t *bytes) {
-    const size_t w = 2 * 10 * static_cast<size_t>(d.J2) * sizeof(float2);
+static bool project_f32_async(const Dims &d, int nthreads, size_t *bytes, int nf = 5) {
+    const size_t w = 2 * 2 * static_cast<size_t>(nf) * d.J2 * sizeof(float2);
     const size_t st = static_cast<size_t>(kPrjDepth) * 4 * nthreads * sizeof(float4);
     const bool async = d.J2 % 2 == 0 && w + st <= 200 * 1024;
     *bytes = async ? w + st : w;
@@ -761,11 +775,17 @@ static cudaError_t configure(const Dims &d, const FftPlan &plan) {
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k1_synthesis_f32<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sms);
     if (e != cudaSuccess) return e;
-    size_t smp = 0;
-    project_f32_async(d, project_f32_threads(d.T), &smp);
-    for (const void *f : {(const void *)k3_project_f32<true, true>, (const void *)k3_project_f32<true, false>,
-                          (const void *)k3_project_f32<false, false>}) {
+    size_t smp = 0, smq = 0;
+    project_f32_async(d, project_f32_threads(d.T), &smp, 5);
+    project_f32_async(d, project_f32_threads(d.T), &smq, 4);
+    for (const void *f : {(const void *)k3_project_f32<true, true, 5>, (const void *)k3_project_f32<true, false, 5>,
+                          (const void *)k3_project_f32<false, false, 5>}) {
         e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smp);
+        if (e != cudaSuccess) return e;
+    }
+    for (const void *f : {(const void *)k3_project_f32<true, true, 4>, (const void *)k3_project_f32<true, false, 4>,
+                          (const void *)k3_project_f32<false, false, 4>}) {
+        e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smq);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -838,9 +858,9 @@ static cudaError_t launch_tendency_t(const Dims &d, const FftPlan &plan, int B, 
             const int nt = project_f32_threads(d.T);
             size_t smp = 0;
             const bool async = project_f32_async(d, nt, &smp);
-            if (d.J2 % 2 != 0) k3_project_f32<false, false><<<g3, nt, smp, s>>>(f2, d, pbar, f3);
-            else if (async) k3_project_f32<true, true><<<g3, nt, smp, s>>>(f2, d, pbar, f3);
-            else k3_project_f32<true, false><<<g3, nt, smp, s>>>(f2, d, pbar, f3);
+            if (d.J2 % 2 != 0) k3_project_f32<false, false, 5><<<g3, nt, smp, s>>>(f2, d, pbar, f3);
+            else if (async) k3_project_f32<true, true, 5><<<g3, nt, smp, s>>>(f2, d, pbar, f3);
+            else k3_project_f32<true, false, 5><<<g3, nt, smp, s>>>(f2, d, pbar, f3);
             if (launches) ++*launches;
         }
     } else {
@@ -864,6 +884,18 @@ cudaError_t configure_transform_kernels(const Dims &d, const FftPlan &plan, bool
     e = cudaFuncSetAttribute(k_scalar_ring_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(k_scalar_ring_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+}
+
+cudaError_t launch_synthesis_transpose_f32(const Dims &d, int B, const float2 *f1bar, const float *pbar, float2 *zbar,
+                                           cudaStream_t s) {
+    const dim3 g3(B, (d.T + 2) / 2);
+    const int nt = project_f32_threads(d.T);
+    size_t smp = 0;
+    const bool async = project_f32_async(d, nt, &smp, 4);
+    if (d.J2 % 2 != 0) k3_project_f32<false, false, 4><<<g3, nt, smp, s>>>(f1bar, d, pbar, zbar);
+    else if (async) k3_project_f32<true, true, 4><<<g3, nt, smp, s>>>(f1bar, d, pbar, zbar);
+    else k3_project_f32<true, false, 4><<<g3, nt, smp, s>>>(f1bar, d, pbar, zbar);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_tendency(const Dims &d, const FftPlan &plan, bool fp32, int B, const double2 *states,
