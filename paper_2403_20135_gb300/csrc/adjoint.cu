@@ -582,8 +582,13 @@ static cudaError_t launch_tendency_adjoint_t(const Dims &d, const FftPlan &plan,
     V2<R> *f3 = static_cast<V2<R> *>(ws.f3);
     const int rows_blocks = (d.next + kAdjThreads - 1) / kAdjThreads;
     k3t_epilogue<R><<<dim3(rows_blocks, B), kAdjThreads, 0, s>>>(abar, astride, d, tb.eps, tb.row_m, f3);
-    k3t_synth<R><<<dim3((d.T + 2) / 2, B, (d.J2 + 63) / 64), 64, static_cast<size_t>(d.T + 4) * 5 * sizeof(V2<R>),
-                   s>>>(f3, d, pbar, f2);
+    if constexpr (sizeof(R) == sizeof(float)) {
+        const cudaError_t e = launch_projection_transpose_f32(d, B, f3, pbar, f2, tb.err, s);
+        if (e != cudaSuccess) return e;
+    } else {
+        k3t_synth<R><<<dim3((d.T + 2) / 2, B, (d.J2 + 63) / 64), 64,
+                       static_cast<size_t>(d.T + 4) * 5 * sizeof(V2<R>), s>>>(f3, d, pbar, f2);
+    }
     if constexpr (sizeof(R) == sizeof(float)) {
         const dim3 g2(d.J2, B);
         const size_t sm = ring_f32_smem_bytes(d.L, tb.ntwp);

@@ -384,21 +384,26 @@ __host__ inline int synthesis_f32_stages(int J2p) {
     int ns = (48 * 1024) / per;
     return ns < 2 ? 2 : (ns > kMaxSynStages ? kMaxSynStages : ns);
 }
-__host__ inline size_t synthesis_f32_smem(const Dims &d, int nstages) {
+__host__ inline size_t synthesis_f32_smem(const Dims &d, int nstages, int nf = 4) {
     return kSynCtrlBytes + static_cast<size_t>(nstages) * kSynRows * d.J2p * sizeof(float) +
-           static_cast<size_t>(d.T + 4) * 4 * sizeof(float2);
+           static_cast<size_t>(d.T + 4) * nf * sizeof(float2);
 }
 
-template <int S>
+// NF = 4: the synthesis (coefficients prepared from the FP64 states, output
+// F1[b][j][f][parity][m]).  NF = 5: the transpose of the analysis projection
+// in the adjoint (coefficients = the rows Y-bar[b][e][5], output
+// W-bar[b][m][g][parity][j]).
+template <int S, int NF>
 __global__ void __launch_bounds__(256) k1_synthesis_f32(const double2 *__restrict__ states, long long sstride,
-                                                        Dims d, const float *__restrict__ pbar,
+                                                        const float2 *__restrict__ ybar, Dims d,
+                                                        const float *__restrict__ pbar,
                                                         const double *__restrict__ syn, float2 *__restrict__ f1,
                                                         int nstages, int *err) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     uint64_t *mbar = reinterpret_cast<uint64_t *>(smem_raw);                 // [kMaxSynStages]
     float *stage = reinterpret_cast<float *>(smem_raw + kSynCtrlBytes);      // [nstages][kSynRows][J2p]
     const size_t stage_elems = static_cast<size_t>(kSynRows) * d.J2p;
-    float2 *cf = reinterpret_cast<float2 *>(stage + nstages * stage_elems);  // [rows][4]
+    float2 *cf = reinterpret_cast<float2 *>(stage + nstages * stage_elems);  // [rows][NF]
     const int T = d.T;
     const int b = blockIdx.x;
     const int m1 = blockIdx.y, m2 = T - blockIdx.y;
@@ -430,9 +435,19 @@ __global__ void __launch_bounds__(256) k1_synthesis_f32(const double2 *__restric
         for (; issued < min(nstages, nch); ++issued) issue(issued);
     }
 
+    if constexpr (NF == 5) {                            // the rows of both orders, 8 bytes per piece
+        for (int i = threadIdx.x; i < rows * 5; i += blockDim.x) {
+            const int r = i / 5, g = i - r * 5;
+            const int m = (r < nn1) ? m1 : m2;
+            const int t = (r < nn1) ? r : r - nn1;
+            cp_async8(cf + i, ybar + (static_cast<size_t>(b) * d.next + ext_offset(T, m) + t) * 5 + g);
+        }
+        cp_async_commit();
+        cp_async_wait<0>();
+    }
     const double2 *st = states + b * sstride;
     const int nc = d.ncoef;
-    for (int r = threadIdx.x; r < rows; r += blockDim.x) {
+    for (int r = threadIdx.x; NF == 4 && r < rows; r += blockDim.x) {
         const int m = (r < nn1) ? m1 : m2;
         const int t = (r < nn1) ? r : r - nn1;
         const int n = m + t;
@@ -457,17 +472,17 @@ __global__ void __launch_bounds__(256) k1_synthesis_f32(const double2 *__restric
     const int j0 = 4 * (threadIdx.x / S);
     const bool active = j0 < d.J2;
     const int jl = active ? j0 : 0;                      // idle lanes read a valid column and store nothing
-    float2 ae[4][4], ao[4][4];                           // [field][latitude]
+    float2 ae[NF][4], ao[NF][4];                         // [field][latitude]
     auto reset = [&]() {
 #pragma unroll
-        for (int f = 0; f < 4; ++f)
+        for (int f = 0; f < NF; ++f)
 #pragma unroll
             for (int k = 0; k < 4; ++k) ae[f][k] = ao[f][k] = make_float2(0.f, 0.f);
     };
-    auto accum = [&](float2 (&a)[4][4], const float4 pv4, const float2 *c) {
+    auto accum = [&](float2 (&a)[NF][4], const float4 pv4, const float2 *c) {
         const float pv[4] = {pv4.x, pv4.y, pv4.z, pv4.w};
 #pragma unroll
-        for (int f = 0; f < 4; ++f) {
+        for (int f = 0; f < NF; ++f) {
             const float2 cc = c[f];
 #pragma unroll
             for (int k = 0; k < 4; ++k) a[f][k] = caxpy(pv[k], cc, a[f][k]);
@@ -484,22 +499,22 @@ __global__ void __launch_bounds__(256) k1_synthesis_f32(const double2 *__restric
             break;
         }
         const float *P = stage + (c % nstages) * stage_elems + jl;
-        const float2 *cc = cf + ((c >= nch1 ? nn1 : 0) + t0) * 4;
+        const float2 *cc = cf + ((c >= nch1 ? nn1 : 0) + t0) * NF;
 #pragma unroll 4
         for (int u = part; 2 * u < cnt; u += S) {
             const int i0 = 2 * u;
             const float4 pe = *reinterpret_cast<const float4 *>(P + i0 * d.J2p);
             if (i0 + 1 < cnt) {
                 const float4 po = *reinterpret_cast<const float4 *>(P + (i0 + 1) * d.J2p);
-                accum(ae, pe, cc + i0 * 4);
-                accum(ao, po, cc + (i0 + 1) * 4);
+                accum(ae, pe, cc + i0 * NF);
+                accum(ao, po, cc + (i0 + 1) * NF);
             } else {
-                accum(ae, pe, cc + i0 * 4);
+                accum(ae, pe, cc + i0 * NF);
             }
         }
         if (c == nch1 - 1 || c == nch - 1) {             // end of an order: reduce and store
 #pragma unroll
-            for (int f = 0; f < 4; ++f)
+            for (int f = 0; f < NF; ++f)
 #pragma unroll
                 for (int k = 0; k < 4; ++k)
 #pragma unroll
@@ -510,14 +525,27 @@ __global__ void __launch_bounds__(256) k1_synthesis_f32(const double2 *__restric
                         ao[f][k].y += __shfl_xor_sync(0xffffffffu, ao[f][k].y, o);
                     }
             if (active && part == 0) {
+                if constexpr (NF == 4) {
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    if (j0 + k >= d.J2) break;
-                    float2 *o = f1 + (static_cast<size_t>(b) * d.J2 + j0 + k) * (4 * 2 * (T + 1)) + m;
+                    for (int k = 0; k < 4; ++k) {
+                        if (j0 + k >= d.J2) break;
+                        float2 *o = f1 + (static_cast<size_t>(b) * d.J2 + j0 + k) * (4 * 2 * (T + 1)) + m;
 #pragma unroll
-                    for (int f = 0; f < 4; ++f) {
-                        o[(f * 2 + 0) * (T + 1)] = ae[f][k];
-                        o[(f * 2 + 1) * (T + 1)] = ao[f][k];
+                        for (int f = 0; f < 4; ++f) {
+                            o[(f * 2 + 0) * (T + 1)] = ae[f][k];
+                            o[(f * 2 + 1) * (T + 1)] = ao[f][k];
+                        }
+                    }
+                } else {
+                    float2 *o = f1 + (static_cast<size_t>(b) * (T + 1) + m) * 10 * d.J2 + j0;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        if (j0 + k >= d.J2) break;
+#pragma unroll
+                        for (int f = 0; f < 5; ++f) {
+                            o[(f * 2 + 0) * d.J2 + k] = ae[f][k];
+                            o[(f * 2 + 1) * d.J2 + k] = ao[f][k];
+                        }
                     }
                 }
             }
@@ -542,15 +570,6 @@ __global__ void __launch_bounds__(256) k1_synthesis_f32(const double2 *__restric
 constexpr int kPrjParts = 4;
 constexpr int kPrjDepth = 4;          // per-thread cp.async stages of the table rows (ASYNC)
 
-__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async8(void *dst, const void *src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 // ASYNC: each lane streams its own four rows through kPrjDepth private
 // shared-memory stages with cp.async (16 bytes per row and 4-latitude
@@ -770,11 +789,16 @@ static cudaError_t configure(const Dims &d, const FftPlan &plan) {
         e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smr);
         if (e != cudaSuccess) return e;
     }
-    const int sms = (int)synthesis_f32_smem(d, synthesis_f32_stages(d.J2p));
-    e = cudaFuncSetAttribute(k1_synthesis_f32<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sms);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k1_synthesis_f32<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sms);
-    if (e != cudaSuccess) return e;
+    const int sms = (int)synthesis_f32_smem(d, synthesis_f32_stages(d.J2p), 4);
+    const int sms5 = (int)synthesis_f32_smem(d, synthesis_f32_stages(d.J2p), 5);
+    for (const void *f : {(const void *)k1_synthesis_f32<2, 4>, (const void *)k1_synthesis_f32<1, 4>}) {
+        e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, sms);
+        if (e != cudaSuccess) return e;
+    }
+    for (const void *f : {(const void *)k1_synthesis_f32<2, 5>, (const void *)k1_synthesis_f32<1, 5>}) {
+        e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, sms5);
+        if (e != cudaSuccess) return e;
+    }
     size_t smp = 0, smq = 0;
     project_f32_async(d, project_f32_threads(d.T), &smp, 5);
     project_f32_async(d, project_f32_threads(d.T), &smq, 4);
@@ -817,11 +841,11 @@ static cudaError_t launch_tendency_t(const Dims &d, const FftPlan &plan, int B, 
             const int ns = synthesis_f32_stages(d.J2p);
             const size_t smk = synthesis_f32_smem(d, ns);
             if (g4 <= 128)
-                k1_synthesis_f32<2><<<gs, (g4 * 2 + 31) / 32 * 32, smk, s>>>(states, sstride, d, pbar, tb.syn, f1,
-                                                                           ns, tb.err);
+                k1_synthesis_f32<2, 4><<<gs, (g4 * 2 + 31) / 32 * 32, smk, s>>>(states, sstride, nullptr, d, pbar,
+                                                                              tb.syn, f1, ns, tb.err);
             else
-                k1_synthesis_f32<1><<<gs, (g4 + 31) / 32 * 32, smk, s>>>(states, sstride, d, pbar, tb.syn, f1, ns,
-                                                                       tb.err);
+                k1_synthesis_f32<1, 4><<<gs, (g4 + 31) / 32 * 32, smk, s>>>(states, sstride, nullptr, d, pbar, tb.syn,
+                                                                          f1, ns, tb.err);
             if (launches) ++*launches;
         }
     } else {
@@ -884,6 +908,21 @@ cudaError_t configure_transform_kernels(const Dims &d, const FftPlan &plan, bool
     e = cudaFuncSetAttribute(k_scalar_ring_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(k_scalar_ring_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+}
+
+cudaError_t launch_projection_transpose_f32(const Dims &d, int B, const float2 *ybar, const float *pbar,
+                                            float2 *wbar, int *err, cudaStream_t s) {
+    const int g4 = (d.J2 + 3) / 4;
+    const dim3 gs(B, (d.T + 2) / 2);
+    const int ns = synthesis_f32_stages(d.J2p);
+    const size_t smk = synthesis_f32_smem(d, ns, 5);
+    if (g4 <= 128)
+        k1_synthesis_f32<2, 5><<<gs, (g4 * 2 + 31) / 32 * 32, smk, s>>>(nullptr, 0, ybar, d, pbar, nullptr, wbar,
+                                                                      ns, err);
+    else
+        k1_synthesis_f32<1, 5><<<gs, (g4 + 31) / 32 * 32, smk, s>>>(nullptr, 0, ybar, d, pbar, nullptr, wbar, ns,
+                                                                  err);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_synthesis_transpose_f32(const Dims &d, int B, const float2 *f1bar, const float *pbar, float2 *zbar,
