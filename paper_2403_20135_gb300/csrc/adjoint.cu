@@ -216,7 +216,8 @@ __global__ void k2t_ring(const V2<R> *__restrict__ wbar, const V2<R> *__restrict
 }
 
 // K2^T in FP32 on the padded radix-16 passes of fft_pass.cuh (as the FP32
-// forward ring): LC > 0 fixes the ring length at compile time.
+// forward ring): LC > 0 fixes the ring length at compile time.  W-bar comes
+// in the layout [b][j2][g][parity][m] (m fastest: the fill loads coalesce).
 template <int LC>
 __global__ void __launch_bounds__(256) k2t_ring_f32(const float2 *__restrict__ wbar, const float2 *__restrict__ gbase,
                                                     float2 *__restrict__ f1bar, Dims d, FftPlan plan,
@@ -241,8 +242,8 @@ __global__ void __launch_bounds__(256) k2t_ring_f32(const float2 *__restrict__ w
         if (k <= T) m = k;
         else if (k >= L - T) { m = L - k; conj = true; }
         if (m >= 0) {
-            const float2 *src = wbar + ((static_cast<size_t>(b) * (T + 1) + m) * 5 + g) * 2 * J2 + j2;
-            const float2 ws = src[0], wa = src[J2];
+            const float2 *src = wbar + (static_cast<size_t>(b) * J2 + j2) * 10 * (T + 1) + g * 2 * (T + 1) + m;
+            const float2 ws = src[0], wa = src[T + 1];
             const float wg = (g == P_E) ? wp : wt;
             const float sc = wg * ((m == 0) ? invL : 0.5f * invL);
             float2 gn = cscale<float>(cadd<float>(ws, wa), sc), gsth = cscale<float>(csub<float>(ws, wa), sc);

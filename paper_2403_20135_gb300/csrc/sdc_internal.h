@@ -250,9 +250,10 @@ cudaError_t launch_grid_to_spec(const Dims &d, const FftPlan &plan, const double
 // F1-bar[b][j][f][parity(e)][m(e)], with the register-tiled projection kernel.
 cudaError_t launch_synthesis_transpose_f32(const Dims &d, int B, const float2 *f1bar, const float *pbar, float2 *zbar,
                                            cudaStream_t s);
-// Transpose of the FP32 analysis projection (adjoint): W-bar[b][m][g][parity][j]
+// Transpose of the FP32 analysis projection (adjoint): W-bar[b][j][g][parity][m]
 // = sum over rows e of order m with that parity of Pbar_e(mu_j) Y-bar[b][e][g],
-// with the staged synthesis kernel.
+// with the staged synthesis kernel (m fastest, as the FP32 ring transpose
+// reads it).
 cudaError_t launch_projection_transpose_f32(const Dims &d, int B, const float2 *ybar, const float *pbar,
                                             float2 *wbar, int *err, cudaStream_t s);
 

@@ -392,7 +392,7 @@ __host__ inline size_t synthesis_f32_smem(const Dims &d, int nstages, int nf = 4
 // NF = 4: the synthesis (coefficients prepared from the FP64 states, output
 // F1[b][j][f][parity][m]).  NF = 5: the transpose of the analysis projection
 // in the adjoint (coefficients = the rows Y-bar[b][e][5], output
-// W-bar[b][m][g][parity][j]).
+// W-bar[b][j][g][parity][m], the layout the FP32 ring transpose reads).
 template <int S, int NF>
 __global__ void __launch_bounds__(256) k1_synthesis_f32(const double2 *__restrict__ states, long long sstride,
                                                         const float2 *__restrict__ ybar, Dims d,
@@ -537,14 +537,14 @@ __global__ void __launch_bounds__(256) k1_synthesis_f32(const double2 *__restric
                         }
                     }
                 } else {
-                    float2 *o = f1 + (static_cast<size_t>(b) * (T + 1) + m) * 10 * d.J2 + j0;
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
                         if (j0 + k >= d.J2) break;
+                        float2 *o = f1 + (static_cast<size_t>(b) * d.J2 + j0 + k) * (5 * 2 * (T + 1)) + m;
 #pragma unroll
                         for (int f = 0; f < 5; ++f) {
-                            o[(f * 2 + 0) * d.J2 + k] = ae[f][k];
-                            o[(f * 2 + 1) * d.J2 + k] = ao[f][k];
+                            o[(f * 2 + 0) * (T + 1)] = ae[f][k];
+                            o[(f * 2 + 1) * (T + 1)] = ao[f][k];
                         }
                     }
                 }
