@@ -73,10 +73,17 @@ typedef enum {
 
 /* Option keys for sdc_set_option. */
 typedef enum {
-    /* MIN-SR-FLEX diagonal q^Delta_{m,m} = tau_m / q(k) at sweep k (Sec. 4.2).
-     * The paper always runs K = M; for k > M the value is
-     * SDC_QDELTA_CLAMPED (default): q(k) = min(k, M), or
-     * SDC_QDELTA_LITERAL: q(k) = k. */
+    /* Diagonal coefficients q^Delta_{m,m} of the implicit part in Eq. (7)
+     * (Sec. 4.2), at sweep k = 1..K:
+     * SDC_QDELTA_CLAMPED (default): MIN-SR-FLEX tau_m / q(k) with
+     *   q(k) = min(k, M) (the paper always runs K = M);
+     * SDC_QDELTA_LITERAL: MIN-SR-FLEX with q(k) = k;
+     * SDC_QDELTA_MIN_SR_NS: tau_m / M in every sweep (Q - diag(q^Delta) is
+     *   nilpotent: the iteration's non-stiff limit);
+     * SDC_QDELTA_IMPLICIT_EULER: tau_m in every sweep (one implicit Euler
+     *   step from t_n to each node).
+     * Any other value returns SDC_EINVAL.  Changing the rule re-uploads the
+     * solve denominators and drops the captured graphs. */
     SDC_OPT_QDELTA_RULE = 1,
     /* The integrator sdc_step / sdc_run / sdc_profile_step advance with:
      * SDC_METHOD_DSDC (default): diagonal IMEX SDC, Algorithm 2, Eq. (7);
@@ -94,7 +101,7 @@ typedef enum {
      * max(2 nodes, 4) extra states (SDC_ECUDA / SDC_ENOMEM on failure). */
     SDC_OPT_METHOD = 2
 } sdc_option;
-enum { SDC_QDELTA_CLAMPED = 0, SDC_QDELTA_LITERAL = 1 };
+enum { SDC_QDELTA_CLAMPED = 0, SDC_QDELTA_LITERAL = 1, SDC_QDELTA_MIN_SR_NS = 2, SDC_QDELTA_IMPLICIT_EULER = 3 };
 enum { SDC_METHOD_DSDC = 0, SDC_METHOD_SERIAL_SDC = 1, SDC_METHOD_IMEX2 = 2 };
 
 /* Create a solver for truncation T on an nlat x nlon Gauss grid with M

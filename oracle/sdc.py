@@ -7,7 +7,11 @@ Test infrastructure only (see the package docstring).
   with l_j the Lagrange basis on the nodes.
 * MIN-SR-FLEX (Sec. 4.2): q^Delta_{m,m} = tau_m / k at sweep k (k = 1..K).  The
   paper always runs K = M; for sweeps k > M this oracle offers two readings,
-  "clamped" q(k) = min(k, M) (default) and "literal" q(k) = k.
+  "clamped" q(k) = min(k, M) (default) and "literal" q(k) = k.  Two further
+  diagonals from the family the paper points to for other coefficient
+  choices (Sec. 4.2, Sec. 6): "min-sr-ns" q^Delta_{m,m} = tau_m / M in every
+  sweep, and "ie" q^Delta_{m,m} = tau_m in every sweep (each node one
+  implicit Euler step from t_n).
 * Node update, Eq. (7): u_m^{k+1} = u_n + dt sum_j Q[m,j] (f_I(u_j^k) + f_E(u_j^k))
   + dt q^Delta_{m,m} (f_I(u_m^{k+1}) - f_I(u_m^k)), solved as
   u_m^{k+1} - alpha f_I(u_m^{k+1}) = beta (Eq. (8)) with alpha = dt q^Delta_{m,m}.
@@ -52,11 +56,21 @@ def collocation_matrix(tau: np.ndarray) -> np.ndarray:
     return Q
 
 
+QDELTA_RULES = ("clamped", "literal", "min-sr-ns", "ie")
+
+
 def qdelta(tau: np.ndarray, k: int, rule: str = "clamped") -> np.ndarray:
-    """MIN-SR-FLEX diagonal at sweep k (1-based): tau_m / q(k)."""
+    """Diagonal q^Delta_{m,m} at sweep k (1-based) under the named rule."""
     M = tau.size
-    q = min(k, M) if rule == "clamped" else k
-    return tau / float(q)
+    if rule == "clamped":
+        return tau / float(min(k, M))
+    if rule == "literal":
+        return tau / float(k)
+    if rule == "min-sr-ns":
+        return tau / float(M)
+    if rule == "ie":
+        return tau.copy()
+    raise ValueError(f"unknown q-delta rule {rule!r}")
 
 
 class Collocation:

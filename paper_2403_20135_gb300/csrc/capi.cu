@@ -125,10 +125,16 @@ cudaError_t upload(T **dst, const T *src, size_t n) {
     return cudaMemcpy(*dst, src, n * sizeof(T), cudaMemcpyHostToDevice);
 }
 
-// q^Delta denominator of sweep k (1-based), Sec. 4.2 (MIN-SR-FLEX).
-double qdelta_den(const sdc_ctx *c, int k) {
-    if (c->qdelta_rule == SDC_QDELTA_LITERAL) return k;
-    return k < c->M ? k : c->M;
+// Diagonal coefficient q^Delta_{m,m} of sweep k (1-based) for node m (0-based),
+// Sec. 4.2: MIN-SR-FLEX tau_m / k (the q(k) reading for k > M selected by the
+// rule), MIN-SR-NS tau_m / M, or the implicit-Euler diagonal tau_m.
+double qdelta_coef(const sdc_ctx *c, int k, int m) {
+    switch (c->qdelta_rule) {
+        case SDC_QDELTA_LITERAL: return c->tau[m] / k;
+        case SDC_QDELTA_MIN_SR_NS: return c->tau[m] / c->M;
+        case SDC_QDELTA_IMPLICIT_EULER: return c->tau[m];
+        default: return c->tau[m] / (k < c->M ? k : c->M);
+    }
 }
 
 DeviceTables tables(const sdc_ctx *c) {
@@ -298,8 +304,7 @@ cudaError_t enqueue_step(sdc_ctx *c, cudaStream_t s, bool with_resid, int *launc
         p.ubase = first ? c->un : c->U;
         p.ustride = first ? 0 : se;
         p.ybatch = first ? 1 : M;
-        const double den = qdelta_den(c, k + 1);
-        for (int m = 0; m < M; ++m) p.alpha[m] = c->dt * c->tau[m] / den;
+        for (int m = 0; m < M; ++m) p.alpha[m] = c->dt * qdelta_coef(c, k + 1, m);
         p.den = c->den + static_cast<size_t>(k) * M * c->d.ncoef;
         if (last) {                           // node M only, written to u_{n+1}
             p.m0 = M - 1;
@@ -337,9 +342,8 @@ cudaError_t upload_denominators(sdc_ctx *c) {
             lam[order_offset(c->T, m) + n - m] = double(n) * double(n + 1) / (c->phys.radius * c->phys.radius);
     const double phibar = c->phys.gravity * c->phys.mean_depth;
     for (int k = 0; k < K; ++k) {
-        const double q = qdelta_den(c, k + 1);
         for (int m = 0; m < M; ++m) {
-            const double al = c->dt * c->tau[m] / q;
+            const double al = c->dt * qdelta_coef(c, k + 1, m);
             for (int i = 0; i < nc; ++i) den[(static_cast<size_t>(k) * M + m) * nc + i] = 1.0 / (1.0 + al * al * phibar * lam[i]);
         }
     }
@@ -401,8 +405,7 @@ cudaError_t enqueue_step_adjoint(sdc_ctx *c, cudaStream_t s, int *launches) {
         p.m1 = M;
         p.fold = (k == 0);
         p.init_un = last;
-        const double den = qdelta_den(c, k + 1);
-        for (int m = 0; m < M; ++m) p.alpha[m] = c->dt * c->tau[m] / den;
+        for (int m = 0; m < M; ++m) p.alpha[m] = c->dt * qdelta_coef(c, k + 1, m);
         e = launch_sweep_adjoint(p, M, s, launches);
         if (e != cudaSuccess) return e;
     }
@@ -786,7 +789,7 @@ int sdc_destroy(sdc_ctx *c) {
 int sdc_set_option(sdc_ctx *c, int key, int value) {
     if (!c) return fail(SDC_EINVAL, "ctx is NULL");
     if (key == SDC_OPT_QDELTA_RULE) {
-        if (value != SDC_QDELTA_CLAMPED && value != SDC_QDELTA_LITERAL) return fail(SDC_EINVAL, "bad q-delta rule");
+        if (value < SDC_QDELTA_CLAMPED || value > SDC_QDELTA_IMPLICIT_EULER) return fail(SDC_EINVAL, "bad q-delta rule");
         if (value != c->qdelta_rule) {
             c->qdelta_rule = value;
             SDC_CUDA(cudaStreamSynchronize(c->stream));

@@ -38,11 +38,15 @@ class Solver:
                                        ctypes.c_void_p(self.stream.cuda_stream)), "sdc_create")
         self.h = h
         if qdelta_rule != _lib.SDC_QDELTA_CLAMPED:
-            _lib.check(self.lib.sdc_set_option(h, _lib.SDC_OPT_QDELTA_RULE, qdelta_rule), "sdc_set_option")
+            self.set_qdelta_rule(qdelta_rule)
         self.ncoef = self.lib.sdc_ncoef(h)
         self.method = _lib.SDC_METHOD_DSDC
         if method != _lib.SDC_METHOD_DSDC:
             self.set_method(method)
+
+    def set_qdelta_rule(self, rule: int):
+        """Diagonal q^Delta rule: SDC_QDELTA_CLAMPED, _LITERAL, _MIN_SR_NS or _IMPLICIT_EULER."""
+        _lib.check(self.lib.sdc_set_option(self.h, _lib.SDC_OPT_QDELTA_RULE, rule), "sdc_set_option")
 
     def set_method(self, method: int):
         """Integrator for step/run: SDC_METHOD_DSDC, SDC_METHOD_SERIAL_SDC or SDC_METHOD_IMEX2."""

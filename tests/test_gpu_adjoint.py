@@ -23,9 +23,9 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 
-def _solver(T, J, L, M, K, dt, precision=0):
+def _solver(T, J, L, M, K, dt, precision=0, **kw):
     from paper_2403_20135_gb300 import Solver
-    return Solver(T, J, L, M, K, dt, si.RADIUS, si.OMEGA, si.GRAVITY, si.MEAN_DEPTH, precision=precision)
+    return Solver(T, J, L, M, K, dt, si.RADIUS, si.OMEGA, si.GRAVITY, si.MEAN_DEPTH, precision=precision, **kw)
 
 
 def _oracle(T, J, L):
@@ -85,6 +85,21 @@ def test_step_adjoint_matches_oracle(M, K):
     ub = _rand(u.shape, rng)
     ref = oadj.swe_step_vjp(o, u, ub, osdc.Collocation(M), K, 600.0)
     s = _solver(T, J, L, M, K, 600.0)
+    got = to_numpy(s.step_adjoint(_cuda(u), _cuda(ub)))
+    assert np.all(rel_l2(got, ref) <= 1e-11), rel_l2(got, ref)
+
+
+@pytest.mark.parametrize("rule", ["min-sr-ns", "ie"])
+def test_step_adjoint_other_qdelta_rules(rule):
+    import paper_2403_20135_gb300 as pkg
+    code = {"min-sr-ns": pkg.SDC_QDELTA_MIN_SR_NS, "ie": pkg.SDC_QDELTA_IMPLICIT_EULER}[rule]
+    T, J, L, M, K = 21, 34, 72, 3, 4
+    o = _oracle(T, J, L)
+    wl = si.Workload("a", 0, T, J, L, M, K, 600.0, 1, 1, (100.0, 100.0))
+    u = swe.initial_state(wl, o)
+    ub = _rand(u.shape, np.random.default_rng(11))
+    ref = oadj.swe_step_vjp(o, u, ub, osdc.Collocation(M, rule), K, 600.0)
+    s = _solver(T, J, L, M, K, 600.0, qdelta_rule=code)
     got = to_numpy(s.step_adjoint(_cuda(u), _cuda(ub)))
     assert np.all(rel_l2(got, ref) <= 1e-11), rel_l2(got, ref)
 

@@ -111,17 +111,44 @@ def test_one_step_and_residuals_match_oracle(M, K):
     np.testing.assert_allclose(r, np.stack(res), rtol=1e-10)
 
 
-def test_literal_qdelta_rule_matches_oracle():
-    from paper_2403_20135_gb300 import SDC_QDELTA_LITERAL
+@pytest.mark.parametrize("rule", ["literal", "min-sr-ns", "ie"])
+def test_qdelta_rules_match_oracle(rule):
+    import paper_2403_20135_gb300 as pkg
+    code = {"literal": pkg.SDC_QDELTA_LITERAL, "min-sr-ns": pkg.SDC_QDELTA_MIN_SR_NS,
+            "ie": pkg.SDC_QDELTA_IMPLICIT_EULER}[rule]
     T, J, L, M, K = 21, 34, 72, 3, 5
     o = _oracle(T, J, L)
     u0 = swe.initial_state(_wl(T, J, L, M, K), o)
-    ref = osdc.swe_step(o, u0, osdc.Collocation(M, "literal"), K, 600.0)
+    ref = osdc.swe_step(o, u0, osdc.Collocation(M, rule), K, 600.0)
     clamped = osdc.swe_step(o, u0, osdc.Collocation(M, "clamped"), K, 600.0)
-    s = _solver(T, J, L, M, K, 600.0, qdelta_rule=SDC_QDELTA_LITERAL)
-    got = to_numpy(s.step(_cuda(u0)))
+    s = _solver(T, J, L, M, K, 600.0, qdelta_rule=code)
+    out, r = s.step(_cuda(u0), residuals=True)
+    res = []
+    osdc.swe_step(o, u0, osdc.Collocation(M, rule), K, 600.0, residuals=res)
+    got = to_numpy(out)
     assert np.all(rel_l2(got, ref) <= TOL_EVAL * 10)
-    assert np.any(rel_l2(got, clamped) > 1e-9)          # the two readings differ
+    res = np.stack(res)
+    # late sweeps of the fast-converging rules reach residuals near the rounding
+    # level of the state: per field, an absolute floor of 1e-12 x the first sweep's
+    assert np.all(np.abs(r - res) <= 1e-10 * np.abs(res) + 1e-12 * res[0]), (r, res)
+    assert np.any(rel_l2(got, clamped) > 1e-9)          # the rules differ
+
+
+def test_qdelta_rule_switch_and_bad_value():
+    import paper_2403_20135_gb300 as pkg
+    from paper_2403_20135_gb300 import _lib
+    T, J, L, M, K = 21, 34, 72, 3, 3
+    o = _oracle(T, J, L)
+    u0 = swe.initial_state(_wl(T, J, L, M, K), o)
+    s = _solver(T, J, L, M, K, 600.0)
+    first = to_numpy(s.step(_cuda(u0)))                  # captures the default graph
+    assert s.lib.sdc_set_option(s.h, _lib.SDC_OPT_QDELTA_RULE, 7) == _lib.SDC_EINVAL
+    s.set_qdelta_rule(pkg.SDC_QDELTA_MIN_SR_NS)
+    got = to_numpy(s.step(_cuda(u0)))
+    ref = osdc.swe_step(o, u0, osdc.Collocation(M, "min-sr-ns"), K, 600.0)
+    assert np.all(rel_l2(got, ref) <= TOL_EVAL * 10)
+    s.set_qdelta_rule(pkg.SDC_QDELTA_CLAMPED)
+    np.testing.assert_array_equal(to_numpy(s.step(_cuda(u0))), first)
 
 
 def test_t31_workload_full_run():

@@ -65,6 +65,60 @@ def test_min_sr_flex_coefficients():
     np.testing.assert_allclose(lit.qdelta(6), lit.tau / 6)
 
 
+def _dahlquist_step_error(rule, M, z):
+    """|dSDC step (K = M) - collocation solution| on y' = z y over dt = 1, y(0) = 1."""
+    coll = sdc.Collocation(M, rule)
+    u = sdc.dsdc_step(np.array([1.0]), lambda v: 0.0 * v, lambda v: z * v, lambda al, b: b / (1.0 - al * z),
+                      coll, M, 1.0)
+    U = np.linalg.solve(np.eye(M) - z * coll.Q, np.ones(M))
+    return abs(u[0] - U[-1])
+
+
+@pytest.mark.parametrize("M", [2, 3, 4])
+def test_min_sr_flex_exact_in_the_stiff_limit(M):
+    """MIN-SR-FLEX: in the stiff limit a sweep's error operator tends to I - D_k^{-1} Q,
+    and the product over k = 1..M of these vanishes, so M sweeps reach the
+    collocation solution; the implicit-Euler diagonal does not."""
+    z = -1e9
+    assert _dahlquist_step_error("clamped", M, z) < 1e-13
+    assert _dahlquist_step_error("literal", M, z) < 1e-13
+    assert _dahlquist_step_error("ie", M, z) > 1e-10
+
+
+@pytest.mark.parametrize("M", [2, 3])
+def test_min_sr_ns_gains_an_order_in_the_non_stiff_limit(M):
+    """MIN-SR-NS: Q - diag(tau / M) is nilpotent, so in the non-stiff limit M sweeps
+    leave an O(z^{M+2}) error against the collocation solution; a diagonal
+    without that property (implicit Euler, tau_m) leaves O(z^{M+1})."""
+    def slope(rule):
+        return np.log2(_dahlquist_step_error(rule, M, -0.02) / _dahlquist_step_error(rule, M, -0.01))
+    assert slope("min-sr-ns") > M + 1.8
+    assert abs(slope("ie") - (M + 1)) < 0.2
+
+
+def test_implicit_euler_diagonal_sweeps_from_t_n():
+    """Every sweep of the implicit-Euler diagonal is, at k = 0, one IMEX Euler step
+    from t_n to t_n + tau_m dt (the FLEX first sweep), and its fixed point is the
+    collocation solution (checked on the IMEX oscillator)."""
+    A = np.array([[0.0, -2.0], [2.0, 0.0]])
+    B = np.array([[-0.3, 0.1], [-0.2, -0.1]])
+    f_E, f_I, solve = _linear_problem(A, B)
+    u0 = np.array([1.0, 0.5])
+    for M in (2, 4):
+        coll = sdc.Collocation(M, "ie")
+        dt = 0.1
+        got = sdc.dsdc_step(u0, f_E, f_I, solve, coll, 1, dt)
+        want = np.linalg.solve(np.eye(2) - dt * A, u0 + dt * (B @ u0))      # tau_M = 1
+        np.testing.assert_allclose(got, want, rtol=1e-14)
+        got = sdc.dsdc_step(u0, f_E, f_I, solve, coll, 80, dt)
+        np.testing.assert_allclose(got, _dense_collocation(A + B, u0, coll.Q, dt), rtol=1e-12)
+
+
+def test_unknown_qdelta_rule_is_rejected():
+    with pytest.raises(ValueError):
+        sdc.Collocation(3, "min-sr-s").qdelta(1)
+
+
 def _linear_problem(A, B):
     """u' = A u (implicit) + B u (explicit), u real vector."""
     n = A.shape[0]
