@@ -59,7 +59,7 @@ struct sdc_ctx {
     double *pbar = nullptr;
     float *pbar32 = nullptr;
     double *eps = nullptr, *lam = nullptr, *mu2 = nullptr, *w2 = nullptr, *syn = nullptr, *ring64 = nullptr;
-    float *ring32 = nullptr, *epi32 = nullptr;
+    float *ring32 = nullptr, *epi32 = nullptr, *syn32 = nullptr;
     int *row_m = nullptr, *coef_m = nullptr;
     double2 *tw = nullptr;
     float2 *tw32 = nullptr;
@@ -107,7 +107,7 @@ void free_ctx(sdc_ctx *c) {
         if (g) cudaGraphExecDestroy(g);
     if (c->graph_retape) cudaGraphExecDestroy(c->graph_retape);
     if (c->graph_adjoint) cudaGraphExecDestroy(c->graph_adjoint);
-    void *ptrs[] = {c->pbar, c->pbar32, c->ring64, c->ring32, c->epi32, c->eps, c->lam, c->mu2, c->w2, c->syn, c->row_m, c->coef_m, c->tw,
+    void *ptrs[] = {c->pbar, c->pbar32, c->ring64, c->ring32, c->epi32, c->syn32, c->eps, c->lam, c->mu2, c->w2, c->syn, c->row_m, c->coef_m, c->tw,
                     c->tw32, c->twp32, c->un, c->U, c->E, c->E0, c->f1, c->f2, c->f3, c->resid_part, c->resid,
                     c->gstore, c->ub, c->eb, c->ubn, c->ubnext, c->eb0, c->snaps, c->phigrid, c->rgrid,
                     c->loss_part, c->loss_dev, c->tc_a3, c->tc_a1, c->tc_t3, c->tc_t1, c->tc_err, c->den,
@@ -153,6 +153,7 @@ DeviceTables tables(const sdc_ctx *c) {
     tb.ring64 = c->ring64;
     tb.ring32 = c->ring32;
     tb.epi32 = c->epi32;
+    tb.syn32 = c->syn32;
     tb.plan16 = c->plan16;
     tb.twp32 = c->twp32;
     tb.ntwp = c->ntwp;
@@ -186,6 +187,7 @@ cudaError_t tendency(sdc_ctx *c, int B, const double2 *states, long long sstride
     tb.ring64 = c->ring64;
     tb.ring32 = c->ring32;
     tb.epi32 = c->epi32;
+    tb.syn32 = c->syn32;
     tb.plan16 = c->plan16;
     tb.twp32 = c->twp32;
     tb.ntwp = c->ntwp;
@@ -740,6 +742,10 @@ int sdc_create(sdc_ctx **out, int T, int J, int L, int M, int K, double dt, cons
                 e32[4 * i + 3] = 0.f;
             }
         SDC_TRY(upload(&c->epi32, e32.data(), e32.size()));
+        std::vector<float> s32(4 * static_cast<size_t>(d.next));
+        for (size_t e = 0; e < static_cast<size_t>(d.next); ++e)
+            for (int k = 0; k < 3; ++k) s32[4 * e + k] = float(syn[3 * e + k]);
+        SDC_TRY(upload(&c->syn32, s32.data(), s32.size()));
     }
     SDC_TRY(upload(&c->w2, c->w.data(), d.J2));
 

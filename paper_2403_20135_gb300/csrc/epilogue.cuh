@@ -10,6 +10,7 @@
 // factors from an FP32 table); the result is returned in FP64.
 #pragma once
 
+#include "convert.cuh"
 #include "fft.cuh"
 #include "sdc_internal.h"
 
@@ -50,9 +51,15 @@ __device__ __forceinline__ void vector_epilogue(const V2<R> *__restrict__ Y, con
     const R tdy = inv_a * (mm * Bh.x - cu * Au.y + cl * Al.y) + lm * Eh.y;
     const R tpx = -inv_a * (-mm * Ch.y + cu * Du.x - cl * Dl.x);
     const R tpy = -inv_a * (mm * Ch.x + cu * Du.y - cl * Dl.y);
-    tp = make_double2(double(tpx), double(tpy));
-    tz = make_double2(double(tzx), double(tzy));
-    td = make_double2(double(tdx), double(tdy));
+    if constexpr (sizeof(R) == sizeof(float)) {       // widened on the integer pipe (convert.cuh)
+        tp = make_double2(f32_to_f64(tpx), f32_to_f64(tpy));
+        tz = make_double2(f32_to_f64(tzx), f32_to_f64(tzy));
+        td = make_double2(f32_to_f64(tdx), f32_to_f64(tdy));
+    } else {
+        tp = make_double2(tpx, tpy);
+        tz = make_double2(tzx, tzy);
+        td = make_double2(tdx, tdy);
+    }
 }
 
 }  // namespace sdc

@@ -125,6 +125,7 @@ struct DeviceTables {
     const double *ring64;  // per northern latitude: 2 Omega mu, 1 / (2 (1 - mu^2)), w / (1 - mu^2), w [J2][4]
     const float *ring32;   // the same in FP32
     const float *epi32;    // FP32 epilogue factors per coefficient: n eps_{n+1}, (n+1) eps_n, lambda_n, 0 [ncoef][4]
+    const float *syn32;    // FP32 wind synthesis factors c0, c1, c2, 0 [next][4]
     int *err;              // device flag set by a kernel whose bounded wait expired
     FftPlan plan16;        // FP32 ring: passes of radix 16, then 8/4/2, then 3
     const float2 *twp32;   // FP32 ring: per-pass twiddles of plan16 (after the first pass)

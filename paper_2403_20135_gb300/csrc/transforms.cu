@@ -22,6 +22,7 @@
 #include "fft.cuh"
 #include "fft_pass.cuh"
 #include "async_copy.cuh"
+#include "convert.cuh"
 #include "epilogue.cuh"
 #include "sdc_internal.h"
 
@@ -559,6 +560,228 @@ __global__ void __launch_bounds__(256) k1_synthesis_f32(const double2 *__restric
     }
 }
 
+// K1 (FP32, NB node states per block): one block per (order pair m, T - m,
+// group of NB states).  Each table row is then read from L2 once per NB
+// states instead of once per state (the per-state kernel above streams the
+// whole table B times per batch, more than L2 delivers to keep its FMAs busy).
+// One thread issues, at the start, bulk copies of the FP64 coefficients of
+// both orders (per state and field, contiguous in the state layout) and of
+// the rows' FP32 wind factors, then the first table chunks of the stage ring
+// (bounded waits as in the per-state kernel).  The states are converted to
+// FP32 once in shared memory (integer-pipe conversions) and the coefficient
+// rows formed there.  Threads split by parity (rows t = n' - m even, odd) and,
+// for S = 2, by alternate rows of that parity (lane pairs, summed with a
+// shuffle at the end of each order); a thread keeps two latitudes x NB states
+// x 4 fields (64 accumulators at NB = 4).
+constexpr int kSynNbMaxThreads = 384;
+constexpr int kSynNbRows = 48;             // table rows per bulk copy (even: chunks start on even t)
+static_assert(8 * (kMaxSynStages + 1) <= static_cast<int>(kSynCtrlBytes), "stage and prologue barriers fit");
+constexpr size_t kSmemLimit = 227 * 1024;
+
+__host__ __device__ inline int synthesis_nb_rowstride(int nb) { return nb * 8 + 4; }   // floats, padded
+__host__ inline int synthesis_nb_threads(int J2, int S) { return 2 * S * (((J2 + 1) / 2 + 32 / S - 1) / (32 / S) * (32 / S)); }
+__host__ inline int synthesis_nb_s(int J2) { return synthesis_nb_threads(J2, 2) <= kSynNbMaxThreads ? 2 : 1; }
+// FP32 state copies of a block, in float2 (rounded up to keep 16-byte alignment)
+__host__ __device__ inline int synthesis_nb_s32_elems(int T, int nb) { return (nb * 3 * (T + 2) + 1) & ~1; }
+__host__ inline size_t synthesis_nb_fixed(const Dims &d, int nb) {
+    return kSynCtrlBytes + static_cast<size_t>(d.T + 4) * synthesis_nb_rowstride(nb) * sizeof(float) +
+           static_cast<size_t>(nb) * 3 * (d.T + 2) * sizeof(double2) +
+           static_cast<size_t>(synthesis_nb_s32_elems(d.T, nb)) * sizeof(float2) +
+           static_cast<size_t>(d.T + 4) * sizeof(float4);
+}
+__host__ inline int synthesis_nb_stages(const Dims &d, int nb) {
+    const size_t per = static_cast<size_t>(kSynNbRows) * d.J2p * sizeof(float);
+    const size_t fixed = synthesis_nb_fixed(d, nb);
+    const int ns = fixed < kSmemLimit ? static_cast<int>((kSmemLimit - fixed) / per) : 0;
+    return ns > kMaxSynStages ? kMaxSynStages : ns;
+}
+__host__ inline size_t synthesis_nb_smem(const Dims &d, int nb) {
+    return synthesis_nb_fixed(d, nb) +
+           static_cast<size_t>(synthesis_nb_stages(d, nb)) * kSynNbRows * d.J2p * sizeof(float);
+}
+// whether the batched kernel serves these sizes (threads, at least two stages)
+__host__ inline bool synthesis_nb_fits(const Dims &d, int nb) {
+    return synthesis_nb_threads(d.J2, 1) <= kSynNbMaxThreads && synthesis_nb_stages(d, nb) >= 2;
+}
+
+template <int NB, int S>
+__global__ void __launch_bounds__(kSynNbMaxThreads, 1)
+    k1_synthesis_f32_nb(const double2 *__restrict__ states, long long sstride, int B, Dims d,
+                        const float *__restrict__ pbar, const float4 *__restrict__ syn32, float2 *__restrict__ f1,
+                        int nstages, int *err) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem_raw);                 // [kMaxSynStages], then the prologue's
+    uint64_t *mpro = mbar + kMaxSynStages;
+    const int T = d.T;
+    constexpr int RS = NB * 8 + 4;                                           // coefficient row stride (floats)
+    float *cf = reinterpret_cast<float *>(smem_raw + kSynCtrlBytes);         // [T + 4 rows][RS]
+    double2 *raw = reinterpret_cast<double2 *>(cf + static_cast<size_t>(T + 4) * RS);   // [NB][3][T + 2]
+    float2 *s32 = reinterpret_cast<float2 *>(raw + static_cast<size_t>(NB) * 3 * (T + 2));   // [NB][3][T + 2]
+    float4 *sy = reinterpret_cast<float4 *>(s32 + synthesis_nb_s32_elems(T, NB));             // [T + 4]
+    float *stage = reinterpret_cast<float *>(sy + (T + 4));                  // [nstages][kSynNbRows][J2p]
+    const size_t stage_elems = static_cast<size_t>(kSynNbRows) * d.J2p;
+    const int m1 = blockIdx.x, m2 = T - blockIdx.x;
+    const int b0 = blockIdx.y * NB;
+    const int nbv = min(NB, B - b0);
+    const bool two = m2 > m1;
+    const int nn1 = T + 2 - m1;
+    const int nn2 = two ? T + 2 - m2 : 0;
+    const int rows = nn1 + nn2;
+    const int nc1 = T + 1 - m1, ncs = nc1 + (two ? T + 1 - m2 : 0);         // state coefficients per field
+    const int nch1 = (nn1 + kSynNbRows - 1) / kSynNbRows;
+    const int nch = nch1 + (nn2 + kSynNbRows - 1) / kSynNbRows;
+    auto chunk = [&](int c, int &m, int &t0, int &cnt) {
+        const bool second = c >= nch1;
+        m = second ? m2 : m1;
+        t0 = (second ? c - nch1 : c) * kSynNbRows;
+        cnt = min(kSynNbRows, (second ? nn2 : nn1) - t0);
+    };
+    auto issue = [&](int c) {
+        int m, t0, cnt;
+        chunk(c, m, t0, cnt);
+        const uint32_t bytes = static_cast<uint32_t>(cnt) * d.J2p * sizeof(float);
+        uint64_t *bar = &mbar[c % nstages];
+        expect_tx(bar, bytes);
+        bulk_copy(stage + (c % nstages) * stage_elems, pbar + static_cast<size_t>(ext_offset(T, m) + t0) * d.J2p,
+                  bytes, bar);
+    };
+    const int nc = d.ncoef;
+    int issued = 0;
+    if (threadIdx.x == 0) {
+        for (int k = 0; k <= kMaxSynStages; ++k) mbar_init(&mbar[k], 1);
+        mbar_init_fence();
+        const uint32_t n1b = static_cast<uint32_t>(nc1) * sizeof(double2);
+        const uint32_t n2b = static_cast<uint32_t>(ncs - nc1) * sizeof(double2);
+        expect_tx(mpro, static_cast<uint32_t>(nbv) * 3 * (n1b + n2b) +
+                            static_cast<uint32_t>(rows) * sizeof(float4));
+        for (int b = 0; b < nbv; ++b)
+            for (int f = 0; f < 3; ++f) {
+                const double2 *src = states + (b0 + b) * sstride + f * nc;
+                double2 *dst = raw + (b * 3 + f) * ncs;
+                bulk_copy(dst, src + order_offset(T, m1), n1b, mpro);
+                if (two) bulk_copy(dst + nc1, src + order_offset(T, m2), n2b, mpro);
+            }
+        bulk_copy(sy, syn32 + ext_offset(T, m1), static_cast<uint32_t>(nn1) * sizeof(float4), mpro);
+        if (two) bulk_copy(sy + nn1, syn32 + ext_offset(T, m2), static_cast<uint32_t>(nn2) * sizeof(float4), mpro);
+        for (; issued < min(nstages, nch); ++issued) issue(issued);
+    }
+    __syncthreads();                                     // the barriers are initialised
+    const bool late = !mbar_wait(mpro, 0);
+    if (__syncthreads_or(late)) {
+        if (threadIdx.x == 0) {
+            atomicExch(err, 5);
+            for (int k = 0; k < issued; ++k) mbar_wait(&mbar[k % nstages], (k / nstages) & 1);
+        }
+        return;
+    }
+    for (int i = threadIdx.x; i < NB * 3 * ncs; i += blockDim.x) {
+        const bool valid = i < nbv * 3 * ncs;
+        const double2 x = valid ? raw[i] : make_double2(0.0, 0.0);
+        s32[i] = make_float2(f64_to_f32_rn(x.x), f64_to_f32_rn(x.y));
+    }
+    __syncthreads();
+    // coefficient rows: zeta, Phi' and the U, V combinations of n' - 1, n', n' + 1
+    for (int i = threadIdx.x; i < rows * NB; i += blockDim.x) {
+        const int r = i / NB, b = i - r * NB;
+        const bool first = r < nn1;
+        const int m = first ? m1 : m2;
+        const int t = first ? r : r - nn1;
+        const int n = m + t;
+        const int base = first ? 0 : nc1;
+        const float2 *sb = s32 + static_cast<size_t>(b) * 3 * ncs;
+        auto ld = [&](int f, int k) -> float2 {
+            return (k < m || k > T) ? make_float2(0.f, 0.f) : sb[f * ncs + base + k - m];
+        };
+        const float2 z0 = ld(F_ZETA, n), zm = ld(F_ZETA, n - 1), zp = ld(F_ZETA, n + 1);
+        const float2 d0 = ld(F_DIV, n), dm = ld(F_DIV, n - 1), dp = ld(F_DIV, n + 1);
+        const float4 cy = sy[r];
+        const float c0 = cy.x, c1 = cy.y, c2 = cy.z;
+        float2 *o = reinterpret_cast<float2 *>(cf + static_cast<size_t>(r) * RS) + b * 4;
+        o[G_ZETA] = z0;
+        o[G_PHI] = ld(F_PHI, n);
+        o[G_U] = make_float2(-c0 * d0.y - c1 * zm.x - c2 * zp.x, c0 * d0.x - c1 * zm.y - c2 * zp.y);
+        o[G_V] = make_float2(-c0 * z0.y + c1 * dm.x + c2 * dp.x, c0 * z0.x + c1 * dm.y + c2 * dp.y);
+    }
+    __syncthreads();
+
+    const int tq = blockDim.x / 2;
+    const int par = threadIdx.x >= tq ? 1 : 0;
+    const int lt = threadIdx.x - par * tq;
+    const int sp = lt % S;                               // alternate rows of this parity
+    const int j0 = 2 * (lt / S);
+    const bool active = j0 < d.J2;
+    const int jl = active ? j0 : 0;                      // idle lanes read a valid column and store nothing
+    float2 a[NB][4][2];                                  // [state][field][latitude]
+    auto reset = [&]() {
+#pragma unroll
+        for (int b = 0; b < NB; ++b)
+#pragma unroll
+            for (int f = 0; f < 4; ++f) a[b][f][0] = a[b][f][1] = make_float2(0.f, 0.f);
+    };
+    reset();
+    int c = 0;
+    for (; c < nch; ++c) {
+        int m, t0, cnt;
+        chunk(c, m, t0, cnt);
+        const bool slow = !mbar_wait(&mbar[c % nstages], (c / nstages) & 1);
+        if (__syncthreads_or(slow)) {                    // the block agrees before anyone leaves
+            if (threadIdx.x == 0) atomicExch(err, 5);
+            break;
+        }
+        const float *P = stage + (c % nstages) * stage_elems + jl;
+        const float *cc = cf + static_cast<size_t>((c >= nch1 ? nn1 : 0) + t0) * RS;
+#pragma unroll 2
+        for (int i = par + 2 * sp; i < cnt; i += 2 * S) {   // chunks start on even t: row i has parity i & 1
+            const float2 pv = *reinterpret_cast<const float2 *>(P + i * d.J2p);
+            const float4 *ci = reinterpret_cast<const float4 *>(cc + i * RS);
+#pragma unroll
+            for (int b = 0; b < NB; ++b) {
+                const float4 q0 = ci[2 * b], q1 = ci[2 * b + 1];
+                const float2 k4[4] = {make_float2(q0.x, q0.y), make_float2(q0.z, q0.w), make_float2(q1.x, q1.y),
+                                      make_float2(q1.z, q1.w)};
+#pragma unroll
+                for (int f = 0; f < 4; ++f) {
+                    a[b][f][0] = caxpy(pv.x, k4[f], a[b][f][0]);
+                    a[b][f][1] = caxpy(pv.y, k4[f], a[b][f][1]);
+                }
+            }
+        }
+        if (c == nch1 - 1 || c == nch - 1) {             // end of an order: sum the lane pair, store, restart
+            if constexpr (S == 2) {
+#pragma unroll
+                for (int b = 0; b < NB; ++b)
+#pragma unroll
+                    for (int f = 0; f < 4; ++f)
+#pragma unroll
+                        for (int k = 0; k < 2; ++k) {
+                            a[b][f][k].x += __shfl_xor_sync(0xffffffffu, a[b][f][k].x, 1);
+                            a[b][f][k].y += __shfl_xor_sync(0xffffffffu, a[b][f][k].y, 1);
+                        }
+            }
+            if (active && sp == 0) {
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    if (j0 + k >= d.J2) break;
+#pragma unroll
+                    for (int b = 0; b < NB; ++b) {
+                        if (b >= nbv) break;
+                        float2 *o = f1 + (static_cast<size_t>(b0 + b) * d.J2 + j0 + k) * (4 * 2 * (T + 1)) +
+                                    par * (T + 1) + m;
+#pragma unroll
+                        for (int f = 0; f < 4; ++f) o[f * 2 * (T + 1)] = a[b][f][k];
+                    }
+                }
+            }
+            reset();
+        }
+        __syncthreads();                                 // every read of this stage is done
+        if (threadIdx.x == 0 && issued < nch) issue(issued++);
+    }
+    if (c < nch && threadIdx.x == 0) {                   // stopped early: let issued copies land (bounded)
+        for (int k = c; k < issued; ++k) mbar_wait(&mbar[k % nstages], (k / nstages) & 1);
+    }
+}
+
 // K3a (FP32): one block per (state, order pair m, T - m).  The W rows of
 // both orders (10 x J2 complex each) are staged in shared memory; a thread
 // group of kPrjParts neighbouring lanes owns a row quad (rows e, e+2, e+4,
@@ -799,6 +1022,20 @@ static cudaError_t configure(const Dims &d, const FftPlan &plan) {
         e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, sms5);
         if (e != cudaSuccess) return e;
     }
+    {
+        const void *fs[2][3] = {{(const void *)k1_synthesis_f32_nb<1, 1>, (const void *)k1_synthesis_f32_nb<2, 1>,
+                                 (const void *)k1_synthesis_f32_nb<4, 1>},
+                                {(const void *)k1_synthesis_f32_nb<1, 2>, (const void *)k1_synthesis_f32_nb<2, 2>,
+                                 (const void *)k1_synthesis_f32_nb<4, 2>}};
+        for (int k = 0; k < 3; ++k) {
+            if (!synthesis_nb_fits(d, 1 << k)) continue;
+            for (int si = 0; si < 2; ++si) {
+                e = cudaFuncSetAttribute(fs[si][k], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)synthesis_nb_smem(d, 1 << k));
+                if (e != cudaSuccess) return e;
+            }
+        }
+    }
     size_t smp = 0, smq = 0;
     project_f32_async(d, project_f32_threads(d.T), &smp, 5);
     project_f32_async(d, project_f32_threads(d.T), &smq, 4);
@@ -813,6 +1050,32 @@ static cudaError_t configure(const Dims &d, const FftPlan &plan) {
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+// Batched FP32 synthesis: NB = 4 states per block where it fits (else 2), 1
+// for a single state; S = 2 lane pairs per latitude pair where the block
+// stays within kSynNbMaxThreads.
+static cudaError_t launch_synthesis_nb(const Dims &d, int B, const double2 *states, long long sstride,
+                                       const float *pbar, const float *syn32, float2 *f1, int *err, cudaStream_t s) {
+    const int nb = B == 1 ? 1 : ((B == 2 || !synthesis_nb_fits(d, 4)) ? 2 : 4);
+    const int S = synthesis_nb_s(d.J2);
+    const dim3 g((d.T + 2) / 2, (B + nb - 1) / nb);
+    const int nt = synthesis_nb_threads(d.J2, S), ns = synthesis_nb_stages(d, nb);
+    const size_t sm = synthesis_nb_smem(d, nb);
+    const float4 *sy = reinterpret_cast<const float4 *>(syn32);
+#define SDC_SYN_NB(NBV, SV) \
+    k1_synthesis_f32_nb<NBV, SV><<<g, nt, sm, s>>>(states, sstride, B, d, pbar, sy, f1, ns, err)
+    if (S == 2) {
+        if (nb == 1) SDC_SYN_NB(1, 2);
+        else if (nb == 2) SDC_SYN_NB(2, 2);
+        else SDC_SYN_NB(4, 2);
+    } else {
+        if (nb == 1) SDC_SYN_NB(1, 1);
+        else if (nb == 2) SDC_SYN_NB(2, 1);
+        else SDC_SYN_NB(4, 1);
+    }
+#undef SDC_SYN_NB
+    return cudaGetLastError();
 }
 
 template <typename R>
@@ -835,6 +1098,10 @@ static cudaError_t launch_tendency_t(const Dims &d, const FftPlan &plan, int B, 
         if (tc) {
             cudaError_t e = launch_tc_synthesis(*tc, d, B, states, sstride, tb.syn, tb.row_m, f1, s, launches);
             if (e != cudaSuccess) return e;
+        } else if (synthesis_nb_fits(d, 2)) {
+            const cudaError_t e = launch_synthesis_nb(d, B, states, sstride, pbar, tb.syn32, f1, tb.err, s);
+            if (e != cudaSuccess) return e;
+            if (launches) ++*launches;
         } else {
             const int g4 = (d.J2 + 3) / 4;
             const dim3 gs(B, (d.T + 2) / 2);
