@@ -505,15 +505,23 @@ def work_precision(hours: float):
                       "reference": f"dSDC FP64, dt = {dt_ref} s"}), flush=True)
 
 
-def profile_run(name: str, steps: int):
-    """A few untimed steps of one precision mode (the command profilers wrap)."""
+def profile_run(name: str, steps: int, adjoint: bool = False):
+    """A few untimed steps of one precision mode (the command profilers wrap);
+    with `adjoint`, reversed steps (retape + step adjoint) instead."""
+    import torch
     from paper_2403_20135_gb300 import Solver
     wl = si.WORKLOADS[WORKLOAD]
     s = Solver.for_workload(wl, precision=PRECISIONS[name])
     u = s.initial_state(wl)
-    s.run(u, steps)
+    if adjoint:
+        ub = torch.ones_like(u)
+        for _ in range(steps):
+            s.step_adjoint(u, ub)
+    else:
+        s.run(u, steps)
     s.sync()
-    print(f"profile-run {name}: {steps} steps of {wl.describe()} ok")
+    kind = "reversed steps" if adjoint else "steps"
+    print(f"profile-run {name}: {steps} {kind} of {wl.describe()} ok")
 
 
 def main():
@@ -529,6 +537,7 @@ def main():
     ap.add_argument("--horizon", type=int, default=500, help="steps of the fixed-error comparison")
     ap.add_argument("--profile-run", choices=sorted(PRECISIONS), default=None,
                     help="only run --steps untimed steps of this precision (for profilers)")
+    ap.add_argument("--adjoint", action="store_true", help="with --profile-run: reversed steps")
     ap.add_argument("--work-precision", type=float, default=None, metavar="HOURS",
                     help="only run the work-precision study over this simulated time")
     args = ap.parse_args()
@@ -536,7 +545,7 @@ def main():
         work_precision(args.work_precision)
         return
     if args.profile_run:
-        profile_run(args.profile_run, args.steps)
+        profile_run(args.profile_run, args.steps, args.adjoint)
         return
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
