@@ -154,6 +154,15 @@ __host__ __device__ constexpr int plan16_npasses(int L) {
     return p;
 }
 
+// Padded index of i + r * step: when step is a multiple of 16 the padding of
+// the sum is the padding of i plus r * step / 16, so one padded base and
+// compile-time offsets serve all R elements of a butterfly.
+template <int STEP>
+__device__ __forceinline__ int fpad_step(int base_padded, int i, int r) {
+    if constexpr (STEP % 16 == 0) return base_padded + r * (STEP + STEP / 16);
+    else return fpad(i + r * STEP);
+}
+
 template <int R, int L, int Ns, int NB>
 __device__ __forceinline__ void fft_pass_ct(const float2 *src, float2 *dst, const float2 *__restrict__ twp,
                                             bool inv) {
@@ -164,8 +173,9 @@ __device__ __forceinline__ void fft_pass_ct(const float2 *src, float2 *dst, cons
         float2 *out = dst + bb * Lp;
         const int k = j % Ns;
         float2 v[R];
+        const int jp = fpad(j);
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = in[fpad(j + r * Lr)];
+        for (int r = 0; r < R; ++r) v[r] = in[fpad_step<Lr>(jp, j, r)];
         if constexpr (Ns > 1) {
 #pragma unroll
             for (int r = 1; r < R; ++r) {
@@ -176,8 +186,14 @@ __device__ __forceinline__ void fft_pass_ct(const float2 *src, float2 *dst, cons
         }
         dft<R>(v, inv);
         const int base = (j - k) * R + k;
+        const int bp = fpad(base);
+        if constexpr (Ns == 1 && R == 16) {              // base = 16 j: the 16 outputs share one padding
 #pragma unroll
-        for (int r = 0; r < R; ++r) out[fpad(base + r * Ns)] = v[r];
+            for (int r = 0; r < R; ++r) out[bp + r] = v[r];
+        } else {
+#pragma unroll
+            for (int r = 0; r < R; ++r) out[fpad_step<Ns>(bp, base, r)] = v[r];
+        }
     }
 }
 
