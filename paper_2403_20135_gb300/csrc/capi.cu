@@ -760,7 +760,7 @@ int sdc_create(sdc_ctx **out, int T, int J, int L, int M, int K, double dt, cons
     SDC_TRY(cudaMalloc(&c->f1, f1b > scal ? f1b : scal));
     SDC_TRY(cudaMalloc(&c->f2, f2b > scal ? f2b : scal));
     SDC_TRY(cudaMalloc(&c->f3, static_cast<size_t>(M) * d.next * 5 * elem));
-    c->sweep_nblocks = sweep_blocks(d.ncoef);
+    c->sweep_nblocks = sweep_blocks(d.ncoef, M);
     SDC_TRY(cudaMalloc(&c->resid_part, static_cast<size_t>(c->sweep_nblocks) * M * 3 * sizeof(double)));
     SDC_TRY(cudaMalloc(&c->resid, static_cast<size_t>(K) * 3 * sizeof(double)));
     SDC_TRY(cudaMalloc(&c->den, static_cast<size_t>(K) * M * d.ncoef * sizeof(double)));

@@ -238,7 +238,7 @@ cudaError_t launch_sweep(const SweepParams &p, int M, bool fp32, cudaStream_t s,
 cudaError_t launch_resid_reduce(const double *part, int nblocks, int M, int m0, int m1,
                                 double *out3, cudaStream_t s, int *launches,
                                 StageTimer *timer = nullptr);
-int sweep_blocks(int ncoef);
+int sweep_blocks(int ncoef, int M);
 
 cudaError_t launch_spec_to_grid(const Dims &d, const FftPlan &plan, const double2 *spec,
                                 double *grid, const double *pbar, const double2 *tw,

@@ -1,7 +1,8 @@
 // K4: fused collocation quadrature, diagonal implicit solve and residual
 // partial sums of one sweep (Eq. (7) with the solver form Eq. (8)), for every
 // node of the sweep at once -- the paper's parallel node loop of Algorithm 2
-// lives inside each thread, which owns one spectral mode for all nodes.
+// becomes G = M (rounded up to a power of two) neighbouring lanes per
+// spectral mode, lane m owning node m.
 //
 // Per mode (n, m) with lambda_n = n(n+1)/a^2 and F_j = L_g(u_j^k) + T_E(u_j^k):
 //   R_m   = u_n + dt sum_j q_{m,j} F_j                   (collocation right side)
@@ -12,9 +13,12 @@
 //     Phi' = (rhs_Phi - alpha Phibar rhs_div) / (1 + alpha^2 Phibar lambda_n)
 //     div  = rhs_div + alpha lambda_n Phi',  zeta = rhs_zeta
 //   residual R_m - u_m^k accumulated as sum w |r|^2 (w = 1 at m = 0, else 2).
-// T_E(u_j^k) is formed here from the projections of the preceding tendency
-// batch by the vector epilogue (epilogue.cuh, in the transform precision);
-// all other arithmetic is FP64.
+// Lane j forms F_j (T_E(u_j^k) from the projections of the preceding tendency
+// batch by the vector epilogue of epilogue.cuh, in the transform precision;
+// on the first sweep every node's T_E is that of u_n, formed once by lane 0);
+// the quadrature rows take the F_j of the group by warp shuffles.  All other
+// arithmetic is FP64.  Spreading the nodes over lanes gives the FP64 pipe G
+// times the warps of a thread-per-mode layout to hide its latency.
 #include <cuda_runtime.h>
 
 #include "epilogue.cuh"
@@ -22,93 +26,102 @@
 
 namespace sdc {
 
-constexpr int kSweepThreads = 64;
+constexpr int kSweepThreads = 128;
 
-int sweep_blocks(int ncoef) { return (ncoef + kSweepThreads - 1) / kSweepThreads; }
+__host__ __device__ constexpr int sweep_lanes(int M) { return M <= 1 ? 1 : (M <= 2 ? 2 : (M <= 4 ? 4 : 8)); }
+
+int sweep_blocks(int ncoef, int M) {
+    return static_cast<int>((static_cast<long long>(ncoef) * sweep_lanes(M) + kSweepThreads - 1) / kSweepThreads);
+}
+
+__device__ __forceinline__ double2 shfl2(double2 v, int src) {
+    return make_double2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
+}
 
 template <int M, bool RESID, typename R>
 __global__ void __launch_bounds__(kSweepThreads) k4_sweep(SweepParams p) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    constexpr int G = sweep_lanes(M);
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int nc = p.ncoef;
-    double rs[M][3];
-#pragma unroll
-    for (int m = 0; m < M; ++m) rs[m][0] = rs[m][1] = rs[m][2] = 0.0;
+    const int i = t / G;                                  // spectral mode
+    const int m = t - i * G;                              // node of this lane (m >= M: idle)
+    const int ic = i < nc ? i : nc - 1;                   // lanes past the end compute on a valid mode, store nothing
+    const int mr = m < M ? m : M - 1;
+    const int lane = threadIdx.x & 31;
+    const int g0 = lane - m;                              // lane of node 0 of this group
+    const double lam = p.lam[ic];
+    const int mo = p.coef_m[ic];
+    const V2<R> *Y = static_cast<const V2<R> *>(p.y);
 
-    if (i < nc) {
-        const double lam = p.lam[i];
-        const double wgt = (i <= p.T) ? 1.0 : 2.0;      // order m = 0 occupies indices 0..T
-        const int mo = p.coef_m[i];
-        const V2<R> *Y = static_cast<const V2<R> *>(p.y);
-        const double2 un_p = p.un[F_PHI * nc + i];
-        const double2 un_z = p.un[F_ZETA * nc + i];
-        const double2 un_d = p.un[F_DIV * nc + i];
-        double2 Fp[M], Fz[M], Fd[M];
-        double2 up[M], uz[M], ud[M];
-        double2 ep, ez, ed;                               // T_E of node j (of u_n when ybatch == 1)
-        if (p.ybatch == 1) vector_epilogue<R>(Y, p.dims, i, mo, p.eps, p.lam, p.epi32, ep, ez, ed);
+    // F of this lane's node
+    const double2 *u = p.ubase + mr * p.ustride;
+    const double2 up = u[F_PHI * nc + ic], uz = u[F_ZETA * nc + ic], ud = u[F_DIV * nc + ic];
+    double2 ep = make_double2(0.0, 0.0), ez = ep, ed = ep;
+    if (p.ybatch == 1) {                                  // first sweep: T_E(u_n) for every node
+        if (m == 0) vector_epilogue<R>(Y, p.dims, ic, mo, p.eps, p.lam, p.epi32, ep, ez, ed);
+        ep = shfl2(ep, g0);
+        ez = shfl2(ez, g0);
+        ed = shfl2(ed, g0);
+    } else {
+        vector_epilogue<R>(Y + static_cast<size_t>(mr) * p.dims.next * 5, p.dims, ic, mo, p.eps, p.lam, p.epi32,
+                           ep, ez, ed);
+    }
+    const double2 Fp = make_double2(ep.x - p.phibar * ud.x, ep.y - p.phibar * ud.y);
+    const double2 Fz = ez;
+    const double2 Fd = make_double2(ed.x + lam * up.x, ed.y + lam * up.y);
+
+    // quadrature row m over the group's F_j
+    double2 Rp = make_double2(0.0, 0.0), Rz = Rp, Rd = Rp;
 #pragma unroll
-        for (int j = 0; j < M; ++j) {
-            const double2 *u = p.ubase + j * p.ustride;
-            up[j] = u[F_PHI * nc + i];
-            uz[j] = u[F_ZETA * nc + i];
-            ud[j] = u[F_DIV * nc + i];
-            if (p.ybatch != 1)
-                vector_epilogue<R>(Y + static_cast<size_t>(j) * p.dims.next * 5, p.dims, i, mo, p.eps, p.lam,
-                                   p.epi32, ep, ez, ed);
-            Fp[j] = make_double2(ep.x - p.phibar * ud[j].x, ep.y - p.phibar * ud[j].y);
-            Fz[j] = ez;
-            Fd[j] = make_double2(ed.x + lam * up[j].x, ed.y + lam * up[j].y);
+    for (int j = 0; j < M; ++j) {
+        const double q = p.Q[mr][j];
+        const double2 a = shfl2(Fp, g0 + j), z = shfl2(Fz, g0 + j), dd = shfl2(Fd, g0 + j);
+        Rp.x = fma(q, a.x, Rp.x); Rp.y = fma(q, a.y, Rp.y);
+        Rz.x = fma(q, z.x, Rz.x); Rz.y = fma(q, z.y, Rz.y);
+        Rd.x = fma(q, dd.x, Rd.x); Rd.y = fma(q, dd.y, Rd.y);
+    }
+
+    double rs[3] = {0.0, 0.0, 0.0};
+    if (i < nc && m < M && m >= p.m0 && m < p.m1) {
+        const double dt = p.dt;
+        const double2 un_p = p.un[F_PHI * nc + i], un_z = p.un[F_ZETA * nc + i], un_d = p.un[F_DIV * nc + i];
+        Rp = make_double2(fma(dt, Rp.x, un_p.x), fma(dt, Rp.y, un_p.y));
+        Rz = make_double2(fma(dt, Rz.x, un_z.x), fma(dt, Rz.y, un_z.y));
+        Rd = make_double2(fma(dt, Rd.x, un_d.x), fma(dt, Rd.y, un_d.y));
+        if (RESID) {   // residual of the current iterate
+            const double wgt = (i <= p.T) ? 1.0 : 2.0;    // order m = 0 occupies indices 0..T
+            const double rpx = Rp.x - up.x, rpy = Rp.y - up.y;
+            const double rzx = Rz.x - uz.x, rzy = Rz.y - uz.y;
+            const double rdx = Rd.x - ud.x, rdy = Rd.y - ud.y;
+            rs[F_PHI] = wgt * (rpx * rpx + rpy * rpy);
+            rs[F_ZETA] = wgt * (rzx * rzx + rzy * rzy);
+            rs[F_DIV] = wgt * (rdx * rdx + rdy * rdy);
         }
-#pragma unroll
-        for (int m = 0; m < M; ++m) {
-            if (m < p.m0 || m >= p.m1) continue;
-            double2 Rp = make_double2(0, 0), Rz = Rp, Rd = Rp;
-#pragma unroll
-            for (int j = 0; j < M; ++j) {
-                const double q = p.Q[m][j];
-                Rp.x = fma(q, Fp[j].x, Rp.x); Rp.y = fma(q, Fp[j].y, Rp.y);
-                Rz.x = fma(q, Fz[j].x, Rz.x); Rz.y = fma(q, Fz[j].y, Rz.y);
-                Rd.x = fma(q, Fd[j].x, Rd.x); Rd.y = fma(q, Fd[j].y, Rd.y);
-            }
-            const double dt = p.dt;
-            Rp = make_double2(fma(dt, Rp.x, un_p.x), fma(dt, Rp.y, un_p.y));
-            Rz = make_double2(fma(dt, Rz.x, un_z.x), fma(dt, Rz.y, un_z.y));
-            Rd = make_double2(fma(dt, Rd.x, un_d.x), fma(dt, Rd.y, un_d.y));
-            if (RESID) {   // residual of the current iterate
-                const double rpx = Rp.x - up[m].x, rpy = Rp.y - up[m].y;
-                const double rzx = Rz.x - uz[m].x, rzy = Rz.y - uz[m].y;
-                const double rdx = Rd.x - ud[m].x, rdy = Rd.y - ud[m].y;
-                rs[m][F_PHI] = wgt * (rpx * rpx + rpy * rpy);
-                rs[m][F_ZETA] = wgt * (rzx * rzx + rzy * rzy);
-                rs[m][F_DIV] = wgt * (rdx * rdx + rdy * rdy);
-            }
-            // rhs = R - alpha L_g(u_m^k)
-            const double al = p.alpha[m];
-            const double2 bp = make_double2(Rp.x + al * p.phibar * ud[m].x, Rp.y + al * p.phibar * ud[m].y);
-            const double2 bd = make_double2(Rd.x - al * lam * up[m].x, Rd.y - al * lam * up[m].y);
-            const double den = p.den[m * nc + i];             // 1 / (1 + alpha^2 Phibar lambda_n)
-            const double2 np = make_double2((bp.x - al * p.phibar * bd.x) * den, (bp.y - al * p.phibar * bd.y) * den);
-            const double2 nd = make_double2(bd.x + al * lam * np.x, bd.y + al * lam * np.y);
-            double2 *o = p.out + (m - p.m0) * p.ostride;
-            o[F_PHI * nc + i] = np;
-            o[F_ZETA * nc + i] = Rz;
-            o[F_DIV * nc + i] = nd;
-        }
+        // rhs = R - alpha L_g(u_m^k)
+        const double al = p.alpha[m];
+        const double2 bp = make_double2(Rp.x + al * p.phibar * ud.x, Rp.y + al * p.phibar * ud.y);
+        const double2 bd = make_double2(Rd.x - al * lam * up.x, Rd.y - al * lam * up.y);
+        const double den = p.den[m * nc + i];             // 1 / (1 + alpha^2 Phibar lambda_n)
+        const double2 np = make_double2((bp.x - al * p.phibar * bd.x) * den, (bp.y - al * p.phibar * bd.y) * den);
+        const double2 nd = make_double2(bd.x + al * lam * np.x, bd.y + al * lam * np.y);
+        double2 *o = p.out + (m - p.m0) * p.ostride;
+        o[F_PHI * nc + i] = np;
+        o[F_ZETA * nc + i] = Rz;
+        o[F_DIV * nc + i] = nd;
     }
 
     if (!RESID) return;
-    // block reduction of the residual partial sums (warp shuffle, then smem)
+    // block reduction of the residual partial sums: lanes of the same node
+    // within a warp (stride G), then the warps through shared memory
     __shared__ double red[kSweepThreads / 32][M * 3];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int warp = threadIdx.x >> 5;
 #pragma unroll
-    for (int m = 0; m < M; ++m)
+    for (int f = 0; f < 3; ++f) {
+        double v = rs[f];
 #pragma unroll
-        for (int f = 0; f < 3; ++f) {
-            double v = rs[m][f];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-            if (lane == 0) red[warp][m * 3 + f] = v;
-        }
+        for (int o = G; o < 32; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane < M) red[warp][lane * 3 + f] = v;
+    }
     __syncthreads();
     if (threadIdx.x < M * 3) {
         double v = 0.0;
@@ -144,7 +157,7 @@ __global__ void k5_resid_reduce(const double *__restrict__ part, int nblocks, in
 
 template <typename R>
 static cudaError_t launch_sweep_t(const SweepParams &p, int M, cudaStream_t s) {
-    const int nb = sweep_blocks(p.ncoef);
+    const int nb = sweep_blocks(p.ncoef, M);
 #define SDC_SWEEP_CASE(MM)                                                           \
     case MM:                                                                         \
         if (p.resid_part) k4_sweep<MM, true, R><<<nb, kSweepThreads, 0, s>>>(p);     \
