@@ -242,11 +242,12 @@ def profile_stages(s, u0, flush, nprof: int):
     return prof, acc
 
 
-def time_adjoint(Solver, wl, nsteps: int, nsnap: int, reps: int):
+def time_adjoint(Solver, wl, nsteps: int, nsnap: int, reps: int, precision: int = 0):
     """Adjoint/forward cost: one reversed step (retape + adjoint) against one forward
-    step, and a checkpointed gradient run against the forward run of nsteps."""
+    step, and a checkpointed gradient run against the forward run of nsteps, both
+    in the given precision mode."""
     import torch
-    s = Solver.for_workload(wl)
+    s = Solver.for_workload(wl, precision=precision)
     u0 = s.initial_state(wl)
     x = u0.clone()
     ub = torch.ones_like(u0)
@@ -421,7 +422,8 @@ def cuda_arm(args, rank: int, world: int):
     adjoint = None
     if not args.no_adjoint:
         adjoint = {"t255": time_adjoint(Solver, wl, 20, 8, 5),
-                   "t127_differentiation": time_adjoint(Solver, si.WORKLOADS["t127adj"], 96, 8, 10)}
+                   "t127_differentiation": time_adjoint(Solver, si.WORKLOADS["t127adj"], 96, 8, 10),
+                   "t255_fp32": time_adjoint(Solver, wl, 20, 8, 5, precision=PRECISIONS["fp32"])}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

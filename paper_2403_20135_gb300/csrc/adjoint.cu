@@ -140,6 +140,8 @@ __global__ void __launch_bounds__(64) k3t_synth(const V2<R> *__restrict__ ybar, 
 // inverse FFT of the m <= T spectrum with m > 0 halved, scaled 1/L), the
 // grid products transposed with the recorded base fields, inverse-DFT
 // transpose (a forward FFT, m > 0 doubled) and the parity split transposed.
+// Output F1-bar[b][m][field][parity][j2] (the FP64 synthesis transpose reads
+// it along the latitudes).
 // ---------------------------------------------------------------------------
 template <typename R>
 __global__ void k2t_ring(const V2<R> *__restrict__ wbar, const V2<R> *__restrict__ gbase,
@@ -199,7 +201,7 @@ __global__ void k2t_ring(const V2<R> *__restrict__ wbar, const V2<R> *__restrict
     __syncthreads();
     fft_inplace<R>(X, S, nscratch, 4, plan, TW, false);
 
-    V2<R> *o = f1bar + (static_cast<size_t>(b) * J2 + j2) * 8 * (T + 1);
+    V2<R> *o = f1bar + static_cast<size_t>(b) * (T + 1) * 8 * J2 + j2;   // [b][m][f][parity][j2]
     for (int i = threadIdx.x; i < 4 * (T + 1); i += blockDim.x) {
         const int f = i / (T + 1), m = i - f * (T + 1);
         const V2<R> y = X[f * L + m];
@@ -210,8 +212,8 @@ __global__ void k2t_ring(const V2<R> *__restrict__ wbar, const V2<R> *__restrict
         const V2<R> fs = cscale<R>(mul_mi<R>(csub<R>(y, yc)), wm);
         V2<R> se = cadd<R>(fn, fs), so = csub<R>(fn, fs);
         if (m == 0) { se.y = 0; so.y = 0; }
-        o[(f * 2 + 0) * (T + 1) + m] = se;
-        o[(f * 2 + 1) * (T + 1) + m] = so;
+        o[(static_cast<size_t>(m) * 8 + f * 2 + 0) * J2] = se;
+        o[(static_cast<size_t>(m) * 8 + f * 2 + 1) * J2] = so;
     }
 }
 
@@ -295,8 +297,10 @@ __global__ void __launch_bounds__(256) k2t_ring_f32(const float2 *__restrict__ w
 }
 
 // ---------------------------------------------------------------------------
-// K1a^T: Z-bar_f[e] = sum_j Pbar_e(mu_j) F1-bar[b][j][f][parity(e)][m(e)],
-// one thread per extended row.
+// K1a^T (FP64): Z-bar_f[e] = sum_j Pbar_e(mu_j) F1-bar[b][m(e)][f][parity(e)][j],
+// one thread per extended row; F1-bar comes from the FP64 ring transpose with
+// the latitude index fastest (the forward projection's access pattern: two
+// latitudes per table load, contiguous rows of F1-bar per order and parity).
 // ---------------------------------------------------------------------------
 template <typename R>
 __global__ void __launch_bounds__(64) k1t_project(const V2<R> *__restrict__ f1bar, Dims d,
@@ -305,23 +309,33 @@ __global__ void __launch_bounds__(64) k1t_project(const V2<R> *__restrict__ f1ba
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     const int b = blockIdx.y;
     if (e >= d.next) return;
-    const int T = d.T;
+    const int T = d.T, J2 = d.J2;
     const int m = row_m[e];
     const int par = (e - ext_offset(T, m)) & 1;
-    const size_t jstride = static_cast<size_t>(8) * (T + 1);
-    const V2<R> *base = f1bar + static_cast<size_t>(b) * d.J2 * jstride + par * (T + 1) + m;
+    const V2<R> *W = f1bar + ((static_cast<size_t>(b) * (T + 1) + m) * 8 + par) * J2;
     const R *prow = pbar + static_cast<size_t>(e) * d.J2p;
     V2<R> acc[4];
 #pragma unroll
     for (int f = 0; f < 4; ++f) acc[f] = mk<R>(0, 0);
-    for (int j = 0; j < d.J2; ++j) {
-        const R p = prow[j];
-        const V2<R> *x = base + j * jstride;
+    const int J2e = J2 & ~1;
+    for (int j = 0; j < J2e; j += 2) {
+        const V2<R> pp = *reinterpret_cast<const V2<R> *>(prow + j);
 #pragma unroll
         for (int f = 0; f < 4; ++f) {
-            const V2<R> v = x[f * 2 * (T + 1)];
-            acc[f].x = fma(p, v.x, acc[f].x);
-            acc[f].y = fma(p, v.y, acc[f].y);
+            const V2<R> w0 = W[f * 2 * J2 + j], w1 = W[f * 2 * J2 + j + 1];
+            acc[f].x = fma(pp.x, w0.x, acc[f].x);
+            acc[f].y = fma(pp.x, w0.y, acc[f].y);
+            acc[f].x = fma(pp.y, w1.x, acc[f].x);
+            acc[f].y = fma(pp.y, w1.y, acc[f].y);
+        }
+    }
+    if (J2e < J2) {
+        const R p = prow[J2e];
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+            const V2<R> w0 = W[f * 2 * J2 + J2e];
+            acc[f].x = fma(p, w0.x, acc[f].x);
+            acc[f].y = fma(p, w0.y, acc[f].y);
         }
     }
     V2<R> *o = zbar + (static_cast<size_t>(b) * d.next + e) * 4;
