@@ -578,47 +578,61 @@ constexpr int kSynNbRows = 48;             // table rows per bulk copy (even: ch
 static_assert(8 * (kMaxSynStages + 1) <= static_cast<int>(kSynCtrlBytes), "stage and prologue barriers fit");
 constexpr size_t kSmemLimit = 227 * 1024;
 
-__host__ __device__ inline int synthesis_nb_rowstride(int nb) { return nb * 8 + 4; }   // floats, padded
+// coefficient row stride in floats: NB x NF complex values rounded to 16
+// bytes, plus 16 bytes of padding; two rows apart (the rows of an S = 2 lane
+// pair) never start in the same bank group
+__host__ __device__ constexpr int synthesis_nb_rowstride(int nb, int nf) {
+    return ((nb * nf * 2 + 3) / 4 * 4 + 4) % 16 == 0 ? (nb * nf * 2 + 3) / 4 * 4 + 8 : (nb * nf * 2 + 3) / 4 * 4 + 4;
+}
 __host__ inline int synthesis_nb_threads(int J2, int S) { return 2 * S * (((J2 + 1) / 2 + 32 / S - 1) / (32 / S) * (32 / S)); }
 __host__ inline int synthesis_nb_s(int J2) { return synthesis_nb_threads(J2, 2) <= kSynNbMaxThreads ? 2 : 1; }
 // FP32 state copies of a block, in float2 (rounded up to keep 16-byte alignment)
 __host__ __device__ inline int synthesis_nb_s32_elems(int T, int nb) { return (nb * 3 * (T + 2) + 1) & ~1; }
-__host__ inline size_t synthesis_nb_fixed(const Dims &d, int nb) {
-    return kSynCtrlBytes + static_cast<size_t>(d.T + 4) * synthesis_nb_rowstride(nb) * sizeof(float) +
-           static_cast<size_t>(nb) * 3 * (d.T + 2) * sizeof(double2) +
-           static_cast<size_t>(synthesis_nb_s32_elems(d.T, nb)) * sizeof(float2) +
-           static_cast<size_t>(d.T + 4) * sizeof(float4);
+// shared memory besides the stage ring: control, coefficient rows and, for the
+// synthesis (NF = 4), the FP64 states, their FP32 copies and the wind factors
+__host__ inline size_t synthesis_nb_fixed(const Dims &d, int nb, int nf) {
+    size_t b = kSynCtrlBytes + static_cast<size_t>(d.T + 4) * synthesis_nb_rowstride(nb, nf) * sizeof(float);
+    if (nf == 4)
+        b += static_cast<size_t>(nb) * 3 * (d.T + 2) * sizeof(double2) +
+             static_cast<size_t>(synthesis_nb_s32_elems(d.T, nb)) * sizeof(float2) +
+             static_cast<size_t>(d.T + 4) * sizeof(float4);
+    return b;
 }
-__host__ inline int synthesis_nb_stages(const Dims &d, int nb) {
+__host__ inline int synthesis_nb_stages(const Dims &d, int nb, int nf) {
     const size_t per = static_cast<size_t>(kSynNbRows) * d.J2p * sizeof(float);
-    const size_t fixed = synthesis_nb_fixed(d, nb);
+    const size_t fixed = synthesis_nb_fixed(d, nb, nf);
     const int ns = fixed < kSmemLimit ? static_cast<int>((kSmemLimit - fixed) / per) : 0;
     return ns > kMaxSynStages ? kMaxSynStages : ns;
 }
-__host__ inline size_t synthesis_nb_smem(const Dims &d, int nb) {
-    return synthesis_nb_fixed(d, nb) +
-           static_cast<size_t>(synthesis_nb_stages(d, nb)) * kSynNbRows * d.J2p * sizeof(float);
+__host__ inline size_t synthesis_nb_smem(const Dims &d, int nb, int nf) {
+    return synthesis_nb_fixed(d, nb, nf) +
+           static_cast<size_t>(synthesis_nb_stages(d, nb, nf)) * kSynNbRows * d.J2p * sizeof(float);
 }
 // whether the batched kernel serves these sizes (threads, at least two stages)
-__host__ inline bool synthesis_nb_fits(const Dims &d, int nb) {
-    return synthesis_nb_threads(d.J2, 1) <= kSynNbMaxThreads && synthesis_nb_stages(d, nb) >= 2;
+__host__ inline bool synthesis_nb_fits(const Dims &d, int nb, int nf) {
+    return synthesis_nb_threads(d.J2, 1) <= kSynNbMaxThreads && synthesis_nb_stages(d, nb, nf) >= 2;
 }
 
-template <int NB, int S>
+// NF = 4: the synthesis (coefficients prepared from the FP64 states, output
+// F1[b][j][f][parity][m]).  NF = 5: the transpose of the analysis projection
+// in the adjoint (coefficients = the rows Y-bar[b][e][5], gathered with
+// cp.async; output W-bar[b][j][g][parity][m]).
+template <int NB, int S, int NF>
 __global__ void __launch_bounds__(kSynNbMaxThreads, 1)
-    k1_synthesis_f32_nb(const double2 *__restrict__ states, long long sstride, int B, Dims d,
-                        const float *__restrict__ pbar, const float4 *__restrict__ syn32, float2 *__restrict__ f1,
-                        int nstages, int *err) {
+    k1_synthesis_f32_nb(const double2 *__restrict__ states, long long sstride, const float2 *__restrict__ ybar,
+                        int B, Dims d, const float *__restrict__ pbar, const float4 *__restrict__ syn32,
+                        float2 *__restrict__ f1, int nstages, int *err) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     uint64_t *mbar = reinterpret_cast<uint64_t *>(smem_raw);                 // [kMaxSynStages], then the prologue's
     uint64_t *mpro = mbar + kMaxSynStages;
     const int T = d.T;
-    constexpr int RS = NB * 8 + 4;                                           // coefficient row stride (floats)
+    constexpr int RS = synthesis_nb_rowstride(NB, NF);                       // coefficient row stride (floats)
     float *cf = reinterpret_cast<float *>(smem_raw + kSynCtrlBytes);         // [T + 4 rows][RS]
-    double2 *raw = reinterpret_cast<double2 *>(cf + static_cast<size_t>(T + 4) * RS);   // [NB][3][T + 2]
+    double2 *raw = reinterpret_cast<double2 *>(cf + static_cast<size_t>(T + 4) * RS);   // [NB][3][T + 2] (NF = 4)
     float2 *s32 = reinterpret_cast<float2 *>(raw + static_cast<size_t>(NB) * 3 * (T + 2));   // [NB][3][T + 2]
     float4 *sy = reinterpret_cast<float4 *>(s32 + synthesis_nb_s32_elems(T, NB));             // [T + 4]
-    float *stage = reinterpret_cast<float *>(sy + (T + 4));                  // [nstages][kSynNbRows][J2p]
+    float *stage = NF == 4 ? reinterpret_cast<float *>(sy + (T + 4))        // [nstages][kSynNbRows][J2p]
+                           : reinterpret_cast<float *>(raw);
     const size_t stage_elems = static_cast<size_t>(kSynNbRows) * d.J2p;
     const int m1 = blockIdx.x, m2 = T - blockIdx.x;
     const int b0 = blockIdx.y * NB;
@@ -647,7 +661,12 @@ __global__ void __launch_bounds__(kSynNbMaxThreads, 1)
     };
     const int nc = d.ncoef;
     int issued = 0;
-    if (threadIdx.x == 0) {
+    if (NF == 5 && threadIdx.x == 0) {
+        for (int k = 0; k < kMaxSynStages; ++k) mbar_init(&mbar[k], 1);
+        mbar_init_fence();
+        for (; issued < min(nstages, nch); ++issued) issue(issued);
+    }
+    if (NF == 4 && threadIdx.x == 0) {
         for (int k = 0; k <= kMaxSynStages; ++k) mbar_init(&mbar[k], 1);
         mbar_init_fence();
         const uint32_t n1b = static_cast<uint32_t>(nc1) * sizeof(double2);
@@ -665,6 +684,22 @@ __global__ void __launch_bounds__(kSynNbMaxThreads, 1)
         if (two) bulk_copy(sy + nn1, syn32 + ext_offset(T, m2), static_cast<uint32_t>(nn2) * sizeof(float4), mpro);
         for (; issued < min(nstages, nch); ++issued) issue(issued);
     }
+    if constexpr (NF == 5) {                             // the Y-bar rows of both orders, 8 bytes per piece
+        for (int i = threadIdx.x; i < rows * NB * 5; i += blockDim.x) {
+            const int r = i / (NB * 5), bg = i - r * (NB * 5), b = bg / 5;
+            float2 *dst = reinterpret_cast<float2 *>(cf + static_cast<size_t>(r) * RS) + bg;
+            if (b < nbv) {
+                const int e = (r < nn1) ? ext_offset(T, m1) + r : ext_offset(T, m2) + r - nn1;
+                cp_async8(dst, ybar + (static_cast<size_t>(b0 + b) * d.next + e) * 5 + (bg - 5 * b));
+            } else {
+                *dst = make_float2(0.f, 0.f);
+            }
+        }
+        cp_async_commit();
+        cp_async_wait<0>();
+        __syncthreads();
+    }
+    if constexpr (NF == 4) {
     __syncthreads();                                     // the barriers are initialised
     const bool late = !mbar_wait(mpro, 0);
     if (__syncthreads_or(late)) {
@@ -703,6 +738,7 @@ __global__ void __launch_bounds__(kSynNbMaxThreads, 1)
         o[G_V] = make_float2(-c0 * z0.y + c1 * dm.x + c2 * dp.x, c0 * z0.x + c1 * dm.y + c2 * dp.y);
     }
     __syncthreads();
+    }
 
     const int tq = blockDim.x / 2;
     const int par = threadIdx.x >= tq ? 1 : 0;
@@ -711,12 +747,12 @@ __global__ void __launch_bounds__(kSynNbMaxThreads, 1)
     const int j0 = 2 * (lt / S);
     const bool active = j0 < d.J2;
     const int jl = active ? j0 : 0;                      // idle lanes read a valid column and store nothing
-    float2 a[NB][4][2];                                  // [state][field][latitude]
+    float2 a[NB][NF][2];                                 // [state][field][latitude]
     auto reset = [&]() {
 #pragma unroll
         for (int b = 0; b < NB; ++b)
 #pragma unroll
-            for (int f = 0; f < 4; ++f) a[b][f][0] = a[b][f][1] = make_float2(0.f, 0.f);
+            for (int f = 0; f < NF; ++f) a[b][f][0] = a[b][f][1] = make_float2(0.f, 0.f);
     };
     reset();
     int c = 0;
@@ -733,25 +769,34 @@ __global__ void __launch_bounds__(kSynNbMaxThreads, 1)
 #pragma unroll 2
         for (int i = par + 2 * sp; i < cnt; i += 2 * S) {   // chunks start on even t: row i has parity i & 1
             const float2 pv = *reinterpret_cast<const float2 *>(P + i * d.J2p);
-            const float4 *ci = reinterpret_cast<const float4 *>(cc + i * RS);
+            float2 kk[NB * NF];                          // the row's coefficients, 16 bytes per load
+            if constexpr ((NB * NF) % 2 == 0) {
+                const float4 *ci = reinterpret_cast<const float4 *>(cc + i * RS);
 #pragma unroll
-            for (int b = 0; b < NB; ++b) {
-                const float4 q0 = ci[2 * b], q1 = ci[2 * b + 1];
-                const float2 k4[4] = {make_float2(q0.x, q0.y), make_float2(q0.z, q0.w), make_float2(q1.x, q1.y),
-                                      make_float2(q1.z, q1.w)};
-#pragma unroll
-                for (int f = 0; f < 4; ++f) {
-                    a[b][f][0] = caxpy(pv.x, k4[f], a[b][f][0]);
-                    a[b][f][1] = caxpy(pv.y, k4[f], a[b][f][1]);
+                for (int q = 0; q < NB * NF / 2; ++q) {
+                    const float4 v = ci[q];
+                    kk[2 * q] = make_float2(v.x, v.y);
+                    kk[2 * q + 1] = make_float2(v.z, v.w);
                 }
+            } else {
+                const float2 *ci = reinterpret_cast<const float2 *>(cc + i * RS);
+#pragma unroll
+                for (int q = 0; q < NB * NF; ++q) kk[q] = ci[q];
             }
+#pragma unroll
+            for (int b = 0; b < NB; ++b)
+#pragma unroll
+                for (int f = 0; f < NF; ++f) {
+                    a[b][f][0] = caxpy(pv.x, kk[b * NF + f], a[b][f][0]);
+                    a[b][f][1] = caxpy(pv.y, kk[b * NF + f], a[b][f][1]);
+                }
         }
         if (c == nch1 - 1 || c == nch - 1) {             // end of an order: sum the lane pair, store, restart
             if constexpr (S == 2) {
 #pragma unroll
                 for (int b = 0; b < NB; ++b)
 #pragma unroll
-                    for (int f = 0; f < 4; ++f)
+                    for (int f = 0; f < NF; ++f)
 #pragma unroll
                         for (int k = 0; k < 2; ++k) {
                             a[b][f][k].x += __shfl_xor_sync(0xffffffffu, a[b][f][k].x, 1);
@@ -765,10 +810,10 @@ __global__ void __launch_bounds__(kSynNbMaxThreads, 1)
 #pragma unroll
                     for (int b = 0; b < NB; ++b) {
                         if (b >= nbv) break;
-                        float2 *o = f1 + (static_cast<size_t>(b0 + b) * d.J2 + j0 + k) * (4 * 2 * (T + 1)) +
+                        float2 *o = f1 + (static_cast<size_t>(b0 + b) * d.J2 + j0 + k) * (NF * 2 * (T + 1)) +
                                     par * (T + 1) + m;
 #pragma unroll
-                        for (int f = 0; f < 4; ++f) o[f * 2 * (T + 1)] = a[b][f][k];
+                        for (int f = 0; f < NF; ++f) o[f * 2 * (T + 1)] = a[b][f][k];
                     }
                 }
             }
@@ -1023,18 +1068,22 @@ static cudaError_t configure(const Dims &d, const FftPlan &plan) {
         if (e != cudaSuccess) return e;
     }
     {
-        const void *fs[2][3] = {{(const void *)k1_synthesis_f32_nb<1, 1>, (const void *)k1_synthesis_f32_nb<2, 1>,
-                                 (const void *)k1_synthesis_f32_nb<4, 1>},
-                                {(const void *)k1_synthesis_f32_nb<1, 2>, (const void *)k1_synthesis_f32_nb<2, 2>,
-                                 (const void *)k1_synthesis_f32_nb<4, 2>}};
-        for (int k = 0; k < 3; ++k) {
-            if (!synthesis_nb_fits(d, 1 << k)) continue;
-            for (int si = 0; si < 2; ++si) {
-                e = cudaFuncSetAttribute(fs[si][k], cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)synthesis_nb_smem(d, 1 << k));
-                if (e != cudaSuccess) return e;
+        const void *fs[2][2][3] = {
+            {{(const void *)k1_synthesis_f32_nb<1, 1, 4>, (const void *)k1_synthesis_f32_nb<2, 1, 4>,
+              (const void *)k1_synthesis_f32_nb<4, 1, 4>},
+             {(const void *)k1_synthesis_f32_nb<1, 2, 4>, (const void *)k1_synthesis_f32_nb<2, 2, 4>,
+              (const void *)k1_synthesis_f32_nb<4, 2, 4>}},
+            {{(const void *)k1_synthesis_f32_nb<1, 1, 5>, (const void *)k1_synthesis_f32_nb<2, 1, 5>, nullptr},
+             {(const void *)k1_synthesis_f32_nb<1, 2, 5>, (const void *)k1_synthesis_f32_nb<2, 2, 5>, nullptr}}};
+        for (int fi = 0; fi < 2; ++fi)
+            for (int k = 0; k < 3 - fi; ++k) {
+                if (!synthesis_nb_fits(d, 1 << k, 4 + fi)) continue;
+                for (int si = 0; si < 2; ++si) {
+                    e = cudaFuncSetAttribute(fs[fi][si][k], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)synthesis_nb_smem(d, 1 << k, 4 + fi));
+                    if (e != cudaSuccess) return e;
+                }
             }
-        }
     }
     size_t smp = 0, smq = 0;
     project_f32_async(d, project_f32_threads(d.T), &smp, 5);
@@ -1052,27 +1101,30 @@ static cudaError_t configure(const Dims &d, const FftPlan &plan) {
     return cudaSuccess;
 }
 
-// Batched FP32 synthesis: NB = 4 states per block where it fits (else 2), 1
-// for a single state; S = 2 lane pairs per latitude pair where the block
-// stays within kSynNbMaxThreads.
+// Batched FP32 synthesis (NF = 4) or projection transpose (NF = 5): NB = 4
+// states per block where it fits (else 2), 1 for a single state; S = 2 lane
+// pairs per latitude pair where the block stays within kSynNbMaxThreads.
+template <int NF>
 static cudaError_t launch_synthesis_nb(const Dims &d, int B, const double2 *states, long long sstride,
-                                       const float *pbar, const float *syn32, float2 *f1, int *err, cudaStream_t s) {
-    const int nb = B == 1 ? 1 : ((B == 2 || !synthesis_nb_fits(d, 4)) ? 2 : 4);
+                                       const float2 *ybar, const float *pbar, const float *syn32, float2 *f1,
+                                       int *err, cudaStream_t s) {
+    // NF = 5 keeps NB <= 2: four states' 40 accumulators and coefficient rows exceed the registers
+    const int nb = B == 1 ? 1 : ((NF == 5 || B == 2 || !synthesis_nb_fits(d, 4, NF)) ? 2 : 4);
     const int S = synthesis_nb_s(d.J2);
     const dim3 g((d.T + 2) / 2, (B + nb - 1) / nb);
-    const int nt = synthesis_nb_threads(d.J2, S), ns = synthesis_nb_stages(d, nb);
-    const size_t sm = synthesis_nb_smem(d, nb);
+    const int nt = synthesis_nb_threads(d.J2, S), ns = synthesis_nb_stages(d, nb, NF);
+    const size_t sm = synthesis_nb_smem(d, nb, NF);
     const float4 *sy = reinterpret_cast<const float4 *>(syn32);
 #define SDC_SYN_NB(NBV, SV) \
-    k1_synthesis_f32_nb<NBV, SV><<<g, nt, sm, s>>>(states, sstride, B, d, pbar, sy, f1, ns, err)
+    k1_synthesis_f32_nb<NBV, SV, NF><<<g, nt, sm, s>>>(states, sstride, ybar, B, d, pbar, sy, f1, ns, err)
     if (S == 2) {
         if (nb == 1) SDC_SYN_NB(1, 2);
         else if (nb == 2) SDC_SYN_NB(2, 2);
-        else SDC_SYN_NB(4, 2);
+        else if constexpr (NF == 4) SDC_SYN_NB(4, 2);
     } else {
         if (nb == 1) SDC_SYN_NB(1, 1);
         else if (nb == 2) SDC_SYN_NB(2, 1);
-        else SDC_SYN_NB(4, 1);
+        else if constexpr (NF == 4) SDC_SYN_NB(4, 1);
     }
 #undef SDC_SYN_NB
     return cudaGetLastError();
@@ -1098,8 +1150,8 @@ static cudaError_t launch_tendency_t(const Dims &d, const FftPlan &plan, int B, 
         if (tc) {
             cudaError_t e = launch_tc_synthesis(*tc, d, B, states, sstride, tb.syn, tb.row_m, f1, s, launches);
             if (e != cudaSuccess) return e;
-        } else if (synthesis_nb_fits(d, 2)) {
-            const cudaError_t e = launch_synthesis_nb(d, B, states, sstride, pbar, tb.syn32, f1, tb.err, s);
+        } else if (synthesis_nb_fits(d, 2, 4)) {
+            const cudaError_t e = launch_synthesis_nb<4>(d, B, states, sstride, nullptr, pbar, tb.syn32, f1, tb.err, s);
             if (e != cudaSuccess) return e;
             if (launches) ++*launches;
         } else {
@@ -1179,6 +1231,7 @@ cudaError_t configure_transform_kernels(const Dims &d, const FftPlan &plan, bool
 
 cudaError_t launch_projection_transpose_f32(const Dims &d, int B, const float2 *ybar, const float *pbar,
                                             float2 *wbar, int *err, cudaStream_t s) {
+    if (synthesis_nb_fits(d, 2, 5)) return launch_synthesis_nb<5>(d, B, nullptr, 0, ybar, pbar, nullptr, wbar, err, s);
     const int g4 = (d.J2 + 3) / 4;
     const dim3 gs(B, (d.T + 2) / 2);
     const int ns = synthesis_f32_stages(d.J2p);
