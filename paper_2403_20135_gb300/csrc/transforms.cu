@@ -837,6 +837,7 @@ __global__ void __launch_bounds__(kSynNbMaxThreads, 1)
 // every W row starts on a 16-byte boundary.
 constexpr int kPrjParts = 4;
 constexpr int kPrjDepth = 4;          // per-thread cp.async stages of the table rows (ASYNC)
+constexpr int kPrjMaxThreads = 288;   // two blocks per SM fit the register file
 
 
 // ASYNC: each lane streams its own four rows through kPrjDepth private
@@ -848,7 +849,7 @@ constexpr int kPrjDepth = 4;          // per-thread cp.async stages of the table
 // W = F1-bar[b][j][f][parity][m] gathered per order into the same
 // [f][parity][j] arrangement, Z-bar[b][e][f].
 template <bool VEC, bool ASYNC, int NF>
-__global__ void __launch_bounds__(512) k3_project_f32(const float2 *__restrict__ src, Dims d,
+__global__ void __launch_bounds__(kPrjMaxThreads, 2) k3_project_f32(const float2 *__restrict__ src, Dims d,
                                                       const float *__restrict__ pbar, float2 *__restrict__ y) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2 *ws = reinterpret_cast<float2 *>(smem_raw);   // [2][2 NF][J2]
@@ -994,7 +995,7 @@ static bool project_f32_async(const Dims &d, int nthreads, size_t *bytes, int nf
 }
 
 // threads of a K3a (FP32) block: all row quads of the largest order pair,
-// kPrjParts lanes each, at most 512 (larger pairs take several passes)
+// kPrjParts lanes each, at most kPrjMaxThreads (larger pairs take several passes)
 static int project_f32_threads(int T) {
     int best = 0;
     for (int m1 = 0; m1 <= T - m1; ++m1) {
@@ -1006,7 +1007,7 @@ static int project_f32_threads(int T) {
         best = best > nq ? best : nq;
     }
     const int t = (best * kPrjParts + 31) / 32 * 32;
-    return t < 512 ? t : 512;
+    return t < kPrjMaxThreads ? t : kPrjMaxThreads;
 }
 
 // ---------------------------------------------------------------------------

@@ -88,3 +88,15 @@ def test_t511_checkpointed_adjoint():
     fd = (vals[0] - vals[1]) / (2 * eps)
     an = float(torch.real(torch.vdot(g.flatten(), d.flatten())))
     assert abs(fd - an) <= 1e-6 * abs(fd), (fd, an)
+
+
+def test_t511_fp32_step_adjoint_close_to_fp64():
+    """The FP32-mode reversed step at T511 (transposed transforms in FP32 on the
+    state-batched kernels) against the FP64 reversed step, same seeded state and
+    seed u-bar, within the FP32 per-tendency bound at this truncation."""
+    u0 = _solver().initial_state(WL)
+    ub = u0 / (u0.abs() ** 2).sum(dim=1, keepdim=True)   # each field weighted by its own scale
+    ref = to_numpy(_solver(0).step_adjoint(u0, ub))
+    got = to_numpy(_solver(1).step_adjoint(u0, ub))
+    err = rel_l2(got, ref)
+    assert np.all(err <= 2 * BASE[1] * (WL.T / 21.0) ** 1.5), err
