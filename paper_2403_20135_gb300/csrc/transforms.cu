@@ -240,34 +240,31 @@ __global__ void __launch_bounds__(256) k2_ring_f32(const float2 *__restrict__ f1
     const int j2 = blockIdx.x;
     const int b = blockIdx.y;
     const int T = d.T;
+    // the block's F1 slice (contiguous, 16-byte aligned) into the scratch arrays
+    // S and the pass twiddles into TW, all copies in flight at once
     const float2 *in = f1 + (static_cast<size_t>(b) * d.J2 + j2) * (4 * 2 * (T + 1));
-    for (int k = threadIdx.x; k < ntw; k += blockDim.x) TW[k] = twp[k];
+    float2 *raw = S;                                     // 8 (T + 1) <= 5 Lp elements
+    if ((Lp & 1) == 0) {                                 // S starts on a 16-byte boundary
+        for (int q = threadIdx.x; q < 4 * (T + 1); q += blockDim.x) cp_async16(raw + 2 * q, in + 2 * q);
+    } else {
+        for (int q = threadIdx.x; q < 8 * (T + 1); q += blockDim.x) cp_async8(raw + q, in + q);
+    }
+    for (int k = threadIdx.x; k < ntw; k += blockDim.x) cp_async8(TW + k, twp + k);
+    cp_async_commit();
     const int gap = L - 2 * T - 1;
     for (int i = threadIdx.x; i < 4 * gap; i += blockDim.x) {
         const int f = i / gap, k = T + 1 + (i - f * gap);
         X[f * Lp + fpad(k)] = make_float2(0.f, 0.f);
     }
-    // four (field, order) items per thread and pass, all loads first
-    for (int i0 = threadIdx.x; i0 < 4 * (T + 1); i0 += 4 * blockDim.x) {
-        float2 ev[4], ov[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int i = min(i0 + u * static_cast<int>(blockDim.x), 4 * (T + 1) - 1);
-            const int f = i / (T + 1), m = i - f * (T + 1);
-            ev[u] = in[(f * 2 + 0) * (T + 1) + m];
-            ov[u] = in[(f * 2 + 1) * (T + 1) + m];
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int i = i0 + u * blockDim.x;
-            if (i >= 4 * (T + 1)) break;
-            const int f = i / (T + 1), m = i - f * (T + 1);
-            float2 e = ev[u], o = ov[u];
-            if (m == 0) { e.y = 0.f; o.y = 0.f; }
-            const float2 n = cadd<float>(e, o), sv = csub<float>(e, o);
-            X[f * Lp + fpad(m)] = make_float2(n.x - sv.y, n.y + sv.x);                // n + i s
-            if (m > 0) X[f * Lp + fpad(L - m)] = make_float2(n.x + sv.y, -n.y + sv.x);   // conj(n) + i conj(s)
-        }
+    cp_async_wait<0>();
+    __syncthreads();
+    for (int i = threadIdx.x; i < 4 * (T + 1); i += blockDim.x) {
+        const int f = i / (T + 1), m = i - f * (T + 1);
+        float2 e = raw[(f * 2 + 0) * (T + 1) + m], o = raw[(f * 2 + 1) * (T + 1) + m];
+        if (m == 0) { e.y = 0.f; o.y = 0.f; }
+        const float2 n = cadd<float>(e, o), sv = csub<float>(e, o);
+        X[f * Lp + fpad(m)] = make_float2(n.x - sv.y, n.y + sv.x);                // n + i s
+        if (m > 0) X[f * Lp + fpad(L - m)] = make_float2(n.x + sv.y, -n.y + sv.x);   // conj(n) + i conj(s)
     }
     __syncthreads();
     const float2 *G;
