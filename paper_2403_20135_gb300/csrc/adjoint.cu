@@ -19,6 +19,7 @@
 // retape of the step.
 #include <cuda_runtime.h>
 
+#include "async_copy.cuh"
 #include "fft.cuh"
 #include "fft_pass.cuh"
 #include "sdc_internal.h"
@@ -233,9 +234,21 @@ __global__ void __launch_bounds__(256) k2t_ring_f32(const float2 *__restrict__ w
     const int j2 = blockIdx.x;
     const int b = blockIdx.y;
     const int T = d.T, J2 = d.J2;
-    for (int k = threadIdx.x; k < ntw; k += blockDim.x) TW[k] = twp[k];
+    // the block's W-bar slice (contiguous, 16-byte aligned) into the scratch
+    // arrays S and the pass twiddles into TW, all copies in flight at once
+    const float2 *win = wbar + (static_cast<size_t>(b) * J2 + j2) * 10 * (T + 1);
+    float2 *raw = S;                                     // 10 (T + 1) <= 5 Lp elements
+    if ((Lp & 1) == 0) {                                 // S starts on a 16-byte boundary
+        for (int q = threadIdx.x; q < 5 * (T + 1); q += blockDim.x) cp_async16(raw + 2 * q, win + 2 * q);
+    } else {
+        for (int q = threadIdx.x; q < 10 * (T + 1); q += blockDim.x) cp_async8(raw + q, win + q);
+    }
+    for (int k = threadIdx.x; k < ntw; k += blockDim.x) cp_async8(TW + k, twp + k);
+    cp_async_commit();
     const float fN = rw[4 * j2], ic2 = 2.f * rw[4 * j2 + 1], wt = rw[4 * j2 + 2], wp = rw[4 * j2 + 3];
     const float invL = 1.f / float(L);
+    cp_async_wait<0>();
+    __syncthreads();
     for (int i = threadIdx.x; i < 5 * L; i += blockDim.x) {
         const int g = i / L, k = i - g * L;
         float2 z = make_float2(0.f, 0.f);
@@ -244,7 +257,7 @@ __global__ void __launch_bounds__(256) k2t_ring_f32(const float2 *__restrict__ w
         if (k <= T) m = k;
         else if (k >= L - T) { m = L - k; conj = true; }
         if (m >= 0) {
-            const float2 *src = wbar + (static_cast<size_t>(b) * J2 + j2) * 10 * (T + 1) + g * 2 * (T + 1) + m;
+            const float2 *src = raw + g * 2 * (T + 1) + m;
             const float2 ws = src[0], wa = src[T + 1];
             const float wg = (g == P_E) ? wp : wt;
             const float sc = wg * ((m == 0) ? invL : 0.5f * invL);
