@@ -42,7 +42,7 @@ template <typename R> __device__ __forceinline__ V2<R> mul_i(V2<R> a) { return m
 template <typename R> __device__ __forceinline__ V2<R> mul_mi(V2<R> a) { return mk<R>(a.y, -a.x); }
 
 // ---------------------------------------------------------------------------
-// Mixed radix (4, 2, 3) Stockham FFT of nb length-L sequences in shared
+// Mixed radix (8, 4, 2, 3) Stockham FFT of nb length-L sequences in shared
 // memory, all threads of the block cooperating.  Forward: e^{-i...};
 // inverse: e^{+i...}, unscaled.  Returns the buffer that holds the result.
 // ---------------------------------------------------------------------------
@@ -60,6 +60,23 @@ __device__ __forceinline__ void butterfly(V2<R> *v, bool inv) {
         const V2<R> a = v[0];
         v[0] = cadd<R>(a, v[1]);
         v[1] = csub<R>(a, v[1]);
+    } else if constexpr (RADIX == 8) {
+        // even and odd samples: two 4-point DFTs, the odd one twiddled by
+        // w_8^k1, then 2-point DFTs: out[k1] = a + w c, out[k1 + 4] = a - w c
+        V2<R> a[4] = {v[0], v[2], v[4], v[6]}, c[4] = {v[1], v[3], v[5], v[7]};
+        butterfly<R, 4>(a, inv);
+        butterfly<R, 4>(c, inv);
+        const R h = R(0.70710678118654752440);   // cos(pi/4)
+        c[1] = inv ? mk<R>(h * (c[1].x - c[1].y), h * (c[1].x + c[1].y))
+                   : mk<R>(h * (c[1].x + c[1].y), h * (c[1].y - c[1].x));
+        c[2] = inv ? mul_i<R>(c[2]) : mul_mi<R>(c[2]);
+        c[3] = inv ? mk<R>(-h * (c[3].x + c[3].y), h * (c[3].x - c[3].y))
+                   : mk<R>(h * (c[3].y - c[3].x), -h * (c[3].x + c[3].y));
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            v[k] = cadd<R>(a[k], c[k]);
+            v[k + 4] = csub<R>(a[k], c[k]);
+        }
     } else {   // 3
         const R h = R(0.86602540378443864676);   // sqrt(3)/2
         const V2<R> t1 = cadd<R>(v[1], v[2]);
@@ -114,7 +131,8 @@ __device__ V2<R> *fft_batch(V2<R> *x, V2<R> *y, int nb, const FftPlan &plan,
     int Ns = 1;
     for (int s = 0; s < plan.nstages; ++s) {
         const int radix = plan.radix[s];
-        if (radix == 4) fft_stage<R, 4>(src, dst, nb, L, Ns, tw, inv);
+        if (radix == 8) fft_stage<R, 8>(src, dst, nb, L, Ns, tw, inv);
+        else if (radix == 4) fft_stage<R, 4>(src, dst, nb, L, Ns, tw, inv);
         else if (radix == 2) fft_stage<R, 2>(src, dst, nb, L, Ns, tw, inv);
         else fft_stage<R, 3>(src, dst, nb, L, Ns, tw, inv);
         __syncthreads();

@@ -303,8 +303,9 @@ bool fft_plan(int L, FftPlan &plan) {
     plan.L = L;
     plan.nstages = 0;
     int rest = L;
-    while (rest % 4 == 0) { plan.radix[plan.nstages++] = 4; rest /= 4; }
-    if (rest % 2 == 0) { plan.radix[plan.nstages++] = 2; rest /= 2; }
+    while (rest % 8 == 0 && plan.nstages < kMaxStages) { plan.radix[plan.nstages++] = 8; rest /= 8; }
+    if (rest % 4 == 0 && plan.nstages < kMaxStages) { plan.radix[plan.nstages++] = 4; rest /= 4; }
+    if (rest % 2 == 0 && plan.nstages < kMaxStages) { plan.radix[plan.nstages++] = 2; rest /= 2; }
     while (rest % 3 == 0) {
         if (plan.nstages >= kMaxStages) return false;
         plan.radix[plan.nstages++] = 3;

@@ -40,7 +40,7 @@ def _cuda(u):
 
 
 # sizes: several latitude chunks and a ragged tail (J/2 = 17, 24, 50 vs 64-wide
-# chunks), odd/even truncations, nlon with radix 2, 3, 4 stages
+# chunks), odd/even truncations, nlon with radix 8, 4, 2, 3 stages
 CASES = [(5, 8, 16), (21, 34, 72), (31, 48, 96), (42, 64, 128), (63, 100, 192)]
 
 
