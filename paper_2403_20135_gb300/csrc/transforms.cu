@@ -159,17 +159,32 @@ __global__ void k2_ring(const V2<R> *__restrict__ f1, V2<R> *__restrict__ f2, Di
     const int b = blockIdx.y;
     const int T = d.T, L = plan.L;
     const V2<R> *in = f1 + (static_cast<size_t>(b) * d.J2 + j2) * (4 * 2 * (T + 1));
-    for (int k = threadIdx.x; k < L; k += blockDim.x) TW[k] = tw[k];
+    // the twiddles and, where the scratch arrays hold it, the block's F1 slice
+    // arrive by cp.async (16-byte pieces: V2<double> elements), all in flight at once
+    const bool staged = sizeof(V2<R>) == 16 && static_cast<size_t>(nscratch) * L >= 8u * (T + 1);
+    if constexpr (sizeof(V2<R>) == 16) {
+        for (int k = threadIdx.x; k < L; k += blockDim.x) cp_async16(TW + k, tw + k);
+        if (staged)
+            for (int q = threadIdx.x; q < 8 * (T + 1); q += blockDim.x) cp_async16(S + q, in + q);
+        cp_async_commit();
+    } else {
+        for (int k = threadIdx.x; k < L; k += blockDim.x) TW[k] = tw[k];
+    }
     // Hermitian packing of north (real part) and south (imaginary part):
     // the band m <= T and its mirror L - m from one load, zeros in between.
     for (int i = threadIdx.x; i < 4 * (L - 2 * T - 1); i += blockDim.x) {
         const int f = i / (L - 2 * T - 1), k = T + 1 + (i - f * (L - 2 * T - 1));
         X[f * L + k] = mk<R>(0, 0);
     }
+    if constexpr (sizeof(V2<R>) == 16) {
+        cp_async_wait<0>();
+        __syncthreads();
+    }
+    const V2<R> *src = staged ? S : in;
     for (int i = threadIdx.x; i < 4 * (T + 1); i += blockDim.x) {
         const int f = i / (T + 1), m = i - f * (T + 1);
-        V2<R> e = in[(f * 2 + 0) * (T + 1) + m];
-        V2<R> o = in[(f * 2 + 1) * (T + 1) + m];
+        V2<R> e = src[(f * 2 + 0) * (T + 1) + m];
+        V2<R> o = src[(f * 2 + 1) * (T + 1) + m];
         if (m == 0) { e.y = 0; o.y = 0; }
         const V2<R> n = cadd<R>(e, o), s = csub<R>(e, o);
         X[f * L + m] = mk<R>(n.x - s.y, n.y + s.x);            // n + i s
