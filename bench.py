@@ -44,7 +44,7 @@ FP32_SIMT_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # a batch of 4 states at the bench workload (ncu capture summarised in
 # profiles/kernels_t255_fp64.md); the traffic is the batch's F1 input, so a
 # launch of b states moves b/4 of it.
-RING_FP64_TRAFFIC_B4 = 25.3e6 + 46.8e3
+RING_FP64_TRAFFIC_B4 = 25.291264e6 + 228.096e3
 
 
 def _peaks():
