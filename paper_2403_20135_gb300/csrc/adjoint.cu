@@ -20,6 +20,7 @@
 #include <cuda_runtime.h>
 
 #include "async_copy.cuh"
+#include "convert.cuh"
 #include "fft.cuh"
 #include "fft_pass.cuh"
 #include "sdc_internal.h"
@@ -61,13 +62,17 @@ __global__ void k3t_epilogue(const double2 *__restrict__ abar, long long astride
     const double2 z0 = ld(F_ZETA, n), zm = ld(F_ZETA, n - 1), zp = ld(F_ZETA, n + 1);
     const double2 d0 = ld(F_DIV, n), dm = ld(F_DIV, n - 1), dp = ld(F_DIV, n + 1);
     const double2 p0 = ld(F_PHI, n), pm = ld(F_PHI, n - 1), pp = ld(F_PHI, n + 1);
-    // (i c) z = (-c z.y, c z.x)
+    // (i c) z = (-c z.y, c z.x); narrowed to FP32 on the integer pipe (convert.cuh)
+    auto nr = [](double x) -> R {
+        if constexpr (sizeof(R) == sizeof(float)) return f64_to_f32_rn(x);
+        else return x;
+    };
     V2<R> *o = ybar + (static_cast<size_t>(b) * d.next + e) * 5;
-    o[P_A] = mk<R>(R(-mi * z0.y - cu * dm.x + cl * dp.x), R(mi * z0.x - cu * dm.y + cl * dp.y));
-    o[P_B] = mk<R>(R(-cu * zm.x + cl * zp.x + mi * d0.y), R(-cu * zm.y + cl * zp.y - mi * d0.x));
-    o[P_C] = mk<R>(R(-mi * p0.y), R(mi * p0.x));
-    o[P_D] = mk<R>(R(-cu * pm.x + cl * pp.x), R(-cu * pm.y + cl * pp.y));
-    o[P_E] = mk<R>(R(lam * d0.x), R(lam * d0.y));
+    o[P_A] = mk<R>(nr(-mi * z0.y - cu * dm.x + cl * dp.x), nr(mi * z0.x - cu * dm.y + cl * dp.y));
+    o[P_B] = mk<R>(nr(-cu * zm.x + cl * zp.x + mi * d0.y), nr(-cu * zm.y + cl * zp.y - mi * d0.x));
+    o[P_C] = mk<R>(nr(-mi * p0.y), nr(mi * p0.x));
+    o[P_D] = mk<R>(nr(-cu * pm.x + cl * pp.x), nr(-cu * pm.y + cl * pp.y));
+    o[P_E] = mk<R>(nr(lam * d0.x), nr(lam * d0.y));
 }
 
 // ---------------------------------------------------------------------------
@@ -375,9 +380,10 @@ __global__ void k1t_epilogue(const V2<R> *__restrict__ zbar, Dims d, const doubl
     const int t = i - order_offset(T, m);
     const int e = ext_offset(T, m) + t;
     const V2<R> *Z = zbar + static_cast<size_t>(b) * d.next * 4;
-    auto ld = [&](int row, int f) -> double2 {
+    auto ld = [&](int row, int f) -> double2 {       // widened on the integer pipe (convert.cuh)
         const V2<R> v = Z[static_cast<size_t>(row) * 4 + f];
-        return make_double2(double(v.x), double(v.y));
+        if constexpr (sizeof(R) == sizeof(float)) return make_double2(f32_to_f64(v.x), f32_to_f64(v.y));
+        else return make_double2(v.x, v.y);
     };
     const double2 z0 = make_double2(0.0, 0.0);
     const double2 zz = ld(e, G_ZETA), zp = ld(e, G_PHI), zu = ld(e, G_U), zv = ld(e, G_V);

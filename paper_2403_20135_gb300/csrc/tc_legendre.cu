@@ -24,6 +24,7 @@
 #include <cstdint>
 
 #include "async_copy.cuh"
+#include "convert.cuh"
 #include "sdc_internal.h"
 
 namespace sdc {
@@ -410,14 +411,14 @@ __global__ void k1_prep_split(TcTables tc, const double2 *__restrict__ states, l
     if (!in(n)) z0 = d0 = p0 = zero;
     if (!in(n - 1)) zm = dm = zero;
     if (!in(n + 1)) zp = dp = zero;
-    const float x[8] = {float(z0.x),
-                        float(z0.y),
-                        float(p0.x),
-                        float(p0.y),
-                        float(-c0 * d0.y - c1 * zm.x - c2 * zp.x),
-                        float(c0 * d0.x - c1 * zm.y - c2 * zp.y),
-                        float(-c0 * z0.y + c1 * dm.x + c2 * dp.x),
-                        float(c0 * z0.x + c1 * dm.y + c2 * dp.y)};
+    const float x[8] = {f64_to_f32_rn(z0.x),             // narrowed on the integer pipe (convert.cuh)
+                        f64_to_f32_rn(z0.y),
+                        f64_to_f32_rn(p0.x),
+                        f64_to_f32_rn(p0.y),
+                        f64_to_f32_rn(-c0 * d0.y - c1 * zm.x - c2 * zp.x),
+                        f64_to_f32_rn(c0 * d0.x - c1 * zm.y - c2 * zp.y),
+                        f64_to_f32_rn(-c0 * z0.y + c1 * dm.x + c2 * dp.x),
+                        f64_to_f32_rn(c0 * z0.x + c1 * dm.y + c2 * dp.y)};
     const int p = ne & 1, q = ne >> 1;
     const int krb = tc_group_krows(T, m, p) / 8;
     const int kb = q >> 3, kr = q & 7;

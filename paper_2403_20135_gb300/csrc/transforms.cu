@@ -469,11 +469,12 @@ __global__ void __launch_bounds__(256) k1_synthesis_f32(const double2 *__restric
         auto ld = [&](int f, int k) -> float2 {
             if (k < m || k > T) return make_float2(0.f, 0.f);
             const double2 v = st[f * nc + off + k - m];
-            return make_float2(float(v.x), float(v.y));
+            return make_float2(f64_to_f32_rn(v.x), f64_to_f32_rn(v.y));
         };
         const float2 z0 = ld(F_ZETA, n), zm = ld(F_ZETA, n - 1), zp = ld(F_ZETA, n + 1);
         const float2 d0 = ld(F_DIV, n), dm = ld(F_DIV, n - 1), dp = ld(F_DIV, n + 1);
-        const float c0 = float(syn[3 * e]), c1 = float(syn[3 * e + 1]), c2 = float(syn[3 * e + 2]);
+        const float c0 = f64_to_f32_rn(syn[3 * e]), c1 = f64_to_f32_rn(syn[3 * e + 1]),
+                    c2 = f64_to_f32_rn(syn[3 * e + 2]);
         cf[r * 4 + G_ZETA] = z0;
         cf[r * 4 + G_PHI] = ld(F_PHI, n);
         cf[r * 4 + G_U] = make_float2(-c0 * d0.y - c1 * zm.x - c2 * zp.x, c0 * d0.x - c1 * zm.y - c2 * zp.y);
