@@ -1,7 +1,8 @@
 // Bulk asynchronous copies (global -> shared, cp.async.bulk) completed on
 // shared-memory mbarriers, and a bounded wait on an mbarrier phase (device
-// code only).  A wait gives up after kWaitLimit polls and returns false; the
-// callers turn that into an error flag instead of spinning forever.
+// code only).  A wait gives up after kWaitLimit polls or kWaitNs nanoseconds
+// of the global timer, whichever comes first, and returns false; the callers
+// turn that into an error flag instead of spinning forever.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -11,6 +12,13 @@
 namespace sdc {
 
 constexpr uint32_t kWaitLimit = 1u << 22;
+constexpr unsigned long long kWaitNs = 1000000000ull;   // one second
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -24,6 +32,7 @@ __device__ __forceinline__ void mbar_init_fence() { asm volatile("fence.mbarrier
 
 __device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t phase) {
     uint32_t done = 0;
+    const unsigned long long t0 = global_ns();
     for (uint32_t it = 0; it < kWaitLimit && !done; ++it) {
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
@@ -31,6 +40,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t phase) {
             "selp.u32 %0, 1, 0, p;\n\t}"
             : "=r"(done)
             : "r"(smem_u32(mbar)), "r"(phase));
+        if (!done && (it & 255u) == 255u && global_ns() - t0 > kWaitNs) break;
     }
     return done != 0;
 }

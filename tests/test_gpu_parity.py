@@ -237,3 +237,23 @@ def test_invalid_shapes_raise():
     from paper_2403_20135_gb300 import SdcError
     with pytest.raises(SdcError):
         s.tendency(torch.zeros((4, 3, s.ncoef), dtype=torch.complex128, device="cuda"))
+
+
+def test_nan_state_reports_divergence_and_context_stays_usable():
+    """Failure injected on the host: a NaN coefficient in the input state makes the
+    residual norms non-finite, sdc_step (residuals requested) returns
+    SDC_EDIVERGED, and the next step of a good state is unaffected."""
+    from paper_2403_20135_gb300 import SdcError
+    from paper_2403_20135_gb300._lib import SDC_EDIVERGED
+    T, J, L, M, K = 21, 34, 72, 3, 3
+    o = _oracle(T, J, L)
+    u0 = swe.initial_state(_wl(T, J, L, M, K), o)
+    bad = u0.copy()
+    bad[1, 7] = complex(np.nan, 0.0)
+    s = _solver(T, J, L, M, K, 600.0)
+    with pytest.raises(SdcError) as err:
+        s.step(_cuda(bad), residuals=True)
+    assert err.value.status == SDC_EDIVERGED
+    got = to_numpy(s.step(_cuda(u0), residuals=True)[0])
+    ref = osdc.swe_step(o, u0, osdc.Collocation(M), K, 600.0)
+    assert np.all(rel_l2(got, ref) <= TOL_EVAL * 10)
