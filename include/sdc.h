@@ -193,6 +193,21 @@ int sdc_grid_to_spec(sdc_ctx *ctx, const double *grid, void *spec);
 int sdc_grid_coords(const sdc_ctx *ctx, double *mu, double *w);
 int sdc_collocation(const sdc_ctx *ctx, double *tau, double *Q);
 
+/* Checkpoint and resume of a state (the paper keeps none between runs).
+ * sdc_save writes to the file `path` (NUL-terminated) one JSON header line --
+ * format tag "sdc-swe-state-1", the context's truncation, nlat, nlon, nodes,
+ * sweeps, dt and physical constants, the caller's step index, ncoef, the field
+ * order ["phi", "zeta", "div"] and the byte count -- followed by the raw FP64
+ * state [3][ncoef] (16 bytes per complex coefficient, little-endian as in
+ * memory).  sdc_load reads such a file into the device state of this context
+ * and returns its step index through `step` (may be NULL).  state: device
+ * memory of 3 * ncoef double2, owned by the caller.  Both synchronise the
+ * context's stream.  SDC_EINVAL for NULL arguments, a file that cannot be
+ * opened, written or read, a header of another format, truncation or size, or
+ * a data section of the wrong length; SDC_ECUDA if a copy fails. */
+int sdc_save(sdc_ctx *ctx, const void *state, long long step, const char *path);
+int sdc_load(sdc_ctx *ctx, void *state, long long *step, const char *path);
+
 /* Work counters since creation (HOST outputs, any may be NULL): explicit
  * tendency evaluations of single states, per-node implicit solves, and the
  * library's own kernel launches.  Algorithm 2 performs 1 + (K-1) M

@@ -52,6 +52,8 @@ SIGNATURES = {
     "sdc_grid_coords": (_I, [_P, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
     "sdc_collocation": (_I, [_P, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
     "sdc_counters": (_I, [_P, ctypes.POINTER(_LL), ctypes.POINTER(_LL), ctypes.POINTER(_LL)]),
+    "sdc_save": (_I, [_P, _P, _LL, ctypes.c_char_p]),
+    "sdc_load": (_I, [_P, _P, ctypes.POINTER(_LL), ctypes.c_char_p]),
     "sdc_launches_per_step": (_I, [_P, ctypes.POINTER(_I)]),
     "sdc_sync": (_I, [_P]),
     "sdc_profile_step": (_I, [_P, _P, ctypes.POINTER(_D), ctypes.POINTER(_I)]),

@@ -901,6 +901,74 @@ int sdc_collocation(const sdc_ctx *c, double *tau, double *Q) {
     return SDC_OK;
 }
 
+// Checkpoint file: one JSON header line, then the raw FP64 state [3][ncoef]
+// (16 bytes per complex coefficient, the machine's little-endian layout).
+static const char kStateFormat[] = "sdc-swe-state-1";
+
+int sdc_save(sdc_ctx *c, const void *state, long long step, const char *path) {
+    if (!c || !state || !path) return fail(SDC_EINVAL, "NULL argument");
+    const size_t n = 3ULL * c->d.ncoef;
+    std::vector<double2> h(n);
+    SDC_CUDA(cudaMemcpyAsync(h.data(), state, n * sizeof(double2), cudaMemcpyDeviceToHost, c->stream));
+    SDC_CUDA(cudaStreamSynchronize(c->stream));
+    char hdr[1024];
+    const int len = std::snprintf(
+        hdr, sizeof(hdr),
+        "{\"format\": \"%s\", \"truncation\": %d, \"nlat\": %d, \"nlon\": %d, \"nodes\": %d, "
+        "\"sweeps\": %d, \"dt\": %.17g, \"radius\": %.17g, \"omega\": %.17g, \"gravity\": %.17g, "
+        "\"mean_depth\": %.17g, \"step\": %lld, \"ncoef\": %d, \"fields\": [\"phi\", \"zeta\", \"div\"], "
+        "\"bytes\": %zu}\n",
+        kStateFormat, c->T, c->J, c->L, c->M, c->K, c->dt, c->phys.radius, c->phys.omega, c->phys.gravity,
+        c->phys.mean_depth, step, c->d.ncoef, n * sizeof(double2));
+    if (len <= 0 || len >= static_cast<int>(sizeof(hdr))) return fail(SDC_EINVAL, "header too long");
+    FILE *f = std::fopen(path, "wb");
+    if (!f) return fail(SDC_EINVAL, "cannot open the file for writing");
+    const bool ok = std::fwrite(hdr, 1, static_cast<size_t>(len), f) == static_cast<size_t>(len) &&
+                    std::fwrite(h.data(), sizeof(double2), n, f) == n;
+    if (std::fclose(f) != 0 || !ok) return fail(SDC_EINVAL, "cannot write the file");
+    return SDC_OK;
+}
+
+// value of an integer field "key": N in a one-line JSON header (false if absent)
+static bool header_int(const std::string &hdr, const char *key, long long *out) {
+    const std::string k = std::string("\"") + key + "\":";
+    const size_t at = hdr.find(k);
+    if (at == std::string::npos) return false;
+    const char *p = hdr.c_str() + at + k.size();
+    char *end = nullptr;
+    *out = std::strtoll(p, &end, 10);
+    return end != p;
+}
+
+int sdc_load(sdc_ctx *c, void *state, long long *step, const char *path) {
+    if (!c || !state || !path) return fail(SDC_EINVAL, "NULL argument");
+    FILE *f = std::fopen(path, "rb");
+    if (!f) return fail(SDC_EINVAL, "cannot open the file for reading");
+    std::string hdr;
+    for (int ch; (ch = std::fgetc(f)) != EOF && ch != '\n' && hdr.size() < 4096;) hdr.push_back(static_cast<char>(ch));
+    long long T = -1, nc = -1, st = 0, bytes = -1;
+    const size_t n = 3ULL * c->d.ncoef;
+    const bool hdr_ok = hdr.find(std::string("\"format\": \"") + kStateFormat + "\"") != std::string::npos &&
+                        header_int(hdr, "truncation", &T) && header_int(hdr, "ncoef", &nc) &&
+                        header_int(hdr, "step", &st) && header_int(hdr, "bytes", &bytes);
+    if (!hdr_ok) {
+        std::fclose(f);
+        return fail(SDC_EINVAL, "not a state file of this library");
+    }
+    if (T != c->T || nc != c->d.ncoef || bytes != static_cast<long long>(n * sizeof(double2))) {
+        std::fclose(f);
+        return fail(SDC_EINVAL, "state file of another truncation");
+    }
+    std::vector<double2> h(n);
+    const bool got = std::fread(h.data(), sizeof(double2), n, f) == n && std::fgetc(f) == EOF;
+    std::fclose(f);
+    if (!got) return fail(SDC_EINVAL, "state file truncated or too long");
+    SDC_CUDA(cudaMemcpyAsync(state, h.data(), n * sizeof(double2), cudaMemcpyHostToDevice, c->stream));
+    SDC_CUDA(cudaStreamSynchronize(c->stream));
+    if (step) *step = st;
+    return SDC_OK;
+}
+
 int sdc_counters(const sdc_ctx *c, long long *evals, long long *solves, long long *launches) {
     if (!c) return fail(SDC_EINVAL, "ctx is NULL");
     if (evals) *evals = c->n_explicit;

@@ -7,6 +7,7 @@ torch provides device memory and the stream, the library does all the work.
 from __future__ import annotations
 
 import ctypes
+import os
 
 import numpy as np
 import torch
@@ -91,6 +92,20 @@ class Solver:
         if residuals:
             return state_out, np.array(res[:]).reshape(self.sweeps, 3)
         return state_out
+
+    def save(self, state: torch.Tensor, path: str, step: int = 0) -> None:
+        """Write the state and a step index to a checkpoint file (sdc_save)."""
+        self._check_state(state)
+        _lib.check(self.lib.sdc_save(self.h, _ptr(state), int(step), os.fsencode(path)), "sdc_save")
+
+    def load(self, path: str, state: torch.Tensor | None = None):
+        """Read a checkpoint file of this truncation (sdc_load): (state, step)."""
+        if state is None:
+            state = torch.empty((3, self.ncoef), dtype=torch.complex128, device="cuda")
+        self._check_state(state)
+        step = ctypes.c_longlong(0)
+        _lib.check(self.lib.sdc_load(self.h, _ptr(state), ctypes.byref(step), os.fsencode(path)), "sdc_load")
+        return state, step.value
 
     def run(self, state: torch.Tensor, nsteps: int) -> torch.Tensor:
         self._check_state(state)
