@@ -295,10 +295,9 @@ cudaError_t enqueue_step(sdc_ctx *c, cudaStream_t s, bool with_resid, int *launc
     p.coef_m = tb.coef_m;
     p.ncoef = c->d.ncoef;
     p.T = c->T;
-    p.dt = c->dt;
     p.phibar = c->phys.gravity * c->phys.mean_depth;
     for (int m = 0; m < M; ++m)
-        for (int j = 0; j < M; ++j) p.Q[m][j] = c->Q[m * M + j];
+        for (int j = 0; j < M; ++j) p.Q[m][j] = c->dt * c->Q[m * M + j];
     p.resid_part = with_resid ? c->resid_part : nullptr;
 
     for (int k = 0; k < K; ++k) {             // sweep k+1

@@ -69,9 +69,8 @@ struct SweepParams {
     int ncoef;
     int T;
     int m0, m1;                   // nodes updated: [m0, m1)
-    double dt;
     double phibar;
-    double Q[kMaxNodes][kMaxNodes];
+    double Q[kMaxNodes][kMaxNodes];   // dt * q_{m,j}
     double alpha[kMaxNodes];      // dt * q^Delta_{m,m}
 };
 

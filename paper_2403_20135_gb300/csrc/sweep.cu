@@ -70,8 +70,8 @@ __global__ void __launch_bounds__(kSweepThreads) k4_sweep(SweepParams p) {
     const double2 Fz = ez;
     const double2 Fd = make_double2(ed.x + lam * up.x, ed.y + lam * up.y);
 
-    // quadrature row m over the group's F_j
-    double2 Rp = make_double2(0.0, 0.0), Rz = Rp, Rd = Rp;
+    // R_m = u_n + quadrature row m over the group's F_j (p.Q holds dt q_{m,j})
+    double2 Rp = p.un[F_PHI * nc + ic], Rz = p.un[F_ZETA * nc + ic], Rd = p.un[F_DIV * nc + ic];
 #pragma unroll
     for (int j = 0; j < M; ++j) {
         const double q = p.Q[mr][j];
@@ -83,11 +83,6 @@ __global__ void __launch_bounds__(kSweepThreads) k4_sweep(SweepParams p) {
 
     double rs[3] = {0.0, 0.0, 0.0};
     if (i < nc && m < M && m >= p.m0 && m < p.m1) {
-        const double dt = p.dt;
-        const double2 un_p = p.un[F_PHI * nc + i], un_z = p.un[F_ZETA * nc + i], un_d = p.un[F_DIV * nc + i];
-        Rp = make_double2(fma(dt, Rp.x, un_p.x), fma(dt, Rp.y, un_p.y));
-        Rz = make_double2(fma(dt, Rz.x, un_z.x), fma(dt, Rz.y, un_z.y));
-        Rd = make_double2(fma(dt, Rd.x, un_d.x), fma(dt, Rd.y, un_d.y));
         if (RESID) {   // residual of the current iterate
             const double wgt = (i <= p.T) ? 1.0 : 2.0;    // order m = 0 occupies indices 0..T
             const double rpx = Rp.x - up.x, rpy = Rp.y - up.y;
