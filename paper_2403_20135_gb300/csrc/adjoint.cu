@@ -451,7 +451,7 @@ __global__ void __launch_bounds__(256) k4t_sweep(SweepAdjParams p) {
         double2 Sp = make_double2(0.0, 0.0), Sz = Sp, Sd = Sp;
 #pragma unroll
         for (int m = 0; m < M; ++m) {
-            const double q = p.dt * p.Q[m][j];
+            const double q = p.Q[m][j];                  // dt q_{m,j}
             Sp.x = fma(q, sp[m].x, Sp.x); Sp.y = fma(q, sp[m].y, Sp.y);
             Sz.x = fma(q, sz[m].x, Sz.x); Sz.y = fma(q, sz[m].y, Sz.y);
             Sd.x = fma(q, sd[m].x, Sd.x); Sd.y = fma(q, sd[m].y, Sd.y);

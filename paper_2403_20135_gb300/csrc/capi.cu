@@ -382,10 +382,9 @@ cudaError_t enqueue_step_adjoint(sdc_ctx *c, cudaStream_t s, int *launches) {
     SweepAdjParams p{};
     p.lam = c->lam;
     p.ncoef = c->d.ncoef;
-    p.dt = c->dt;
     p.phibar = c->phys.gravity * c->phys.mean_depth;
     for (int m = 0; m < M; ++m)
-        for (int j = 0; j < M; ++j) p.Q[m][j] = c->Q[m * M + j];
+        for (int j = 0; j < M; ++j) p.Q[m][j] = c->dt * c->Q[m * M + j];
     p.ubn = c->ubn;
     p.ebar0 = c->eb0;
     p.ubout = c->ub;

@@ -151,9 +151,8 @@ struct SweepAdjParams {
     int m0, m1;                   // nodes the sweep updated
     int fold;                     // first sweep: sum node adjoints into u-bar_n / E-bar_0
     int init_un;
-    double dt;
     double phibar;
-    double Q[kMaxNodes][kMaxNodes];
+    double Q[kMaxNodes][kMaxNodes];   // dt * q_{m,j}
     double alpha[kMaxNodes];
 };
 
