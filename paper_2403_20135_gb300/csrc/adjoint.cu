@@ -418,8 +418,10 @@ __global__ void k1t_epilogue(const V2<R> *__restrict__ zbar, Dims d, const doubl
 // With `fold` (the first sweep, where every u_j^0 is u_n and every E_j^0 is
 // T_E(u_n)) the node adjoints are summed into u-bar_n and E-bar_0.
 // ---------------------------------------------------------------------------
+constexpr int kAdjSweepThreads = 64;   // 514 blocks at T255: every SM gets work
+
 template <int M>
-__global__ void __launch_bounds__(256) k4t_sweep(SweepAdjParams p) {
+__global__ void __launch_bounds__(kAdjSweepThreads) k4t_sweep(SweepAdjParams p) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int nc = p.ncoef;
     if (i >= nc) return;
@@ -667,16 +669,17 @@ cudaError_t launch_tendency_adjoint(const Dims &d, const FftPlan &plan, bool fp3
 }
 
 cudaError_t launch_sweep_adjoint(const SweepAdjParams &p, int M, cudaStream_t s, int *launches) {
-    const int nb = (p.ncoef + 255) / 256;
+    const int nb = (p.ncoef + kAdjSweepThreads - 1) / kAdjSweepThreads;
+    constexpr int t = kAdjSweepThreads;
     switch (M) {
-        case 1: k4t_sweep<1><<<nb, 256, 0, s>>>(p); break;
-        case 2: k4t_sweep<2><<<nb, 256, 0, s>>>(p); break;
-        case 3: k4t_sweep<3><<<nb, 256, 0, s>>>(p); break;
-        case 4: k4t_sweep<4><<<nb, 256, 0, s>>>(p); break;
-        case 5: k4t_sweep<5><<<nb, 256, 0, s>>>(p); break;
-        case 6: k4t_sweep<6><<<nb, 256, 0, s>>>(p); break;
-        case 7: k4t_sweep<7><<<nb, 256, 0, s>>>(p); break;
-        case 8: k4t_sweep<8><<<nb, 256, 0, s>>>(p); break;
+        case 1: k4t_sweep<1><<<nb, t, 0, s>>>(p); break;
+        case 2: k4t_sweep<2><<<nb, t, 0, s>>>(p); break;
+        case 3: k4t_sweep<3><<<nb, t, 0, s>>>(p); break;
+        case 4: k4t_sweep<4><<<nb, t, 0, s>>>(p); break;
+        case 5: k4t_sweep<5><<<nb, t, 0, s>>>(p); break;
+        case 6: k4t_sweep<6><<<nb, t, 0, s>>>(p); break;
+        case 7: k4t_sweep<7><<<nb, t, 0, s>>>(p); break;
+        case 8: k4t_sweep<8><<<nb, t, 0, s>>>(p); break;
         default: return cudaErrorInvalidValue;
     }
     if (launches) *launches += 1;
