@@ -81,7 +81,11 @@ typedef enum {
      * SDC_QDELTA_MIN_SR_NS: tau_m / M in every sweep (Q - diag(q^Delta) is
      *   nilpotent: the iteration's non-stiff limit);
      * SDC_QDELTA_IMPLICIT_EULER: tau_m in every sweep (one implicit Euler
-     *   step from t_n to each node).
+     *   step from t_n to each node);
+     * SDC_QDELTA_MIN_SR_S: in every sweep the positive diagonal, increasing
+     *   in m, for which I - diag(q^Delta)^{-1} Q is nilpotent (the stiff limit
+     *   of the sweep vanishes after M sweeps), found once per context by
+     *   damped Newton; SDC_EUNSUPPORTED if it is not reached.
      * Any other value returns SDC_EINVAL.  Changing the rule re-uploads the
      * solve denominators and drops the captured graphs. */
     SDC_OPT_QDELTA_RULE = 1,
@@ -101,7 +105,13 @@ typedef enum {
      * max(2 nodes, 4) extra states (SDC_ECUDA / SDC_ENOMEM on failure). */
     SDC_OPT_METHOD = 2
 } sdc_option;
-enum { SDC_QDELTA_CLAMPED = 0, SDC_QDELTA_LITERAL = 1, SDC_QDELTA_MIN_SR_NS = 2, SDC_QDELTA_IMPLICIT_EULER = 3 };
+enum {
+    SDC_QDELTA_CLAMPED = 0,
+    SDC_QDELTA_LITERAL = 1,
+    SDC_QDELTA_MIN_SR_NS = 2,
+    SDC_QDELTA_IMPLICIT_EULER = 3,
+    SDC_QDELTA_MIN_SR_S = 4
+};
 enum { SDC_METHOD_DSDC = 0, SDC_METHOD_SERIAL_SDC = 1, SDC_METHOD_IMEX2 = 2 };
 
 /* Create a solver for truncation T on an nlat x nlon Gauss grid with M
@@ -207,6 +217,14 @@ int sdc_collocation(const sdc_ctx *ctx, double *tau, double *Q);
  * a data section of the wrong length; SDC_ECUDA if a copy fails. */
 int sdc_save(sdc_ctx *ctx, const void *state, long long step, const char *path);
 int sdc_load(sdc_ctx *ctx, void *state, long long *step, const char *path);
+
+/* The diagonal coefficients q^Delta_{m,m} (m = 0..nodes-1) that rule (an
+ * SDC_QDELTA_* value) gives at sweep `sweep` (1-based) on Radau-right nodes
+ * -- what a context with that rule uses (Sec. 4.2).  Host only (no GPU, no
+ * context); qdelta is a HOST array of `nodes` doubles.  SDC_EINVAL for nodes
+ * outside [1, 8], sweep < 1, an unknown rule or NULL; SDC_EUNSUPPORTED if the
+ * MIN-SR-S iteration does not reach its root. */
+int sdc_qdelta(int nodes, int rule, int sweep, double *qdelta);
 
 /* Work counters since creation (HOST outputs, any may be NULL): explicit
  * tendency evaluations of single states, per-node implicit solves, and the

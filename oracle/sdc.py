@@ -10,8 +10,11 @@ Test infrastructure only (see the package docstring).
   "clamped" q(k) = min(k, M) (default) and "literal" q(k) = k.  Two further
   diagonals from the family the paper points to for other coefficient
   choices (Sec. 4.2, Sec. 6): "min-sr-ns" q^Delta_{m,m} = tau_m / M in every
-  sweep, and "ie" q^Delta_{m,m} = tau_m in every sweep (each node one
-  implicit Euler step from t_n).
+  sweep, "ie" q^Delta_{m,m} = tau_m in every sweep (each node one implicit
+  Euler step from t_n), and "min-sr-s": the positive diagonal D, increasing
+  in m, for which I - D^{-1} Q is nilpotent (all eigenvalues of D^{-1} Q
+  equal to 1), found as the root of "characteristic polynomial of D^{-1} Q
+  = (x - 1)^M" by a general nonlinear solver from D = 2 tau / M.
 * Node update, Eq. (7): u_m^{k+1} = u_n + dt sum_j Q[m,j] (f_I(u_j^k) + f_E(u_j^k))
   + dt q^Delta_{m,m} (f_I(u_m^{k+1}) - f_I(u_m^k)), solved as
   u_m^{k+1} - alpha f_I(u_m^{k+1}) = beta (Eq. (8)) with alpha = dt q^Delta_{m,m}.
@@ -56,7 +59,33 @@ def collocation_matrix(tau: np.ndarray) -> np.ndarray:
     return Q
 
 
-QDELTA_RULES = ("clamped", "literal", "min-sr-ns", "ie")
+QDELTA_RULES = ("clamped", "literal", "min-sr-ns", "ie", "min-sr-s")
+
+
+_MIN_SR_S_CACHE: dict = {}
+
+
+def min_sr_s(tau: np.ndarray) -> np.ndarray:
+    """MIN-SR-S diagonal: eigenvalues of D^{-1} Q all 1 (see the module notes)."""
+    key = tuple(np.asarray(tau, dtype=float).tolist())
+    if key not in _MIN_SR_S_CACHE:
+        _MIN_SR_S_CACHE[key] = _min_sr_s_solve(np.asarray(tau, dtype=float))
+    return _MIN_SR_S_CACHE[key].copy()
+
+
+def _min_sr_s_solve(tau: np.ndarray) -> np.ndarray:
+    from scipy.optimize import root
+    M = tau.size
+    if M == 1:                                        # D^{-1} Q = q_11 / d_1 = 1 / d_1
+        return np.ones(1)
+    Q = collocation_matrix(tau)
+    target = np.poly(np.ones(M))                      # coefficients of (x - 1)^M
+    sol = root(lambda d: np.poly(Q / d[:, None])[1:] - target[1:], 2.0 * tau / M, method="hybr",
+               options={"xtol": 1e-14})
+    d = sol.x
+    if not (np.all(d > 0) and np.all(np.diff(d) > 0)):
+        raise ValueError("MIN-SR-S: the increasing positive root was not reached")
+    return d
 
 
 def qdelta(tau: np.ndarray, k: int, rule: str = "clamped") -> np.ndarray:
@@ -70,6 +99,8 @@ def qdelta(tau: np.ndarray, k: int, rule: str = "clamped") -> np.ndarray:
         return tau / float(M)
     if rule == "ie":
         return tau.copy()
+    if rule == "min-sr-s":
+        return min_sr_s(tau)
     raise ValueError(f"unknown q-delta rule {rule!r}")
 
 

@@ -16,7 +16,7 @@ SDC_FP64, SDC_MIXED_FP32, SDC_MIXED_BF16X3, SDC_MIXED_BF16X6 = 0, 1, 2, 3
 SDC_OK, SDC_EINVAL, SDC_ENOMEM, SDC_ECUDA, SDC_EDIVERGED, SDC_ESTATE, SDC_EUNSUPPORTED = range(7)
 SDC_OPT_QDELTA_RULE = 1
 SDC_OPT_METHOD = 2
-SDC_QDELTA_CLAMPED, SDC_QDELTA_LITERAL, SDC_QDELTA_MIN_SR_NS, SDC_QDELTA_IMPLICIT_EULER = 0, 1, 2, 3
+SDC_QDELTA_CLAMPED, SDC_QDELTA_LITERAL, SDC_QDELTA_MIN_SR_NS, SDC_QDELTA_IMPLICIT_EULER, SDC_QDELTA_MIN_SR_S = range(5)
 SDC_METHOD_DSDC, SDC_METHOD_SERIAL_SDC, SDC_METHOD_IMEX2 = 0, 1, 2
 
 
@@ -53,6 +53,7 @@ SIGNATURES = {
     "sdc_collocation": (_I, [_P, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
     "sdc_counters": (_I, [_P, ctypes.POINTER(_LL), ctypes.POINTER(_LL), ctypes.POINTER(_LL)]),
     "sdc_save": (_I, [_P, _P, _LL, ctypes.c_char_p]),
+    "sdc_qdelta": (_I, [_I, _I, _I, ctypes.POINTER(_D)]),
     "sdc_load": (_I, [_P, _P, ctypes.POINTER(_LL), ctypes.c_char_p]),
     "sdc_launches_per_step": (_I, [_P, ctypes.POINTER(_I)]),
     "sdc_sync": (_I, [_P]),

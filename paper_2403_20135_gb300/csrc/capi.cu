@@ -54,6 +54,7 @@ struct sdc_ctx {
     cudaStream_t stream = nullptr;       // caller's stream
     cudaStream_t cap = nullptr;          // private stream used for graph capture
     std::vector<double> mu, w, tau, Q;
+    std::vector<double> qd_min_sr_s;     // MIN-SR-S diagonal, computed when that rule is selected
 
     // device tables
     double *pbar = nullptr;
@@ -127,14 +128,21 @@ cudaError_t upload(T **dst, const T *src, size_t n) {
 
 // Diagonal coefficient q^Delta_{m,m} of sweep k (1-based) for node m (0-based),
 // Sec. 4.2: MIN-SR-FLEX tau_m / k (the q(k) reading for k > M selected by the
-// rule), MIN-SR-NS tau_m / M, or the implicit-Euler diagonal tau_m.
-double qdelta_coef(const sdc_ctx *c, int k, int m) {
-    switch (c->qdelta_rule) {
-        case SDC_QDELTA_LITERAL: return c->tau[m] / k;
-        case SDC_QDELTA_MIN_SR_NS: return c->tau[m] / c->M;
-        case SDC_QDELTA_IMPLICIT_EULER: return c->tau[m];
-        default: return c->tau[m] / (k < c->M ? k : c->M);
+// rule), MIN-SR-NS tau_m / M, the implicit-Euler diagonal tau_m, or
+// MIN-SR-S (computed once per context by min_sr_s_diagonal).
+// MIN-SR-S: the increasing diagonal making the stiff-limit sweep nilpotent.
+double qdelta_value(int rule, int M, const std::vector<double> &tau, const std::vector<double> &mss, int k, int m) {
+    switch (rule) {
+        case SDC_QDELTA_LITERAL: return tau[m] / k;
+        case SDC_QDELTA_MIN_SR_NS: return tau[m] / M;
+        case SDC_QDELTA_IMPLICIT_EULER: return tau[m];
+        case SDC_QDELTA_MIN_SR_S: return mss[m];
+        default: return tau[m] / (k < M ? k : M);
     }
+}
+
+double qdelta_coef(const sdc_ctx *c, int k, int m) {
+    return qdelta_value(c->qdelta_rule, c->M, c->tau, c->qd_min_sr_s, k, m);
 }
 
 DeviceTables tables(const sdc_ctx *c) {
@@ -793,7 +801,13 @@ int sdc_destroy(sdc_ctx *c) {
 int sdc_set_option(sdc_ctx *c, int key, int value) {
     if (!c) return fail(SDC_EINVAL, "ctx is NULL");
     if (key == SDC_OPT_QDELTA_RULE) {
-        if (value < SDC_QDELTA_CLAMPED || value > SDC_QDELTA_IMPLICIT_EULER) return fail(SDC_EINVAL, "bad q-delta rule");
+        if (value < SDC_QDELTA_CLAMPED || value > SDC_QDELTA_MIN_SR_S) return fail(SDC_EINVAL, "bad q-delta rule");
+        if (value == SDC_QDELTA_MIN_SR_S && c->qd_min_sr_s.empty()) {
+            std::vector<double> dd;
+            if (!min_sr_s_diagonal(c->M, c->tau, c->Q, dd))
+                return fail(SDC_EUNSUPPORTED, "MIN-SR-S diagonal not reached for this node count");
+            c->qd_min_sr_s = dd;
+        }
         if (value != c->qdelta_rule) {
             c->qdelta_rule = value;
             SDC_CUDA(cudaStreamSynchronize(c->stream));
@@ -964,6 +978,17 @@ int sdc_load(sdc_ctx *c, void *state, long long *step, const char *path) {
     SDC_CUDA(cudaMemcpyAsync(state, h.data(), n * sizeof(double2), cudaMemcpyHostToDevice, c->stream));
     SDC_CUDA(cudaStreamSynchronize(c->stream));
     if (step) *step = st;
+    return SDC_OK;
+}
+
+int sdc_qdelta(int nodes, int rule, int sweep, double *qdelta) {
+    if (nodes < 1 || nodes > kMaxNodes || sweep < 1 || !qdelta) return fail(SDC_EINVAL, "bad argument");
+    if (rule < SDC_QDELTA_CLAMPED || rule > SDC_QDELTA_MIN_SR_S) return fail(SDC_EINVAL, "bad q-delta rule");
+    std::vector<double> tau, Q, mss;
+    radau_right(nodes, tau, Q);
+    if (rule == SDC_QDELTA_MIN_SR_S && !min_sr_s_diagonal(nodes, tau, Q, mss))
+        return fail(SDC_EUNSUPPORTED, "MIN-SR-S diagonal not reached for this node count");
+    for (int m = 0; m < nodes; ++m) qdelta[m] = qdelta_value(rule, nodes, tau, mss, sweep, m);
     return SDC_OK;
 }
 

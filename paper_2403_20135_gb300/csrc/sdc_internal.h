@@ -203,6 +203,8 @@ __host__ __device__ inline int tc_group_krows(int T, int m, int p) { return (tc_
 // ---- host-side precompute (tables.cpp) ----------------------------------
 void gauss_legendre(int J, std::vector<double> &mu, std::vector<double> &w);
 void radau_right(int M, std::vector<double> &tau, std::vector<double> &Q);
+// MIN-SR-S diagonal (increasing root of the stiff-limit nilpotency conditions); false if not reached
+bool min_sr_s_diagonal(int M, const std::vector<double> &tau, const std::vector<double> &Q, std::vector<double> &d);
 // Pbar_n^m(mu_j) for the northern latitudes j < J2, extended packing, rows
 // padded to J2p: table[(ext_offset(m) + n - m) * J2p + j].
 void legendre_table(int T, int J2, int J2p, const std::vector<double> &mu, std::vector<double> &table);

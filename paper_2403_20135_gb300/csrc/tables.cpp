@@ -117,6 +117,140 @@ void radau_right(int M, std::vector<double> &tau, std::vector<double> &Q) {
     }
 }
 
+// Determinant of the square submatrix of the M x M row-major A kept by the
+// index mask `keep` (Gaussian elimination with partial pivoting; 1 for none).
+static double masked_det(const std::vector<double> &A, int M, unsigned keep) {
+    int idx[16], n = 0;
+    for (int i = 0; i < M; ++i)
+        if (keep & (1u << i)) idx[n++] = i;
+    double a[16][16];
+    for (int r = 0; r < n; ++r)
+        for (int c = 0; c < n; ++c) a[r][c] = A[idx[r] * M + idx[c]];
+    double det = 1.0;
+    for (int k = 0; k < n; ++k) {
+        int piv = k;
+        for (int r = k + 1; r < n; ++r)
+            if (std::fabs(a[r][k]) > std::fabs(a[piv][k])) piv = r;
+        if (a[piv][k] == 0.0) return 0.0;
+        if (piv != k) {
+            for (int c = 0; c < n; ++c) std::swap(a[k][c], a[piv][c]);
+            det = -det;
+        }
+        det *= a[k][k];
+        for (int r = k + 1; r < n; ++r) {
+            const double f = a[r][k] / a[k][k];
+            for (int c = k; c < n; ++c) a[r][c] -= f * a[k][c];
+        }
+    }
+    return det;
+}
+
+// MIN-SR-S diagonal: the positive, increasing d_1 < ... < d_M for which the
+// stiff-limit sweep matrix I - D^{-1} Q is nilpotent, i.e. every eigenvalue
+// of D^{-1} Q is 1, i.e. det(x Q - D) = det(Q) (x - 1)^M.  Comparing the
+// coefficients of x^{M-k} gives, for k = 1..M,
+//   sum over index sets S of size k of (prod_{i in S} d_i) det(Q with S's rows and columns removed)
+//     = C(M, k) det(Q),
+// solved by damped Newton in y = log d (keeps d positive) from d = 2 tau / M,
+// each equation scaled by C(M, k) |det Q|.  Returns false if the iteration
+// does not reach such a root (d increasing, ||(I - D^{-1}Q)^M|| < 1e-9).
+bool min_sr_s_diagonal(int M, const std::vector<double> &tau, const std::vector<double> &Q, std::vector<double> &d) {
+    if (M < 1 || M > 8) return false;
+    d.assign(M, 0.0);
+    const unsigned full = (1u << M) - 1u;
+    std::vector<double> minor(1u << M);                   // det of Q without the rows/columns in S
+    for (unsigned S = 0; S <= full; ++S) minor[S] = masked_det(Q, M, full & ~S);
+    const double detQ = minor[0];
+    double binom[9] = {1, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int k = 1; k <= M; ++k) binom[k] = binom[k - 1] * (M - k + 1) / k;
+    std::vector<double> y(M), F(M), J(M * M), step(M);
+    for (int i = 0; i < M; ++i) y[i] = std::log(2.0 * tau[i] / M);
+    auto residual = [&](const std::vector<double> &yy, std::vector<double> &FF, std::vector<double> *JJ) {
+        std::fill(FF.begin(), FF.end(), 0.0);
+        if (JJ) std::fill(JJ->begin(), JJ->end(), 0.0);
+        for (unsigned S = 1; S <= full; ++S) {
+            int k = 0;
+            double sumy = 0.0;
+            for (int i = 0; i < M; ++i)
+                if (S & (1u << i)) { ++k; sumy += yy[i]; }
+            const double term = std::exp(sumy) * minor[S];
+            FF[k - 1] += term;
+            if (JJ)
+                for (int i = 0; i < M; ++i)
+                    if (S & (1u << i)) (*JJ)[(k - 1) * M + i] += term;
+        }
+        double nrm = 0.0;
+        for (int k = 1; k <= M; ++k) {
+            const double sc = binom[k] * std::fabs(detQ);
+            FF[k - 1] = (FF[k - 1] - binom[k] * detQ) / sc;
+            if (JJ)
+                for (int i = 0; i < M; ++i) (*JJ)[(k - 1) * M + i] /= sc;
+            nrm += FF[k - 1] * FF[k - 1];
+        }
+        return std::sqrt(nrm);
+    };
+    std::vector<double> yt(M), Ft(M);
+    for (int it = 0; it < 100; ++it) {
+        const double f0 = residual(y, F, &J);
+        if (!std::isfinite(f0)) return false;
+        // solve J step = F (partial pivoting on a copy)
+        std::vector<double> A = J, b = F;
+        for (int k = 0; k < M; ++k) {
+            int piv = k;
+            for (int r = k + 1; r < M; ++r)
+                if (std::fabs(A[r * M + k]) > std::fabs(A[piv * M + k])) piv = r;
+            if (A[piv * M + k] == 0.0) return false;
+            if (piv != k) {
+                for (int c = 0; c < M; ++c) std::swap(A[k * M + c], A[piv * M + c]);
+                std::swap(b[k], b[piv]);
+            }
+            for (int r = k + 1; r < M; ++r) {
+                const double f = A[r * M + k] / A[k * M + k];
+                for (int c = k; c < M; ++c) A[r * M + c] -= f * A[k * M + c];
+                b[r] -= f * b[k];
+            }
+        }
+        for (int k = M - 1; k >= 0; --k) {
+            double acc = b[k];
+            for (int c = k + 1; c < M; ++c) acc -= A[k * M + c] * step[c];
+            step[k] = acc / A[k * M + k];
+        }
+        double lam = 1.0, f1 = f0;
+        for (; lam > 1e-8; lam *= 0.5) {
+            for (int i = 0; i < M; ++i) yt[i] = y[i] - lam * step[i];
+            f1 = residual(yt, Ft, nullptr);
+            if (std::isfinite(f1) && f1 < (1.0 - 1e-4 * lam) * f0) break;
+        }
+        if (lam <= 1e-8) break;                          // no descent left: converged or stuck
+        double move = 0.0;
+        for (int i = 0; i < M; ++i) {
+            move = std::max(move, std::fabs(lam * step[i]));
+            y[i] = yt[i];
+        }
+        if (move < 1e-14) break;
+    }
+    for (int i = 0; i < M; ++i) d[i] = std::exp(y[i]);
+    for (int i = 1; i < M; ++i)
+        if (!(d[i] > d[i - 1])) return false;
+    // nilpotency check: (I - D^{-1} Q)^M
+    std::vector<double> K(M * M), P(M * M, 0.0), T(M * M);
+    for (int r = 0; r < M; ++r)
+        for (int c = 0; c < M; ++c) K[r * M + c] = (r == c ? 1.0 : 0.0) - Q[r * M + c] / d[r];
+    P = K;
+    for (int p = 1; p < M; ++p) {
+        for (int r = 0; r < M; ++r)
+            for (int c = 0; c < M; ++c) {
+                double acc = 0.0;
+                for (int k = 0; k < M; ++k) acc += P[r * M + k] * K[k * M + c];
+                T[r * M + c] = acc;
+            }
+        P = T;
+    }
+    double worst = 0.0;
+    for (double v : P) worst = std::max(worst, std::fabs(v));
+    return worst < 1e-9;
+}
+
 // Normalised associated Legendre functions (unit L2 norm on [-1, 1], no
 // Condon-Shortley phase) at the northern Gauss latitudes, degrees m..T+1.
 // Pbar_0^0 = 1/sqrt(2), Pbar_m^m = sqrt((2m+1)/(2m)) sqrt(1-mu^2) Pbar_{m-1}^{m-1},

@@ -46,7 +46,7 @@ class Solver:
             self.set_method(method)
 
     def set_qdelta_rule(self, rule: int):
-        """Diagonal q^Delta rule: SDC_QDELTA_CLAMPED, _LITERAL, _MIN_SR_NS or _IMPLICIT_EULER."""
+        """Diagonal q^Delta rule: SDC_QDELTA_CLAMPED, _LITERAL, _MIN_SR_NS, _IMPLICIT_EULER or _MIN_SR_S."""
         _lib.check(self.lib.sdc_set_option(self.h, _lib.SDC_OPT_QDELTA_RULE, rule), "sdc_set_option")
 
     def set_method(self, method: int):

@@ -4,6 +4,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -70,3 +71,33 @@ def test_null_arguments(lib):
     assert lib.sdc_ncoef(None) == -1
     assert lib.sdc_step(None, None, None, None) == _lib.SDC_EINVAL
     assert lib.sdc_run(None, None, 1) == _lib.SDC_EINVAL
+
+
+@pytest.mark.parametrize("M", range(1, 9))
+def test_host_qdelta_coefficients_match_oracle(lib, M):
+    """sdc_qdelta (host only, no GPU): the diagonal of every rule at sweeps 1..6
+    against the oracle, which finds MIN-SR-S by a different formulation and
+    solver (characteristic-polynomial root with scipy against the library's
+    damped Newton on the principal-minor expansion)."""
+    from oracle import sdc as osdc
+    from paper_2403_20135_gb300 import _lib
+    names = {_lib.SDC_QDELTA_CLAMPED: "clamped", _lib.SDC_QDELTA_LITERAL: "literal",
+             _lib.SDC_QDELTA_MIN_SR_NS: "min-sr-ns", _lib.SDC_QDELTA_IMPLICIT_EULER: "ie",
+             _lib.SDC_QDELTA_MIN_SR_S: "min-sr-s"}
+    out = (ctypes.c_double * M)()
+    for rule, name in names.items():
+        coll = osdc.Collocation(M, name)
+        for k in range(1, 7):
+            assert lib.sdc_qdelta(M, rule, k, out) == 0
+            # the MIN-SR-S root is ill-conditioned (a coalescing eigenvalue): 1e-10 at M = 8
+            tol = 1e-10 if name == "min-sr-s" else 1e-13
+            np.testing.assert_allclose(np.array(out[:]), coll.qdelta(k), rtol=tol, atol=1e-14)
+
+
+def test_host_qdelta_rejects_bad_arguments(lib):
+    out = (ctypes.c_double * 8)()
+    assert lib.sdc_qdelta(0, 0, 1, out) == 1
+    assert lib.sdc_qdelta(9, 0, 1, out) == 1
+    assert lib.sdc_qdelta(4, 0, 0, out) == 1
+    assert lib.sdc_qdelta(4, 5, 1, out) == 1
+    assert lib.sdc_qdelta(4, 0, 1, None) == 1

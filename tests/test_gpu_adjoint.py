@@ -89,10 +89,11 @@ def test_step_adjoint_matches_oracle(M, K):
     assert np.all(rel_l2(got, ref) <= 1e-11), rel_l2(got, ref)
 
 
-@pytest.mark.parametrize("rule", ["min-sr-ns", "ie"])
+@pytest.mark.parametrize("rule", ["min-sr-ns", "ie", "min-sr-s"])
 def test_step_adjoint_other_qdelta_rules(rule):
     import paper_2403_20135_gb300 as pkg
-    code = {"min-sr-ns": pkg.SDC_QDELTA_MIN_SR_NS, "ie": pkg.SDC_QDELTA_IMPLICIT_EULER}[rule]
+    code = {"min-sr-ns": pkg.SDC_QDELTA_MIN_SR_NS, "ie": pkg.SDC_QDELTA_IMPLICIT_EULER,
+            "min-sr-s": pkg.SDC_QDELTA_MIN_SR_S}[rule]
     T, J, L, M, K = 21, 34, 72, 3, 4
     o = _oracle(T, J, L)
     wl = si.Workload("a", 0, T, J, L, M, K, 600.0, 1, 1, (100.0, 100.0))

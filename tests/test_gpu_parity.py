@@ -111,11 +111,11 @@ def test_one_step_and_residuals_match_oracle(M, K):
     np.testing.assert_allclose(r, np.stack(res), rtol=1e-10)
 
 
-@pytest.mark.parametrize("rule", ["literal", "min-sr-ns", "ie"])
+@pytest.mark.parametrize("rule", ["literal", "min-sr-ns", "ie", "min-sr-s"])
 def test_qdelta_rules_match_oracle(rule):
     import paper_2403_20135_gb300 as pkg
     code = {"literal": pkg.SDC_QDELTA_LITERAL, "min-sr-ns": pkg.SDC_QDELTA_MIN_SR_NS,
-            "ie": pkg.SDC_QDELTA_IMPLICIT_EULER}[rule]
+            "ie": pkg.SDC_QDELTA_IMPLICIT_EULER, "min-sr-s": pkg.SDC_QDELTA_MIN_SR_S}[rule]
     T, J, L, M, K = 21, 34, 72, 3, 5
     o = _oracle(T, J, L)
     u0 = swe.initial_state(_wl(T, J, L, M, K), o)

@@ -114,9 +114,32 @@ def test_implicit_euler_diagonal_sweeps_from_t_n():
         np.testing.assert_allclose(got, _dense_collocation(A + B, u0, coll.Q, dt), rtol=1e-12)
 
 
+def test_min_sr_s_two_nodes_closed_form():
+    """M = 2 (tau = 1/3, 1): det(xQ - D) = det(Q)(x - 1)^2 reduces to d1 d2 = 1/6 and
+    3 d1 + 5 d2 = 4, whose increasing positive root is ((4 - sqrt 6)/6, (4 + sqrt 6)/10)."""
+    d = sdc.Collocation(2, "min-sr-s").qdelta(1)
+    np.testing.assert_allclose(d, [(4 - np.sqrt(6)) / 6, (4 + np.sqrt(6)) / 10], rtol=1e-13)
+
+
+@pytest.mark.parametrize("M", [2, 3, 4, 5, 8])
+def test_min_sr_s_stiff_limit_nilpotent(M):
+    """MIN-SR-S: positive, increasing, the same in every sweep, and the stiff-limit
+    sweep matrix I - D^{-1} Q nilpotent -- checked through its eigenvalues (a
+    different computation from the characteristic-polynomial root the oracle
+    solves for: a nilpotent perturbation of size eps spreads them by about
+    eps^(1/M)) and through its M-th power."""
+    coll = sdc.Collocation(M, "min-sr-s")
+    d = coll.qdelta(3)
+    assert np.all(d > 0) and np.all(np.diff(d) > 0)
+    np.testing.assert_array_equal(d, coll.qdelta(1))
+    K = np.eye(M) - coll.Q / d[:, None]
+    assert np.abs(np.linalg.eigvals(K)).max() < 1e-12 ** (1.0 / M) * 10
+    assert np.abs(np.linalg.matrix_power(K, M)).max() < 1e-10
+
+
 def test_unknown_qdelta_rule_is_rejected():
     with pytest.raises(ValueError):
-        sdc.Collocation(3, "min-sr-s").qdelta(1)
+        sdc.Collocation(3, "min-sr-x").qdelta(1)
 
 
 def _linear_problem(A, B):
