@@ -133,7 +133,10 @@ int sdc_create(sdc_ctx **out, int truncation, int nlat, int nlon, int nodes, int
  * no-op. */
 int sdc_destroy(sdc_ctx *ctx);
 
-/* Set an option (sdc_option); SDC_EINVAL for an unknown key or value. */
+/* Set an option (sdc_option); SDC_EINVAL for an unknown key or value,
+ * SDC_EUNSUPPORTED if the MIN-SR-S diagonal is not reached, SDC_ECUDA /
+ * SDC_ENOMEM if a reference integrator's first selection cannot allocate.
+ * Synchronises the context's stream when the setting changes. */
 int sdc_set_option(sdc_ctx *ctx, int key, int value);
 
 /* Number of complex coefficients per field, (T+1)(T+2)/2; -1 for NULL. */
