@@ -587,7 +587,7 @@ __global__ void __launch_bounds__(256) k1_synthesis_f32(const double2 *__restric
 // shuffle at the end of each order); a thread keeps two latitudes x NB states
 // x 4 fields (64 accumulators at NB = 4).
 constexpr int kSynNbMaxThreads = 384;
-constexpr int kSynNbRows = 48;             // table rows per bulk copy (even: chunks start on even t)
+constexpr int kSynNbRows = 56;             // table rows per bulk copy (even: chunks start on even t)
 static_assert(8 * (kMaxSynStages + 1) <= static_cast<int>(kSynCtrlBytes), "stage and prologue barriers fit");
 constexpr size_t kSmemLimit = 227 * 1024;
 
@@ -779,7 +779,7 @@ __global__ void __launch_bounds__(kSynNbMaxThreads, 1)
         }
         const float *P = stage + (c % nstages) * stage_elems + jl;
         const float *cc = cf + static_cast<size_t>((c >= nch1 ? nn1 : 0) + t0) * RS;
-#pragma unroll 2
+#pragma unroll 4
         for (int i = par + 2 * sp; i < cnt; i += 2 * S) {   // chunks start on even t: row i has parity i & 1
             const float2 pv = *reinterpret_cast<const float2 *>(P + i * d.J2p);
             float2 kk[NB * NF];                          // the row's coefficients, 16 bytes per load
