@@ -6,8 +6,10 @@
 //                                  northern latitudes, split by the parity of
 //                                  n - m (even/odd symmetry about the equator)
 //   K2 ring       (per ring pair): inverse FFT -> grid products -> forward FFT
-//   K3 analysis   (per order m):   Fourier -> spectral, with the vector
-//                                  (div/curl) epilogue written out per mode
+//   K3 analysis   (per order m):   Fourier -> spectral projections; the vector
+//                                  (div/curl) epilogue per mode runs in
+//                                  k3_epilogue for a standalone tendency and
+//                                  inside the sweep kernel within a step
 //
 // The (1 - mu^2) d/dmu terms of the vector transforms are moved onto the
 // coefficients with the recurrence
