@@ -103,7 +103,17 @@ typedef enum {
      * sdc_tendency_adjoint) need SDC_METHOD_DSDC and return SDC_EUNSUPPORTED
      * otherwise.  Selecting a reference integrator the first time allocates
      * max(2 nodes, 4) extra states (SDC_ECUDA / SDC_ENOMEM on failure). */
-    SDC_OPT_METHOD = 2
+    SDC_OPT_METHOD = 2,
+    /* Implicit node weights of serial IMEX SDC (SDC_METHOD_SERIAL_SDC), the
+     * lower-triangular q^Delta of Eq. (6):
+     * SDC_SERIAL_IMPLICIT_EULER (default): dtau_j, backward Euler across the
+     *   node intervals as Eq. (6) writes it;
+     * SDC_SERIAL_IMPLICIT_LU: the transpose of the upper factor of the
+     *   Doolittle factorisation Q^T = L U (the lower-triangular choice of
+     *   Sec. 4.2's first paragraph, which makes the stiff-limit sweep matrix
+     *   I - q^Delta^{-1} Q = I - L^T nilpotent).
+     * The explicit weights stay forward Euler (dtau_{j+1}). */
+    SDC_OPT_SERIAL_IMPLICIT = 3
 } sdc_option;
 enum {
     SDC_QDELTA_CLAMPED = 0,
@@ -113,6 +123,7 @@ enum {
     SDC_QDELTA_MIN_SR_S = 4
 };
 enum { SDC_METHOD_DSDC = 0, SDC_METHOD_SERIAL_SDC = 1, SDC_METHOD_IMEX2 = 2 };
+enum { SDC_SERIAL_IMPLICIT_EULER = 0, SDC_SERIAL_IMPLICIT_LU = 1 };
 
 /* Create a solver for truncation T on an nlat x nlon Gauss grid with M
  * Radau-right collocation nodes (tau_M = 1, Sec. 4.2), K sweeps per step

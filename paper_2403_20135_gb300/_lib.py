@@ -15,6 +15,8 @@ LIB_PATH = os.path.join(_HERE, "lib", "libsdc_swe.so")
 SDC_FP64, SDC_MIXED_FP32, SDC_MIXED_BF16X3, SDC_MIXED_BF16X6 = 0, 1, 2, 3
 SDC_OK, SDC_EINVAL, SDC_ENOMEM, SDC_ECUDA, SDC_EDIVERGED, SDC_ESTATE, SDC_EUNSUPPORTED = range(7)
 SDC_OPT_QDELTA_RULE = 1
+SDC_OPT_SERIAL_IMPLICIT = 3
+SDC_SERIAL_IMPLICIT_EULER, SDC_SERIAL_IMPLICIT_LU = 0, 1
 SDC_OPT_METHOD = 2
 SDC_QDELTA_CLAMPED, SDC_QDELTA_LITERAL, SDC_QDELTA_MIN_SR_NS, SDC_QDELTA_IMPLICIT_EULER, SDC_QDELTA_MIN_SR_S = range(5)
 SDC_METHOD_DSDC, SDC_METHOD_SERIAL_SDC, SDC_METHOD_IMEX2 = 0, 1, 2

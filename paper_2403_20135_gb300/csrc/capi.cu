@@ -47,6 +47,8 @@ struct sdc_ctx {
     int precision = SDC_FP64;
     int qdelta_rule = SDC_QDELTA_CLAMPED;
     int method = SDC_METHOD_DSDC;
+    int serial_implicit = SDC_SERIAL_IMPLICIT_EULER;
+    std::vector<double> qi_lu;           // LU implicit weights of serial SDC, row-major M x M
     double dt = 0.0;
     sdc_phys phys{};
     Dims d{};
@@ -220,7 +222,8 @@ cudaError_t enqueue_serial(sdc_ctx *c, cudaStream_t s, int *launches, StageTimer
     p.ncoef = c->d.ncoef;
     p.dt = c->dt;
     p.phibar = c->phys.gravity * c->phys.mean_depth;
-    for (int j = 0; j < M; ++j) p.dtau[j] = c->tau[j] - (j > 0 ? c->tau[j - 1] : 0.0);
+    std::vector<double> dtau(M);
+    for (int j = 0; j < M; ++j) dtau[j] = c->tau[j] - (j > 0 ? c->tau[j - 1] : 0.0);
     double2 *su[2] = {c->U, c->alt}, *sv[2] = {c->E, c->alt + M * se};
     for (int k = 0; k < K; ++k) {
         p.uk = k == 0 ? c->un : su[k % 2];
@@ -233,7 +236,12 @@ cudaError_t enqueue_serial(sdc_ctx *c, cudaStream_t s, int *launches, StageTimer
         for (int m = 0; m < M; ++m) {
             const bool final = (k == K - 1 && m == M - 1);
             p.m = m;
-            for (int j = 0; j < M; ++j) p.Q[j] = c->Q[m * M + j];
+            for (int j = 0; j < M; ++j) {
+                p.Q[j] = c->Q[m * M + j];
+                p.qe[j] = j < m ? dtau[j + 1] : 0.0;
+                p.qi[j] = j > m ? 0.0
+                                : (c->serial_implicit == SDC_SERIAL_IMPLICIT_LU ? c->qi_lu[m * M + j] : dtau[j]);
+            }
             p.out = final ? c->un : nu + m * se;
             if (timer) timer->mark(STAGE_SWEEP);
             e = launch_serial_node(p, M, s, launches);
@@ -829,6 +837,22 @@ int sdc_set_option(sdc_ctx *c, int key, int value) {
         if (value != c->method) {
             SDC_CUDA(cudaStreamSynchronize(c->stream));
             c->method = value;
+            for (auto &g : c->graph)
+                if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+        }
+        return SDC_OK;
+    }
+    if (key == SDC_OPT_SERIAL_IMPLICIT) {
+        if (value != SDC_SERIAL_IMPLICIT_EULER && value != SDC_SERIAL_IMPLICIT_LU)
+            return fail(SDC_EINVAL, "bad serial implicit weights");
+        if (value == SDC_SERIAL_IMPLICIT_LU && c->qi_lu.empty()) {
+            std::vector<double> qd;
+            if (!lu_implicit_weights(c->M, c->Q, qd)) return fail(SDC_EUNSUPPORTED, "Q^T has no LU factorisation");
+            c->qi_lu = qd;
+        }
+        if (value != c->serial_implicit) {
+            SDC_CUDA(cudaStreamSynchronize(c->stream));
+            c->serial_implicit = value;
             for (auto &g : c->graph)
                 if (g) { cudaGraphExecDestroy(g); g = nullptr; }
         }

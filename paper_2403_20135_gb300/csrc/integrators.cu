@@ -3,10 +3,12 @@
 //
 // Serial IMEX SDC, Algorithm 1 with Eq. (6), node m of sweep k+1:
 //   beta = u_n + dt sum_j q_{m,j} F_j^k
-//        + dt sum_{j<m} [dtau_{j+1} (E_j^{k+1} - E_j^k) + dtau_j L_g(u_j^{k+1} - u_j^k)]
-//        - dt dtau_m L_g u_m^k,
-//   (I - dt dtau_m L_g) u_m^{k+1} = beta  (Eq. (8), closed form as in the sweep),
-// with F_j = E_j + L_g u_j and dtau_1 = tau_1, dtau_j = tau_j - tau_{j-1}.
+//        + dt sum_{j<m} [qe_{m,j} (E_j^{k+1} - E_j^k) + qi_{m,j} L_g(u_j^{k+1} - u_j^k)]
+//        - dt qi_{m,m} L_g u_m^k,
+//   (I - dt qi_{m,m} L_g) u_m^{k+1} = beta  (Eq. (8), closed form as in the sweep),
+// with F_j = E_j + L_g u_j, explicit weights qe_{m,j} = dtau_{j+1} and implicit
+// weights qi_{m,j} = dtau_j (Eq. (6); dtau_1 = tau_1, dtau_j = tau_j - tau_{j-1})
+// or the rows of the LU choice (host table).
 //
 // IMEX-o2 (Sec. 3.2): Strang splitting, Crank-Nicolson half steps on L_g
 // around one Heun step on T_E:
@@ -78,7 +80,7 @@ __global__ void __launch_bounds__(kModeThreads) k4_serial_node(SerialNodeParams 
             load3(p.uk1 + j * p.k1stride, nc, i, u1);
             load3(p.ek1 + j * p.k1stride, nc, i, e1);
             lg(u1, phibar, lam, l1);
-            const double ce = dt * p.dtau[j + 1], ci = dt * p.dtau[j];
+            const double ce = dt * p.qe[j], ci = dt * p.qi[j];
 #pragma unroll
             for (int f = 0; f < 3; ++f) {
                 beta[f].x += ce * (e1[f].x - e[f].x) + ci * (l1[f].x - l[f].x);
@@ -86,7 +88,7 @@ __global__ void __launch_bounds__(kModeThreads) k4_serial_node(SerialNodeParams 
             }
         }
     }
-    const double alpha = dt * p.dtau[m];
+    const double alpha = dt * p.qi[m];
 #pragma unroll
     for (int f = 0; f < 3; ++f) {
         beta[f].x -= alpha * lum[f].x;

@@ -88,7 +88,8 @@ struct SerialNodeParams {
     double dt;
     double phibar;
     double Q[kMaxNodes];          // row m of the collocation matrix
-    double dtau[kMaxNodes];       // tau_1, tau_2 - tau_1, ...
+    double qe[kMaxNodes];         // row m of the explicit weights (j < m): dtau_{j+1}
+    double qi[kMaxNodes];         // row m of the implicit weights (j <= m)
 };
 
 // Per-kernel CUDA-event timing of a directly launched (not graph) step:
@@ -205,6 +206,8 @@ void gauss_legendre(int J, std::vector<double> &mu, std::vector<double> &w);
 void radau_right(int M, std::vector<double> &tau, std::vector<double> &Q);
 // MIN-SR-S diagonal (increasing root of the stiff-limit nilpotency conditions); false if not reached
 bool min_sr_s_diagonal(int M, const std::vector<double> &tau, const std::vector<double> &Q, std::vector<double> &d);
+// Q_Delta = U^T of the Doolittle factorisation Q^T = L U (row-major M x M); false on a zero pivot
+bool lu_implicit_weights(int M, const std::vector<double> &Q, std::vector<double> &qd);
 // Pbar_n^m(mu_j) for the northern latitudes j < J2, extended packing, rows
 // padded to J2p: table[(ext_offset(m) + n - m) * J2p + j].
 void legendre_table(int T, int J2, int J2p, const std::vector<double> &mu, std::vector<double> &table);

@@ -251,6 +251,32 @@ bool min_sr_s_diagonal(int M, const std::vector<double> &tau, const std::vector<
     return worst < 1e-9;
 }
 
+// Implicit weights of the LU trick for serial SDC: Q^T = L U with L unit
+// lower triangular (Doolittle, no pivoting), q^Delta = U^T (lower triangular).
+bool lu_implicit_weights(int M, const std::vector<double> &Q, std::vector<double> &qd) {
+    std::vector<double> A(M * M), U(M * M, 0.0), L(M * M, 0.0);
+    for (int r = 0; r < M; ++r)
+        for (int c = 0; c < M; ++c) A[r * M + c] = Q[c * M + r];   // Q^T
+    for (int i = 0; i < M; ++i) {
+        for (int k = i; k < M; ++k) {
+            double s = A[i * M + k];
+            for (int j = 0; j < i; ++j) s -= L[i * M + j] * U[j * M + k];
+            U[i * M + k] = s;
+        }
+        if (U[i * M + i] == 0.0) return false;
+        L[i * M + i] = 1.0;
+        for (int k = i + 1; k < M; ++k) {
+            double s = A[k * M + i];
+            for (int j = 0; j < i; ++j) s -= L[k * M + j] * U[j * M + i];
+            L[k * M + i] = s / U[i * M + i];
+        }
+    }
+    qd.assign(M * M, 0.0);
+    for (int r = 0; r < M; ++r)
+        for (int c = 0; c <= r; ++c) qd[r * M + c] = U[c * M + r];
+    return true;
+}
+
 // Normalised associated Legendre functions (unit L2 norm on [-1, 1], no
 // Condon-Shortley phase) at the northern Gauss latitudes, degrees m..T+1.
 // Pbar_0^0 = 1/sqrt(2), Pbar_m^m = sqrt((2m+1)/(2m)) sqrt(1-mu^2) Pbar_{m-1}^{m-1},

@@ -54,6 +54,10 @@ class Solver:
         _lib.check(self.lib.sdc_set_option(self.h, _lib.SDC_OPT_METHOD, method), "sdc_set_option")
         self.method = method
 
+    def set_serial_implicit(self, weights: int):
+        """Implicit weights of serial IMEX SDC: SDC_SERIAL_IMPLICIT_EULER or SDC_SERIAL_IMPLICIT_LU."""
+        _lib.check(self.lib.sdc_set_option(self.h, _lib.SDC_OPT_SERIAL_IMPLICIT, weights), "sdc_set_option")
+
     @classmethod
     def for_workload(cls, wl, precision: int = _lib.SDC_FP64, **kw):
         import swe_inputs as si

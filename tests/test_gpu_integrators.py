@@ -43,6 +43,23 @@ def test_serial_sdc_matches_oracle(T, J, L, M, K):
     assert s.launches_per_step() == 5 * K * M          # E0 + K M node kernels + (K M - 1) tendencies
 
 
+@pytest.mark.parametrize("M,K", [(3, 3), (4, 5)])
+def test_serial_sdc_lu_weights_match_oracle(M, K):
+    """Serial IMEX SDC with the LU implicit weights (SDC_OPT_SERIAL_IMPLICIT)
+    against the oracle, and the two weight choices give different steps."""
+    from paper_2403_20135_gb300 import SDC_METHOD_SERIAL_SDC, SDC_SERIAL_IMPLICIT_EULER, SDC_SERIAL_IMPLICIT_LU
+    T, J, L = 21, 34, 72
+    o, u, s = _setup(T, J, L, M, K, 600.0, SDC_METHOD_SERIAL_SDC)
+    s.set_serial_implicit(SDC_SERIAL_IMPLICIT_LU)
+    ref = oi.swe_imex_sdc_run(o, u, osdc.Collocation(M), K, 600.0, 2, implicit="lu")
+    got = to_numpy(s.run(_cuda(u), 2))
+    s.sync()
+    assert np.all(rel_l2(got, ref) <= TOL), rel_l2(got, ref)
+    s.set_serial_implicit(SDC_SERIAL_IMPLICIT_EULER)
+    euler = to_numpy(s.run(_cuda(u), 2))
+    assert np.any(rel_l2(euler, got) > 1e-9)
+
+
 @pytest.mark.parametrize("T,J,L", [(21, 34, 72), (31, 48, 96)])
 def test_imex2_matches_oracle(T, J, L):
     from paper_2403_20135_gb300 import SDC_METHOD_IMEX2

@@ -52,8 +52,9 @@ def test_first_serial_sweep_is_imex_euler_over_the_nodes(M):
     np.testing.assert_allclose(got, x, rtol=1e-13, atol=1e-14)
 
 
+@pytest.mark.parametrize("implicit", ["euler", "lu"])
 @pytest.mark.parametrize("M", [2, 3, 4])
-def test_serial_sweeps_converge_to_collocation(M):
+def test_serial_sweeps_converge_to_collocation(M, implicit):
     n = 4
     A, B = _linear(n, 10 + M)
     coll = sdc.Collocation(M)
@@ -62,8 +63,29 @@ def test_serial_sweeps_converge_to_collocation(M):
     # collocation system U = 1 (x) u_n + dt (Q (x) (A + B)) U
     big = np.eye(M * n) - dt * np.kron(coll.Q, A + B)
     U = np.linalg.solve(big, np.tile(u_n, M))
-    got = oi.imex_sdc_step(u_n, lambda x: B @ x, lambda x: A @ x, _solver(A), coll, 60, dt)
+    got = oi.imex_sdc_step(u_n, lambda x: B @ x, lambda x: A @ x, _solver(A), coll, 60, dt, implicit)
     np.testing.assert_allclose(got, U[-n:], rtol=1e-12, atol=1e-13)
+
+
+def test_lu_weights_two_nodes_closed_form():
+    """M = 2 (tau = 1/3, 1; Q = [[5/12, -1/12], [3/4, 1/4]]): Q^T = L U with
+    L = [[1, 0], [-1/5, 1]], U = [[5/12, 3/4], [0, 2/5]], so the implicit weights
+    are U^T = [[5/12, 0], [3/4, 2/5]]."""
+    np.testing.assert_allclose(oi.lu_weights(sdc.Collocation(2).Q), [[5 / 12, 0.0], [3 / 4, 2 / 5]], atol=1e-15)
+
+
+@pytest.mark.parametrize("M", [3, 4, 8])
+def test_lu_weights_make_the_stiff_limit_nilpotent(M):
+    """With q^Delta = U^T, q^Delta^{-1} Q = L^T is unit upper triangular, so the
+    stiff-limit sweep matrix I - q^Delta^{-1} Q is strictly upper triangular
+    (checked by a generic solve) and its M-th power vanishes; q^Delta is lower
+    triangular."""
+    Q = sdc.Collocation(M).Q
+    Qd = oi.lu_weights(Q)
+    assert np.all(np.triu(Qd, 1) == 0.0)
+    K = np.eye(M) - np.linalg.solve(Qd, Q)
+    assert np.abs(np.tril(K)).max() < 1e-13
+    assert np.abs(np.linalg.matrix_power(K, M)).max() < 1e-14
 
 
 def _nonlinear_problem():
@@ -88,10 +110,11 @@ def _observed_order(step, nsteps_list):
     return np.log2(errs[0] / errs[1])
 
 
+@pytest.mark.parametrize("implicit", ["euler", "lu"])
 @pytest.mark.parametrize("K,order", [(1, 1), (2, 2), (3, 3)])
-def test_serial_sdc_order(K, order):
+def test_serial_sdc_order(K, order, implicit):
     coll = sdc.Collocation(3)
-    p = _observed_order(lambda x, fe, fi, so, dt: oi.imex_sdc_step(x, fe, fi, so, coll, K, dt), [16, 32])
+    p = _observed_order(lambda x, fe, fi, so, dt: oi.imex_sdc_step(x, fe, fi, so, coll, K, dt, implicit), [16, 32])
     assert abs(p - order) < 0.3, p
 
 
