@@ -749,16 +749,16 @@ int sdc_create(sdc_ctx **out, int T, int J, int L, int M, int K, double dt, cons
         for (int m = 0; m <= T; ++m)
             for (int n = m; n <= T; ++n) {
                 const size_t i = static_cast<size_t>(order_offset(T, m) + n - m);
-                const int e = ext_offset(T, m) + n - m;
-                e32[4 * i + 0] = float(n * eps[e + 1]);
-                e32[4 * i + 1] = float(n > m ? (n + 1.0) * eps[e] : 0.0);
+                const int x = ext_offset(T, m) + n - m;
+                e32[4 * i + 0] = float(n * eps[x + 1]);
+                e32[4 * i + 1] = float(n > m ? (n + 1.0) * eps[x] : 0.0);
                 e32[4 * i + 2] = float(lam[i]);
                 e32[4 * i + 3] = 0.f;
             }
         SDC_TRY(upload(&c->epi32, e32.data(), e32.size()));
         std::vector<float> s32(4 * static_cast<size_t>(d.next));
-        for (size_t e = 0; e < static_cast<size_t>(d.next); ++e)
-            for (int k = 0; k < 3; ++k) s32[4 * e + k] = float(syn[3 * e + k]);
+        for (size_t r = 0; r < static_cast<size_t>(d.next); ++r)
+            for (int k = 0; k < 3; ++k) s32[4 * r + k] = float(syn[3 * r + k]);
         SDC_TRY(upload(&c->syn32, s32.data(), s32.size()));
     }
     SDC_TRY(upload(&c->w2, c->w.data(), d.J2));
