@@ -80,11 +80,13 @@ def epsilon(n, m):
     return np.sqrt((n * n - m * m) / (4.0 * n * n - 1.0))
 
 
-def legendre_pbar(T: int, mu: np.ndarray, nmax_extra: int = 1):
+def legendre_pbar(T: int, mu: np.ndarray, nmax_extra: int = 1, orders=None):
     """Pbar[m] = array (len(mu), T + 1 + nmax_extra - m) of Pbar_n^m(mu), n = m..T+nmax_extra.
 
     Pbar_0^0 = 1/sqrt(2); Pbar_m^m = sqrt((2m+1)/(2m)) sqrt(1-mu^2) Pbar_{m-1}^{m-1};
     Pbar_n^m = (mu Pbar_{n-1}^m - eps_{n-1}^m Pbar_{n-2}^m) / eps_n^m.
+    With ``orders`` given, only those orders' columns are formed (the others
+    are None); the sectoral start still runs through every m.
     """
     mu = np.asarray(mu, dtype=np.float64)
     s = np.sqrt((1.0 - mu) * (1.0 + mu))          # sqrt(1 - mu^2) without cancellation near the poles
@@ -94,6 +96,9 @@ def legendre_pbar(T: int, mu: np.ndarray, nmax_extra: int = 1):
     for m in range(T + 1):
         if m > 0:
             pmm = np.sqrt((2.0 * m + 1.0) / (2.0 * m)) * s * pmm
+        if orders is not None and m not in orders:
+            out.append(None)
+            continue
         col = np.zeros(mu.shape + (nmax + 1 - m,))
         col[..., 0] = pmm
         for n in range(m + 1, nmax + 1):
