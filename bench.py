@@ -37,14 +37,27 @@ import swe_inputs as si  # noqa: E402
 METRIC = "SDC steps/s at T255 M=4 K=5: FP64 vs mixed at fixed error; adjoint/fwd ratio"
 WORKLOAD = "t255"
 L2_FLUSH_BYTES = 512 << 20          # > 129 MB L2
-FP64_NOMINAL_TFLOPS = 1.25          # GB300 dense FP64 (nominal; no measured FP64 peak)
+FP64_NOMINAL_TFLOPS = 1.25          # GB300 dense FP64: 152 SMs x 4 flops/clock x 2.07 GHz (nominal)
 # FP32 SIMT: 152 SMs x 128 FMA lanes x 2 flops x 2.07 GHz (maximum SM clock)
 FP32_SIMT_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-# DRAM bytes (read + write) of one captured launch of the FP64 ring kernel with
-# a batch of 4 states at the bench workload (ncu capture summarised in
-# profiles/kernels_t255_fp64.md); the traffic is the batch's F1 input, so a
-# launch of b states moves b/4 of it.
+# DRAM bytes (read + write) of one launch of the FP64 ring kernel with a batch
+# of 4 states at the T255 workload, from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum), and the SHA-256 prefix of
+# the kernel's sources at that capture.  The traffic is the batch's F1 input,
+# so a launch of b states moves b/4 of it.  When the sources differ the
+# counters no longer describe the kernel and the bench reports null.
 RING_FP64_TRAFFIC_B4 = 25.291264e6 + 228.096e3
+RING_FP64_SOURCES = ("paper_2403_20135_gb300/csrc/transforms.cu", "paper_2403_20135_gb300/csrc/fft.cuh")
+RING_FP64_SOURCES_SHA = None
+
+
+def _sources_sha(paths) -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for p in paths:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 def _peaks():
@@ -57,7 +70,7 @@ def _peaks():
 
 
 # ---------------------------------------------------------------------------
-# algorithmic work per launch (units stated in the design notes)
+# algorithmic work per launch: flops per node evaluation times the batch
 # ---------------------------------------------------------------------------
 def stage_flops(wl, stage: str, batch: int) -> float:
     T, J2, L = wl.T, wl.nlat // 2, wl.nlon
@@ -168,6 +181,56 @@ def oracle_steps_per_s(wl, budget_s: float, max_steps: int):
     return n / el, n, el
 
 
+def oracle_steps_per_s_single_thread(key: str, budget_s: float, max_steps: int):
+    """oracle_steps_per_s in a fresh interpreter with every BLAS/OpenMP pool
+    pinned to one thread (the pools size themselves at import)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = ("import json, sys; sys.path.insert(0, %r); import bench, swe_inputs as si; "
+            "print(json.dumps(bench.oracle_steps_per_s(si.WORKLOADS[%r], %r, %r)))" % (ROOT, key, budget_s, max_steps))
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                       timeout=4 * budget_s + 300)
+    if r.returncode != 0:
+        raise RuntimeError(f"single-thread oracle run failed: {r.stderr[-2000:]}")
+    v, n, el = json.loads(r.stdout.strip().splitlines()[-1])
+    return v, n, el
+
+
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the platform string)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def cpu_baseline_entry(key: str, budget_s: float, max_steps: int) -> dict:
+    """The oracle timed on the host cores twice: every pool pinned to one
+    thread, and with the default pools (all cores the process may use)."""
+    wl = si.WORKLOADS[key]
+    v1, n1, el1 = oracle_steps_per_s_single_thread(key, budget_s, max_steps)
+    va, na, ela = oracle_steps_per_s(wl, budget_s=budget_s, max_steps=max_steps)
+    cores = host_cores()
+    return {"value": va, "unit": "steps/s", "cores": cores, "kind": "oracle", "cpu_model": cpu_model(),
+            "sample": f"{na} full T{wl.T} dSDC steps of the seeded state ({ela:.1f} s, numpy FP64, default "
+                      f"thread pools over {cores} cores)",
+            "single_thread": {"value": v1, "unit": "steps/s", "threads": 1,
+                              "sample": f"{n1} full steps ({el1:.1f} s), BLAS/OpenMP pinned to 1 thread"},
+            "all_cores": {"value": va, "unit": "steps/s", "threads": cores,
+                          "sample": f"{na} full steps ({ela:.1f} s)"}}
+
+
 def host_cores() -> int:
     try:
         return len(os.sched_getaffinity(0))
@@ -189,7 +252,8 @@ def reference_arm(args, rank: int, world: int):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": wl.describe(), "parallelism": "host cores"},
         "cpu_baseline": {"value": v, "unit": "steps/s", "cores": host_cores(), "kind": "oracle",
-                         "sample": f"{n} full T255 dSDC steps (of {args.steps} requested)"},
+                         "cpu_model": cpu_model(),
+                         "sample": f"{n} full T255 dSDC steps (of {args.steps} requested), default thread pools"},
         "e2e": {"value": v, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -303,6 +367,7 @@ def cuda_arm(args, rank: int, world: int):
     import torch.distributed as dist
 
     from paper_2403_20135_gb300 import SDC_FP64, SDC_MIXED_BF16X3, SDC_MIXED_BF16X6, SDC_MIXED_FP32, Solver
+    from paper_2403_20135_gb300.solver import fp64_fma_rate
 
     dev = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev)
@@ -336,24 +401,29 @@ def cuda_arm(args, rank: int, world: int):
     launches_per_step = prof[dom]["launches_per_step"]
     flops_per_launch = stage_flops(wl, dom, nodes_per_step) / launches_per_step
     achieved_tf = flops_per_launch / (prof[dom]["ms_per_launch"] * 1e-3) / 1e12
-    traffic = RING_FP64_TRAFFIC_B4 * (nodes_per_step / launches_per_step) / 4.0 if dom == "ring" else None
-    roofline = {"bound": "alu", "achieved": achieved_tf, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved_tf / FP64_NOMINAL_TFLOPS, "traffic": traffic, "kernel": dom,
-                "peak_kind": "nominal FP64 (no measured FP64 peak)"}
+    traffic = None
+    if dom == "ring" and RING_FP64_SOURCES_SHA == _sources_sha(RING_FP64_SOURCES):
+        traffic = RING_FP64_TRAFFIC_B4 * (nodes_per_step / launches_per_step) / 4.0
+    fp64_peak = fp64_fma_rate()
+    roofline = {"bound": "alu", "achieved": achieved_tf, "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": achieved_tf / fp64_peak, "traffic": traffic, "kernel": dom,
+                "peak_kind": "measured FP64 FMA rate of this GPU (sdc_fp64_fma_rate, same run)",
+                "peak_nominal": FP64_NOMINAL_TFLOPS, "frac_of_nominal": achieved_tf / FP64_NOMINAL_TFLOPS}
     # the whole step: algorithmic flops of every stage over the step time
     step_flops = sum(stage_flops(wl, k, nodes_per_step) for k in ("synthesis", "ring", "analysis"))
     step_flops += (sweep_flops(wl, 1, M) + (K - 2) * sweep_flops(wl, M, M) + sweep_flops(wl, M, 1))
     step_tf = step_flops / (total_ms / args.steps * 1e-3) / 1e12
-    roofline_step = {"bound": "alu", "achieved": step_tf, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
-                     "frac": step_tf / FP64_NOMINAL_TFLOPS, "flops_per_step": step_flops}
+    roofline_step = {"bound": "alu", "achieved": step_tf, "peak": fp64_peak, "unit": "TFLOP/s",
+                     "frac": step_tf / fp64_peak, "frac_of_nominal": step_tf / FP64_NOMINAL_TFLOPS,
+                     "flops_per_step": step_flops}
     # the sweep kernel (FP64 in every mode): FP64 flops and the bytes it moves
     sw_ms = prof["sweep"]["ms_per_launch"]
     # K sweeps per step: the first reads the projections of one state, the
     # others of M; sweeps 1..K-1 update all M nodes, the last one node
     sw_bytes = (sweep_bytes(wl, True, 1) + (K - 2) * sweep_bytes(wl, True, M) + sweep_bytes(wl, False, M)) / K
     sw_flops = (sweep_flops(wl, 1, M) + (K - 2) * sweep_flops(wl, M, M) + sweep_flops(wl, M, 1)) / K
-    roofline_sweep = {"bound": "alu", "achieved": sw_flops / (sw_ms * 1e-3) / 1e12, "peak": FP64_NOMINAL_TFLOPS,
-                      "unit": "TFLOP/s", "frac": sw_flops / (sw_ms * 1e-3) / 1e12 / FP64_NOMINAL_TFLOPS,
+    roofline_sweep = {"bound": "alu", "achieved": sw_flops / (sw_ms * 1e-3) / 1e12, "peak": fp64_peak,
+                      "unit": "TFLOP/s", "frac": sw_flops / (sw_ms * 1e-3) / 1e12 / fp64_peak,
                       "hbm_gbs": sw_bytes / (sw_ms * 1e-3) / 1e9, "hbm_peak_gbs": peaks["hbm_gbs"],
                       "hbm_frac": sw_bytes / (sw_ms * 1e-3) / 1e9 / peaks["hbm_gbs"], "kernel": "sweep"}
 
@@ -425,11 +495,13 @@ def cuda_arm(args, rank: int, world: int):
                    "t127_differentiation": time_adjoint(Solver, si.WORKLOADS["t127adj"], 96, 8, 10),
                    "t255_fp32": time_adjoint(Solver, wl, 20, 8, 5, precision=PRECISIONS["fp32"])}
 
+    t511 = None
+    if not args.no_t511:
+        t511 = t511_leg(max(3, min(args.steps, 10)), args.t511_horizon, args.t511_adjoint_steps, flush)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, n, el = oracle_steps_per_s(wl, budget_s=args.cpu_budget, max_steps=50)
-        cpu = {"value": v, "unit": "steps/s", "cores": host_cores(), "kind": "oracle",
-               "sample": f"{n} full T255 dSDC steps of the seeded state ({el:.1f} s, numpy FP64)"}
+        cpu = cpu_baseline_entry(WORKLOAD, args.cpu_budget, 50)
 
     if rank == 0:
         line = {
@@ -443,6 +515,7 @@ def cuda_arm(args, rank: int, world: int):
             "roofline_sweep": roofline_sweep, "roofline_step": roofline_step,
             "stages": prof, "mixed": mixed,
             "adjoint_fwd_ratio": adjoint["t255"]["step_ratio"] if adjoint else None, "adjoint": adjoint,
+            "t511": t511,
             "cpu_baseline": cpu,
             "peaks_source": peak_kind,
         }
@@ -451,6 +524,91 @@ def cuda_arm(args, rank: int, world: int):
 
 
 PRECISIONS = {"fp64": 0, "fp32": 1, "bf16x3": 2, "bf16x6": 3}
+
+
+def t511_leg(steps: int, horizon: int, adj_steps: int, flush):
+    """The largest combined form: T511 on 768 x 1536, M = 4, K = 5, dt = 75 s.
+    Forward steps/s in every precision (CUDA events, L2 flushed before each
+    step), per-field error of each mixed mode against the FP64 GPU path after
+    `horizon` steps, the reversed-step/forward-step cost in FP64 and FP32 mode,
+    the checkpointed gradient run over `adj_steps` steps with 16 snapshots in
+    FP32 mode (the mixed form), and device memory: the library's own
+    allocations (free-memory drop from before create) and torch's peak."""
+    import torch
+    from paper_2403_20135_gb300 import Solver
+    wl = si.WORKLOADS["t511"]
+    torch.cuda.synchronize()
+    torch.cuda.reset_peak_memory_stats()
+    free0 = torch.cuda.mem_get_info()[0]
+    fields = ("phi", "zeta", "div")
+    out = {"workload": wl.describe().replace(f"{wl.nsteps} steps", f"{horizon}-step horizon")}
+    s64 = Solver.for_workload(wl, precision=0)
+    u0 = s64.initial_state(wl)
+    ref = u0.clone()
+    s64.run(ref, horizon)
+    s64.sync()
+
+    def rate(s):
+        x = u0.clone()
+        s.run(x, 2)
+        tm = time_device(s, x, steps, flush)
+        return steps / (sum(tm) * 1e-3), sum(tm) / steps
+
+    v64, ms64 = rate(s64)
+    out["fp64"] = {"value": v64, "unit": "steps/s", "ms_per_step": ms64}
+    min_free = torch.cuda.mem_get_info()[0]
+    for name in ("fp32", "bf16x3", "bf16x6"):
+        sm = Solver.for_workload(wl, precision=PRECISIONS[name])
+        v, ms = rate(sm)
+        x = u0.clone()
+        sm.run(x, horizon)
+        sm.sync()
+        err = ((x - ref).abs().pow(2).sum(1) / ref.abs().pow(2).sum(1)).sqrt().cpu().numpy()
+        out[name] = {"value": v, "unit": "steps/s", "ms_per_step": ms, "speedup_vs_fp64": v / v64,
+                     "rel_l2_vs_fp64_gpu": dict(zip(fields, map(float, err)))}
+        min_free = min(min_free, torch.cuda.mem_get_info()[0])
+        sm.close()
+    # reversed step against forward step, FP64 and FP32 mode
+    for name, prec in (("fp64", 0), ("fp32", 1)):
+        s = s64 if prec == 0 else Solver.for_workload(wl, precision=prec)
+        ub = torch.ones_like(u0)
+        x = u0.clone()
+        s.run(x, 1)
+        s.step_adjoint(u0, ub)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        torch.cuda.synchronize()
+        ev[0].record()
+        for _ in range(3):
+            s.run(x, 1)
+        ev[1].record()
+        for _ in range(3):
+            s.step_adjoint(u0, ub)
+        ev[2].record()
+        torch.cuda.synchronize()
+        out[name]["adjoint_step_ratio"] = ev[1].elapsed_time(ev[2]) / ev[0].elapsed_time(ev[1])
+        min_free = min(min_free, torch.cuda.mem_get_info()[0])
+        if prec != 0:
+            # the checkpointed gradient run of the mixed form
+            target = si.MEAN_DEPTH + s.spec_to_grid(u0[0].contiguous()) / si.GRAVITY
+            x = u0.clone()
+            ev[0].record()
+            s.run(x, adj_steps)
+            ev[1].record()
+            loss, g = s.adjoint_run(u0, adj_steps, target, 16)
+            ev[2].record()
+            torch.cuda.synchronize()
+            out["fp32"]["adjoint_run"] = {"steps": adj_steps, "snapshots": 16,
+                                          "fwd_ms": ev[0].elapsed_time(ev[1]), "adjoint_ms": ev[1].elapsed_time(ev[2]),
+                                          "ratio": ev[1].elapsed_time(ev[2]) / ev[0].elapsed_time(ev[1]),
+                                          "finite": bool(torch.isfinite(g).all().item())}
+            min_free = min(min_free, torch.cuda.mem_get_info()[0])
+            s.close()
+    s64.close()
+    out["device_memory"] = {"library_and_torch_peak_bytes": int(free0 - min_free),
+                            "torch_max_allocated_bytes": int(torch.cuda.max_memory_allocated()),
+                            "note": "free-memory drop from before the first create to its minimum over the leg "
+                                    "(sampled between calls); one FP64 and one mixed context alive at a time"}
+    return out
 
 
 def work_precision(hours: float):
@@ -536,6 +694,9 @@ def main():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--no-t511", action="store_true", help="skip the T511 leg")
+    ap.add_argument("--t511-horizon", type=int, default=400, help="steps of the T511 error comparison")
+    ap.add_argument("--t511-adjoint-steps", type=int, default=400, help="steps of the T511 gradient run")
     ap.add_argument("--horizon", type=int, default=500, help="steps of the fixed-error comparison")
     ap.add_argument("--profile-run", choices=sorted(PRECISIONS), default=None,
                     help="only run --steps untimed steps of this precision (for profilers)")

@@ -264,6 +264,18 @@ int sdc_sync(sdc_ctx *ctx);
  * batch (K per step) plus one sweep kernel per sweep. */
 int sdc_launches_per_step(const sdc_ctx *ctx, int *launches);
 
+/* FP64 fused multiply-add rate of the current device, measured: `repeats`
+ * timed launches (after one warm-up launch) of blocks that fill every SM,
+ * each thread running 8 independent FMA chains of `iters` steps; HOST output
+ * *tflops in TFLOP/s, an FMA counting two flops.  The paper has no
+ * counterpart: it is the peak the FP64 transform kernels are reported
+ * against.  sink is a DEVICE double the kernel never writes for these
+ * inputs (it keeps the chains from being optimised away).  Synchronises
+ * cuda_stream (a cudaStream_t, NULL = legacy default); changes no GPU
+ * setting.  SDC_EINVAL for NULL pointers or iters, repeats < 1, SDC_ECUDA if
+ * a CUDA call fails; sdc_last_error() is not updated. */
+int sdc_fp64_fma_rate(int iters, int repeats, void *cuda_stream, double *sink, double *tflops);
+
 /* Spectral-to-grid transform of one field that allocates nothing and needs no
  * context.  The paper has no counterpart: this serves callers that cannot call
  * cudaMalloc -- host applications that own all device memory through their

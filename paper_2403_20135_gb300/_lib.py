@@ -61,6 +61,7 @@ SIGNATURES = {
     "sdc_sync": (_I, [_P]),
     "sdc_profile_step": (_I, [_P, _P, ctypes.POINTER(_D), ctypes.POINTER(_I)]),
     "sdc_spec_to_grid_static": (_I, [_I, _I, _I, _P, _P, _P]),
+    "sdc_fp64_fma_rate": (_I, [_I, _I, _P, _P, ctypes.POINTER(_D)]),
     "sdc_strerror": (ctypes.c_char_p, [_I]),
     "sdc_last_error": (ctypes.c_char_p, []),
 }

@@ -232,3 +232,13 @@ class Solver:
         u[1] = torch.from_numpy(zeta).to("cuda")
         u[2] = torch.from_numpy(div).to("cuda")
         return u
+
+
+def fp64_fma_rate(iters: int = 4096, repeats: int = 5) -> float:
+    """Measured FP64 FMA rate of the current device in TFLOP/s (sdc_fp64_fma_rate)."""
+    lib = _lib.load()
+    sink = torch.zeros(1, dtype=torch.float64, device="cuda")
+    out = ctypes.c_double()
+    stream = torch.cuda.current_stream().cuda_stream
+    _lib.check(lib.sdc_fp64_fma_rate(iters, repeats, stream, _ptr(sink), ctypes.byref(out)), "sdc_fp64_fma_rate")
+    return out.value

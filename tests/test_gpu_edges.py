@@ -10,12 +10,12 @@ from oracle import adjoint as oadj
 from oracle import sdc as osdc
 from oracle import sht, swe
 from tests.helpers import rel_l2, to_numpy
+from tests.test_gpu_mixed import bound
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 TOL_EVAL = 1e-12
-MIXED = {1: 6e-6, 3: 6e-6}                  # FP32 / BF16x6 per-tendency bound at T21 (see test_gpu_mixed)
 
 
 def _solver(T, J, L, M=3, K=3, dt=600.0, precision=0):
@@ -45,7 +45,7 @@ def test_smallest_truncations(T, J, L):
         sm = _solver(T, J, L, precision=prec)
         err = rel_l2(to_numpy(sm.tendency(_cuda(u))), ref)
         sm.sync()
-        assert np.all(err <= MIXED[prec]), (prec, err)
+        assert np.all(err <= bound(prec, T, J, L)), (prec, err)
 
 
 def test_longest_rings():
@@ -58,7 +58,7 @@ def test_longest_rings():
     assert e.value.status == 6
     for prec in (1, 3):
         err = rel_l2(to_numpy(_solver(T, J, 2304, precision=prec).tendency(_cuda(u))), ref)
-        assert np.all(err <= MIXED[prec]), (prec, err)
+        assert np.all(err <= bound(prec, T, J, 2304)), (prec, err)
     o2, u2 = _state(T, J, 2048)
     assert np.all(rel_l2(to_numpy(_solver(T, J, 2048).tendency(_cuda(u2))), o2.explicit(u2)) <= TOL_EVAL)
 
@@ -70,7 +70,7 @@ def test_most_latitudes():
     assert np.all(rel_l2(to_numpy(_solver(T, J, L).tendency(_cuda(u))), ref) <= TOL_EVAL)
     for prec in (1, 3):
         err = rel_l2(to_numpy(_solver(T, J, L, precision=prec).tendency(_cuda(u))), ref)
-        assert np.all(err <= 2 * MIXED[prec]), (prec, err)
+        assert np.all(err <= bound(prec, T, J, L)), (prec, err)
 
 
 def test_eight_nodes_step_adjoint():
