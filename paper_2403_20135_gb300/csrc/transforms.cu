@@ -1164,7 +1164,7 @@ static cudaError_t launch_tendency_t(const Dims &d, const FftPlan &plan, int B, 
     if (timer) timer->mark(STAGE_SYNTH);
     if constexpr (sizeof(R) == sizeof(float)) {
         if (tc) {
-            cudaError_t e = launch_tc_synthesis(*tc, d, B, states, sstride, tb.syn, tb.row_m, f1, s, launches);
+            cudaError_t e = launch_tc_synthesis(*tc, d, B, states, sstride, tb.syn, f1, s, launches);
             if (e != cudaSuccess) return e;
         } else if (synthesis_nb_fits(d, 2, 4)) {
             const cudaError_t e = launch_synthesis_nb<4>(d, B, states, sstride, nullptr, pbar, tb.syn32, f1, tb.err, s);

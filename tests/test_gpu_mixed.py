@@ -142,3 +142,20 @@ def test_mixed_adjoint_close_to_fp64_adjoint(precision):
     err = rel_l2(to_numpy(g), to_numpy(ref_g))
     print(f"precision {precision}: gradient rel L2 vs FP64 adjoint {err}")
     assert np.all(err <= 1e-5), err
+
+
+@pytest.mark.parametrize("precision", [2, 3])
+def test_tensor_core_eight_states(precision):
+    """The largest batch (eight node states: 80 projection and 64 synthesis
+    columns per tile) and odd latitude-pair counts (J2 = 17, 25)."""
+    for T, J, L in ((21, 34, 72), (31, 50, 96)):
+        o = swe.SWE(sht.Grid(T, J, L), swe.default_physics())
+        wl = si.Workload("m", 3, T, J, L, 8, 3, 300.0, 1, 1, (100.0, 100.0))
+        u = swe.initial_state(wl, o)
+        facs = np.linspace(0.5, 2.0, 8)
+        s = _solver(T, J, L, 8, 3, 300.0, precision)
+        got = to_numpy(s.tendency(_cuda(np.stack([f * u for f in facs]))))
+        s.sync()
+        for b, f in enumerate(facs):
+            err = rel_l2(got[b], o.explicit(f * u))
+            assert np.all(err <= bound(precision, T, J, L)), (T, b, err)
