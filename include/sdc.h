@@ -227,8 +227,11 @@ int sdc_collocation(const sdc_ctx *ctx, double *tau, double *Q);
  * and returns its step index through `step` (may be NULL).  state: device
  * memory of 3 * ncoef double2, owned by the caller.  Both synchronise the
  * context's stream.  SDC_EINVAL for NULL arguments, a file that cannot be
- * opened, written or read, a header of another format, truncation or size, or
- * a data section of the wrong length; SDC_ECUDA if a copy fails. */
+ * opened, written or read, a header of another format, truncation or size, a
+ * header whose grid, nodes, sweeps, dt or physical constants differ from the
+ * context's (compared exactly: the step index is a model time only under the
+ * same configuration), or a data section of the wrong length; SDC_ECUDA if a
+ * copy fails. */
 int sdc_save(sdc_ctx *ctx, const void *state, long long step, const char *path);
 int sdc_load(sdc_ctx *ctx, void *state, long long *step, const char *path);
 
@@ -290,10 +293,15 @@ int sdc_fp64_fma_rate(int iters, int repeats, void *cuda_stream, double *sink, d
  * until exit: the call is rejected with SDC_EUNSUPPORTED unless
  * (nlat/2)*2*(T+1) + ceil(nlat/4) <= 131072 complex doubles (T255 on 384
  * latitudes fits; T511 on 768 does not).  SDC_EINVAL for NULL pointers or
- * invalid sizes, SDC_ECUDA if a CUDA call fails; sdc_last_error() is not
+ * invalid sizes, SDC_ECUDA if a CUDA call fails or if a CUDA error from
+ * earlier work is already pending on the calling thread (it is then left
+ * pending for its owner and nothing is launched); sdc_last_error() is not
  * updated.  The first call on each device does a one-time set-up on the
  * current device (looks up the array's device address, raises a kernel's
- * shared-memory limit); make that first call before any stream capture.
+ * shared-memory limit); make that first call before any stream capture.  The
+ * set-up is kept for the life of the process: after cudaDeviceReset() of a
+ * device the kept address may be stale, so do not call this function on that
+ * device again in the same process.
  * Every call shares the array: calls whose work overlaps on the GPU (several
  * streams or host threads) race and must be serialised by the caller.
  * Asynchronous on cuda_stream (a cudaStream_t, NULL = legacy default). */

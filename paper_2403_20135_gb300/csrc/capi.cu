@@ -86,8 +86,7 @@ struct sdc_ctx {
 
     // tensor-core Legendre tables (split-BF16 modes)
     TcTables tc{};
-    uint16_t *tc_a3 = nullptr, *tc_a1 = nullptr, *tc_wb = nullptr, *tc_cb = nullptr;
-    long long *tc_cboff = nullptr;
+    uint16_t *tc_a3 = nullptr, *tc_a1 = nullptr;
     TcTile3 *tc_t3 = nullptr;
     TcTile1 *tc_t1 = nullptr;
     int *tc_err = nullptr;
@@ -114,7 +113,7 @@ void free_ctx(sdc_ctx *c) {
                     c->tw32, c->twp32, c->un, c->U, c->E, c->E0, c->f1, c->f2, c->f3, c->resid_part, c->resid,
                     c->gstore, c->ub, c->eb, c->ubn, c->ubnext, c->eb0, c->snaps, c->phigrid, c->rgrid,
                     c->loss_part, c->loss_dev, c->tc_a3, c->tc_a1, c->tc_t3, c->tc_t1, c->tc_err, c->den,
-                    c->tc_wb, c->tc_cb, c->tc_cboff, c->alt};
+                    c->alt};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->cap) cudaStreamDestroy(c->cap);
@@ -620,6 +619,11 @@ int sdc_create(sdc_ctx **out, int T, int J, int L, int M, int K, double dt, cons
     d.inv_a = 1.0 / phys->radius;
     d.two_omega = 2.0 * phys->omega;
     if (!fft_plan(L, c->plan)) { free_ctx(c); return fail(SDC_EINVAL, "no FFT plan for nlon"); }
+    if ((precision == SDC_MIXED_BF16X3 || precision == SDC_MIXED_BF16X6) &&
+        !tc_fits(T, precision == SDC_MIXED_BF16X3 ? 2 : 3, M)) {
+        free_ctx(c);
+        return fail(SDC_EUNSUPPORTED, "tensor-core kernels: the operands of this size do not fit shared memory");
+    }
     if (precision == SDC_FP64 && ring_smem_bytes(L, sizeof(double2), nullptr) == 0) {
         free_ctx(c);
         return fail(SDC_EUNSUPPORTED, "nlon too long for the FP64 ring kernel (at most 2048 longitudes in FP64)");
@@ -706,26 +710,6 @@ int sdc_create(sdc_ctx **out, int T, int J, int L, int M, int K, double dt, cons
         c->tc.ntiles1 = static_cast<int>(t1.size());
         c->tc.npieces = np;
         c->tc.kj = kj;
-        // dynamic operands, split per launch; zero once so that K padding
-        // and never-written columns stay zero
-        std::vector<long long> cboff(2 * (T + 1));
-        long long ncb = 0;
-        for (int m = 0; m <= T; ++m)
-            for (int p = 0; p < 2; ++p) {
-                cboff[2 * m + p] = ncb;
-                ncb += static_cast<long long>(kNbc1) * (tc_group_krows(T, m, p) / 8) * 64;
-            }
-        const long long nwb = 2LL * (T + 1) * kNbc3 * (kj / 8) * 64;
-        SDC_TRY(cudaMalloc(&c->tc_wb, static_cast<size_t>(nwb) * np * sizeof(uint16_t)));
-        SDC_TRY(cudaMemset(c->tc_wb, 0, static_cast<size_t>(nwb) * np * sizeof(uint16_t)));
-        SDC_TRY(cudaMalloc(&c->tc_cb, static_cast<size_t>(ncb) * np * sizeof(uint16_t)));
-        SDC_TRY(cudaMemset(c->tc_cb, 0, static_cast<size_t>(ncb) * np * sizeof(uint16_t)));
-        SDC_TRY(upload(&c->tc_cboff, cboff.data(), cboff.size()));
-        c->tc.wb = c->tc_wb;
-        c->tc.cb = c->tc_cb;
-        c->tc.wb_elems = nwb;
-        c->tc.cb_elems = ncb;
-        c->tc.cb_off = c->tc_cboff;
         c->tc.err = c->tc_err;
     }
     SDC_TRY(upload(&c->eps, eps.data(), eps.size()));
@@ -976,6 +960,18 @@ static bool header_int(const std::string &hdr, const char *key, long long *out) 
     return end != p;
 }
 
+// value of a floating-point field "key": x (printed with %.17g, so strtod
+// gives back the same double) in a one-line JSON header (false if absent)
+static bool header_double(const std::string &hdr, const char *key, double *out) {
+    const std::string k = std::string("\"") + key + "\":";
+    const size_t at = hdr.find(k);
+    if (at == std::string::npos) return false;
+    const char *p = hdr.c_str() + at + k.size();
+    char *end = nullptr;
+    *out = std::strtod(p, &end);
+    return end != p;
+}
+
 int sdc_load(sdc_ctx *c, void *state, long long *step, const char *path) {
     if (!c || !state || !path) return fail(SDC_EINVAL, "NULL argument");
     FILE *f = std::fopen(path, "rb");
@@ -994,6 +990,20 @@ int sdc_load(sdc_ctx *c, void *state, long long *step, const char *path) {
     if (T != c->T || nc != c->d.ncoef || bytes != static_cast<long long>(n * sizeof(double2))) {
         std::fclose(f);
         return fail(SDC_EINVAL, "state file of another truncation");
+    }
+    // the step count only means a model time under the same grid, nodes,
+    // sweeps, step size and physical constants: all must match exactly
+    long long J = -1, L = -1, M = -1, K = -1;
+    double dt = 0, a = 0, om = 0, g = 0, H = 0;
+    const bool same = header_int(hdr, "nlat", &J) && header_int(hdr, "nlon", &L) && header_int(hdr, "nodes", &M) &&
+                      header_int(hdr, "sweeps", &K) && header_double(hdr, "dt", &dt) &&
+                      header_double(hdr, "radius", &a) && header_double(hdr, "omega", &om) &&
+                      header_double(hdr, "gravity", &g) && header_double(hdr, "mean_depth", &H) && J == c->J &&
+                      L == c->L && M == c->M && K == c->K && dt == c->dt && a == c->phys.radius &&
+                      om == c->phys.omega && g == c->phys.gravity && H == c->phys.mean_depth;
+    if (!same) {
+        std::fclose(f);
+        return fail(SDC_EINVAL, "state file of another configuration (grid, nodes, sweeps, dt or constants)");
     }
     std::vector<double2> h(n);
     const bool got = std::fread(h.data(), sizeof(double2), n, f) == n && std::fgetc(f) == EOF;

@@ -178,6 +178,9 @@ extern "C" int sdc_spec_to_grid_static(int T, int nlat, int nlon, const void *sp
     if (mu_slots + four_slots > kStaticScratchElems) return SDC_EUNSUPPORTED;
     FftPlan plan{};
     if (!fft_plan(nlon, plan)) return SDC_EINVAL;
+    // an error left pending by earlier work is the caller's: report it without
+    // clearing it, so that the launches below are checked on their own
+    if (cudaPeekAtLastError() != cudaSuccess) return SDC_ECUDA;
     double2 *scratch = nullptr;
     int st = setup_device(&scratch);
     if (st != SDC_OK) return st;

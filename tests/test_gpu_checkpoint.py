@@ -1,7 +1,8 @@
 """Checkpoint and resume of a state through the C ABI (sdc_save / sdc_load):
 bitwise round trip, a header that parses as JSON with the context's sizes,
 resume equal bit for bit to an uninterrupted run, and rejection of files of
-another truncation, truncated files and foreign files (GPU only)."""
+another truncation or configuration, truncated files and foreign files
+(GPU only)."""
 import json
 
 import numpy as np
@@ -78,3 +79,30 @@ def test_rejects_foreign_and_damaged_files(tmp_path):
         s21.load(foreign)
     with pytest.raises(SdcError):
         s21.load(str(tmp_path / "missing.sdc"))
+
+
+@pytest.mark.parametrize("other", [dict(dt=300.0), dict(M=4), dict(K=4), dict(L=96)])
+def test_rejects_another_configuration(tmp_path, other):
+    """A file saved under another step size, node or sweep count or grid (same
+    truncation) is refused: its step index would not be a model time here."""
+    from paper_2403_20135_gb300 import SdcError
+    T, J, L = 21, 34, 72
+    kw = dict(M=3, K=3, dt=600.0, L=L)
+    kw.update(other)
+    s_other = _solver(T, J, kw["L"], M=kw["M"], K=kw["K"], dt=kw["dt"])
+    path = str(tmp_path / "other.sdc")
+    s_other.save(torch.zeros(3, s_other.ncoef, dtype=torch.complex128, device="cuda"), path, step=4)
+    with pytest.raises(SdcError) as e:
+        _solver(T, J, L).load(path)
+    assert e.value.status == 1
+    assert "another configuration" in str(e.value)
+
+
+def test_rejects_other_physical_constants(tmp_path):
+    from paper_2403_20135_gb300 import SdcError, Solver
+    T, J, L = 21, 34, 72
+    s = Solver(T, J, L, 3, 3, 600.0, si.RADIUS, si.OMEGA, si.GRAVITY, 2.0 * si.MEAN_DEPTH)
+    path = str(tmp_path / "deep.sdc")
+    s.save(torch.zeros(3, s.ncoef, dtype=torch.complex128, device="cuda"), path)
+    with pytest.raises(SdcError):
+        _solver(T, J, L).load(path)
