@@ -100,3 +100,22 @@ def test_t511_fp32_step_adjoint_close_to_fp64():
     got = to_numpy(_solver(1).step_adjoint(u0, ub))
     err = rel_l2(got, ref)
     assert np.all(err <= bound(1, WL.T, WL.nlat, WL.nlon)), err
+
+
+def test_t511_tensor_core_five_states():
+    """Five node states at T511 in the 3-piece mode (80 projection and 48
+    synthesis columns per tile, the longest groups: the tensor-core kernels'
+    largest shared-memory layouts).  The batch's tendencies against the FP64
+    context's, within the per-tendency bound."""
+    from paper_2403_20135_gb300 import Solver
+    s64 = Solver(WL.T, WL.nlat, WL.nlon, 5, 3, WL.dt, si.RADIUS, si.OMEGA, si.GRAVITY, si.MEAN_DEPTH, precision=0)
+    u0 = s64.initial_state(WL)
+    batch = torch.stack([u0 * f for f in (0.5, 0.75, 1.0, 1.5, 2.0)]).contiguous()
+    ref = to_numpy(s64.tendency(batch))
+    s64.close()
+    sm = Solver(WL.T, WL.nlat, WL.nlon, 5, 3, WL.dt, si.RADIUS, si.OMEGA, si.GRAVITY, si.MEAN_DEPTH, precision=3)
+    got = to_numpy(sm.tendency(batch))
+    sm.sync()
+    for b in range(5):
+        err = rel_l2(got[b], ref[b])
+        assert np.all(err <= bound(3, WL.T, WL.nlat, WL.nlon)), (b, err)
