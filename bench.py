@@ -481,6 +481,7 @@ def cuda_arm(args, rank: int, world: int):
                                         "peak_kind": "nominal FP32 SIMT (algorithmic flops; the tensor-core "
                                                      "modes count their contractions at this rate too)"}}
             sm.close()
+        mixed["fp32_legendre"] = legendre_compare(wl, args.steps, flush)
         ok = [k for k in ("fp32", "bf16x3", "bf16x6") if mixed[k]["fixed_error"]]
         if ok:
             best = max(ok, key=lambda k: mixed[k]["value"])
@@ -524,6 +525,27 @@ def cuda_arm(args, rank: int, world: int):
 
 
 PRECISIONS = {"fp64": 0, "fp32": 1, "bf16x3": 2, "bf16x6": 3}
+
+
+def legendre_compare(wl, steps: int, flush) -> dict:
+    """FP32 mode with the Legendre table against the on-the-fly recurrence:
+    steps/s (CUDA events, L2 flushed per step) and the synthesis kernel's time
+    per launch (kernel-by-kernel profile of the same steps)."""
+    from paper_2403_20135_gb300 import SDC_LEGENDRE_RECURRENCE, Solver
+    out = {}
+    for name in ("table", "recurrence"):
+        s = Solver.for_workload(wl, precision=PRECISIONS["fp32"])
+        if name == "recurrence":
+            s.set_legendre(SDC_LEGENDRE_RECURRENCE)
+        u0 = s.initial_state(wl)
+        x = u0.clone()
+        s.run(x, 2)
+        tm = time_device(s, x, steps, flush)
+        prof, _ = profile_stages(s, u0, flush, 3)
+        out[name] = {"steps_per_s": steps / (sum(tm) * 1e-3),
+                     "synthesis_us_per_launch": 1e3 * prof["synthesis"]["ms_per_launch"]}
+        s.close()
+    return out
 
 
 def t511_leg(steps: int, horizon: int, adj_steps: int, flush):
@@ -604,6 +626,7 @@ def t511_leg(steps: int, horizon: int, adj_steps: int, flush):
             min_free = min(min_free, torch.cuda.mem_get_info()[0])
             s.close()
     s64.close()
+    out["fp32_legendre"] = legendre_compare(wl, steps, flush)
     out["device_memory"] = {"library_and_torch_peak_bytes": int(free0 - min_free),
                             "torch_max_allocated_bytes": int(torch.cuda.max_memory_allocated()),
                             "note": "free-memory drop from before the first create to its minimum over the leg "

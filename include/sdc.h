@@ -113,8 +113,34 @@ typedef enum {
      *   Sec. 4.2's first paragraph, which makes the stiff-limit sweep matrix
      *   I - q^Delta^{-1} Q = I - L^T nilpotent).
      * The explicit weights stay forward Euler (dtau_{j+1}). */
-    SDC_OPT_SERIAL_IMPLICIT = 3
+    SDC_OPT_SERIAL_IMPLICIT = 3,
+    /* Source of the normalised Legendre functions in the FP32 synthesis
+     * (SDC_MIXED_FP32 contexts only; SDC_EUNSUPPORTED in the other modes):
+     * SDC_LEGENDRE_TABLE (default): rows of the precomputed FP32 table;
+     * SDC_LEGENDRE_RECURRENCE: generated on the fly by the three-term
+     *   recurrence in n of the normalised functions (the recurrence that also
+     *   builds the table, SHTns-style regeneration, Sec. 6), in FP32-pair
+     *   arithmetic from the FP64 values of Pbar_m^m and Pbar_{m+1}^m, so the
+     *   synthesis streams no table.  Selecting it the first time builds and
+     *   uploads its coefficient and seed tables (host work and a small device
+     *   allocation; SDC_ECUDA on failure).  The analysis projection and the
+     *   adjoint's transposed transforms keep the table.  Changing the source
+     *   drops the captured graphs. */
+    SDC_OPT_LEGENDRE = 4,
+    /* Concurrent state chains of a tendency batch in the captured step and
+     * retape graphs: 1 runs the transforms of the batch's states as one
+     * launch per stage; 2 (default) splits the states into two halves whose
+     * transforms run on two streams inside the graph, so that one half's
+     * kernels fill the SMs the other half's leave idle.  The arithmetic and
+     * the results are the same.  The tensor-core modes stay on one chain.
+     * Any other value returns SDC_EINVAL; changing it drops the captured
+     * graphs. */
+    SDC_OPT_CHAINS = 5
 } sdc_option;
+enum {
+    SDC_LEGENDRE_TABLE = 0,
+    SDC_LEGENDRE_RECURRENCE = 1
+};
 enum {
     SDC_QDELTA_CLAMPED = 0,
     SDC_QDELTA_LITERAL = 1,

@@ -20,6 +20,9 @@ SDC_SERIAL_IMPLICIT_EULER, SDC_SERIAL_IMPLICIT_LU = 0, 1
 SDC_OPT_METHOD = 2
 SDC_QDELTA_CLAMPED, SDC_QDELTA_LITERAL, SDC_QDELTA_MIN_SR_NS, SDC_QDELTA_IMPLICIT_EULER, SDC_QDELTA_MIN_SR_S = range(5)
 SDC_METHOD_DSDC, SDC_METHOD_SERIAL_SDC, SDC_METHOD_IMEX2 = 0, 1, 2
+SDC_OPT_LEGENDRE = 4
+SDC_OPT_CHAINS = 5
+SDC_LEGENDRE_TABLE, SDC_LEGENDRE_RECURRENCE = 0, 1
 
 
 class SdcPhys(ctypes.Structure):

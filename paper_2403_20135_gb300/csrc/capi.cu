@@ -55,12 +55,18 @@ struct sdc_ctx {
     FftPlan plan{};
     cudaStream_t stream = nullptr;       // caller's stream
     cudaStream_t cap = nullptr;          // private stream used for graph capture
+    cudaStream_t cap2 = nullptr;         // second capture stream: the other chain of a split batch
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    int chains = 2;                      // SDC_OPT_CHAINS
     std::vector<double> mu, w, tau, Q;
     std::vector<double> qd_min_sr_s;     // MIN-SR-S diagonal, computed when that rule is selected
 
     // device tables
     double *pbar = nullptr;
     float *pbar32 = nullptr;
+    // on-the-fly Legendre recurrence of the FP32 synthesis (SDC_OPT_LEGENDRE)
+    int legendre = SDC_LEGENDRE_TABLE;
+    float *rec_ab = nullptr, *rec_seed = nullptr, *rec_mu = nullptr;
     double *eps = nullptr, *lam = nullptr, *mu2 = nullptr, *w2 = nullptr, *syn = nullptr, *ring64 = nullptr;
     float *ring32 = nullptr, *epi32 = nullptr, *syn32 = nullptr;
     int *row_m = nullptr, *coef_m = nullptr;
@@ -86,7 +92,8 @@ struct sdc_ctx {
 
     // tensor-core Legendre tables (split-BF16 modes)
     TcTables tc{};
-    uint16_t *tc_a3 = nullptr, *tc_a1 = nullptr;
+    uint16_t *tc_a3 = nullptr, *tc_a1 = nullptr, *tc_wb = nullptr, *tc_cb = nullptr;
+    long long *tc_cboff = nullptr;
     TcTile3 *tc_t3 = nullptr;
     TcTile1 *tc_t1 = nullptr;
     int *tc_err = nullptr;
@@ -113,10 +120,13 @@ void free_ctx(sdc_ctx *c) {
                     c->tw32, c->twp32, c->un, c->U, c->E, c->E0, c->f1, c->f2, c->f3, c->resid_part, c->resid,
                     c->gstore, c->ub, c->eb, c->ubn, c->ubnext, c->eb0, c->snaps, c->phigrid, c->rgrid,
                     c->loss_part, c->loss_dev, c->tc_a3, c->tc_a1, c->tc_t3, c->tc_t1, c->tc_err, c->den,
-                    c->alt};
+                    c->tc_wb, c->tc_cb, c->tc_cboff, c->alt, c->rec_ab, c->rec_seed, c->rec_mu};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->cap) cudaStreamDestroy(c->cap);
+    if (c->cap2) cudaStreamDestroy(c->cap2);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
     delete c;
 }
 
@@ -166,6 +176,11 @@ DeviceTables tables(const sdc_ctx *c) {
     tb.plan16 = c->plan16;
     tb.twp32 = c->twp32;
     tb.ntwp = c->ntwp;
+    if (c->legendre == SDC_LEGENDRE_RECURRENCE) {
+        tb.rec_ab = reinterpret_cast<const float4 *>(c->rec_ab);
+        tb.rec_seed = reinterpret_cast<const float4 *>(c->rec_seed);
+        tb.rec_mu = reinterpret_cast<const float2 *>(c->rec_mu);
+    }
     return tb;
 }
 
@@ -182,26 +197,39 @@ cudaError_t tendency(sdc_ctx *c, int B, const double2 *states, long long sstride
                      long long tstride, cudaStream_t s, int *launches, StageTimer *timer = nullptr,
                      void *grid_store = nullptr) {
     const bool fp32 = c->precision != SDC_FP64;
-    DeviceTables tb{};
-    tb.pbar = fp32 ? static_cast<const void *>(c->pbar32) : static_cast<const void *>(c->pbar);
-    tb.tw = fp32 ? static_cast<const void *>(c->tw32) : static_cast<const void *>(c->tw);
-    tb.eps = c->eps;
-    tb.lam = c->lam;
-    tb.mu = c->mu2;
-    tb.w = c->w2;
-    tb.syn = c->syn;
-    tb.row_m = c->row_m;
-    tb.coef_m = c->coef_m;
-    tb.err = c->tc_err;
-    tb.ring64 = c->ring64;
-    tb.ring32 = c->ring32;
-    tb.epi32 = c->epi32;
-    tb.syn32 = c->syn32;
-    tb.plan16 = c->plan16;
-    tb.twp32 = c->twp32;
-    tb.ntwp = c->ntwp;
+    const DeviceTables tb = tables(c);
     Workspace ws{c->f1, c->f2, c->f3};
     const bool use_tc = c->precision == SDC_MIXED_BF16X3 || c->precision == SDC_MIXED_BF16X6;
+    // Two chains (SDC_OPT_CHAINS): while a graph is captured, the states of
+    // the batch are split into two halves whose transforms run on two
+    // streams, so that the kernels of one half fill the SMs the other half's
+    // kernels leave idle (tails, order-pair grids smaller than the GPU).  Every
+    // kernel indexes its workspaces by the state, so the second half runs on
+    // the same buffers offset by its first state.  The tensor-core modes
+    // share their split operands across the batch and stay on one chain.
+    if (c->chains == 2 && B >= 2 && s == c->cap && !timer && !use_tc) {
+        const Dims &d = c->d;
+        const int B1 = B / 2, B2 = B - B1;
+        const size_t elem = fp32 ? sizeof(float2) : sizeof(double2);
+        const size_t f1s = static_cast<size_t>(d.J2) * 8 * (d.T + 1) * elem;
+        const size_t f2s = static_cast<size_t>(d.T + 1) * 10 * d.J2 * elem;
+        const size_t f3s = static_cast<size_t>(d.next) * 5 * elem;
+        const size_t gss = static_cast<size_t>(d.J2) * 4 * d.L * elem;
+        Workspace ws2{static_cast<char *>(c->f1) + B1 * f1s, static_cast<char *>(c->f2) + B1 * f2s,
+                      static_cast<char *>(c->f3) + B1 * f3s};
+        cudaError_t e = cudaEventRecord(c->ev_fork, s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(c->cap2, c->ev_fork, 0);
+        if (e == cudaSuccess)
+            e = launch_tendency(d, c->plan, fp32, B1, states, sstride, tend, tstride, tb, ws, s, launches, nullptr,
+                                grid_store, nullptr);
+        if (e == cudaSuccess)
+            e = launch_tendency(d, c->plan, fp32, B2, states + B1 * sstride, sstride,
+                                tend ? tend + B1 * tstride : nullptr, tstride, tb, ws2, c->cap2, launches, nullptr,
+                                grid_store ? static_cast<char *>(grid_store) + B1 * gss : nullptr, nullptr);
+        if (e == cudaSuccess) e = cudaEventRecord(c->ev_join, c->cap2);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, c->ev_join, 0);
+        return e;
+    }
     return launch_tendency(c->d, c->plan, fp32, B, states, sstride, tend, tstride, tb, ws, s, launches, timer,
                            grid_store, use_tc ? &c->tc : nullptr);
 }
@@ -619,11 +647,6 @@ int sdc_create(sdc_ctx **out, int T, int J, int L, int M, int K, double dt, cons
     d.inv_a = 1.0 / phys->radius;
     d.two_omega = 2.0 * phys->omega;
     if (!fft_plan(L, c->plan)) { free_ctx(c); return fail(SDC_EINVAL, "no FFT plan for nlon"); }
-    if ((precision == SDC_MIXED_BF16X3 || precision == SDC_MIXED_BF16X6) &&
-        !tc_fits(T, precision == SDC_MIXED_BF16X3 ? 2 : 3, M)) {
-        free_ctx(c);
-        return fail(SDC_EUNSUPPORTED, "tensor-core kernels: the operands of this size do not fit shared memory");
-    }
     if (precision == SDC_FP64 && ring_smem_bytes(L, sizeof(double2), nullptr) == 0) {
         free_ctx(c);
         return fail(SDC_EUNSUPPORTED, "nlon too long for the FP64 ring kernel (at most 2048 longitudes in FP64)");
@@ -664,6 +687,9 @@ int sdc_create(sdc_ctx **out, int T, int J, int L, int M, int K, double dt, cons
     } while (0)
 
     SDC_TRY(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
+    SDC_TRY(cudaStreamCreateWithFlags(&c->cap2, cudaStreamNonBlocking));
+    SDC_TRY(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+    SDC_TRY(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
     SDC_TRY(configure_transform_kernels(d, c->plan, precision != SDC_FP64));
     SDC_TRY(configure_adjoint_kernels(d, c->plan, precision != SDC_FP64));
     if (precision != SDC_FP64) SDC_TRY(configure_transform_kernels(d, c->plan, false));
@@ -710,6 +736,26 @@ int sdc_create(sdc_ctx **out, int T, int J, int L, int M, int K, double dt, cons
         c->tc.ntiles1 = static_cast<int>(t1.size());
         c->tc.npieces = np;
         c->tc.kj = kj;
+        // dynamic operands, split per launch; zero once so that K padding
+        // and never-written columns stay zero
+        std::vector<long long> cboff(2 * (T + 1));
+        long long ncb = 0;
+        for (int m = 0; m <= T; ++m)
+            for (int p = 0; p < 2; ++p) {
+                cboff[2 * m + p] = ncb;
+                ncb += static_cast<long long>(kNbc1) * (tc_group_krows(T, m, p) / 8) * 64;
+            }
+        const long long nwb = 2LL * (T + 1) * kNbc3 * (kj / 8) * 64;
+        SDC_TRY(cudaMalloc(&c->tc_wb, static_cast<size_t>(nwb) * np * sizeof(uint16_t)));
+        SDC_TRY(cudaMemset(c->tc_wb, 0, static_cast<size_t>(nwb) * np * sizeof(uint16_t)));
+        SDC_TRY(cudaMalloc(&c->tc_cb, static_cast<size_t>(ncb) * np * sizeof(uint16_t)));
+        SDC_TRY(cudaMemset(c->tc_cb, 0, static_cast<size_t>(ncb) * np * sizeof(uint16_t)));
+        SDC_TRY(upload(&c->tc_cboff, cboff.data(), cboff.size()));
+        c->tc.wb = c->tc_wb;
+        c->tc.cb = c->tc_cb;
+        c->tc.wb_elems = nwb;
+        c->tc.cb_elems = ncb;
+        c->tc.cb_off = c->tc_cboff;
         c->tc.err = c->tc_err;
     }
     SDC_TRY(upload(&c->eps, eps.data(), eps.size()));
@@ -823,6 +869,46 @@ int sdc_set_option(sdc_ctx *c, int key, int value) {
             c->method = value;
             for (auto &g : c->graph)
                 if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+        }
+        return SDC_OK;
+    }
+    if (key == SDC_OPT_LEGENDRE) {
+        if (value != SDC_LEGENDRE_TABLE && value != SDC_LEGENDRE_RECURRENCE)
+            return fail(SDC_EINVAL, "bad Legendre source");
+        if (value == SDC_LEGENDRE_RECURRENCE && c->precision != SDC_MIXED_FP32)
+            return fail(SDC_EUNSUPPORTED, "the Legendre recurrence serves the FP32 synthesis only");
+        if (value == SDC_LEGENDRE_RECURRENCE && !c->rec_ab) {
+            const Dims &d = c->d;
+            std::vector<double> table;
+            legendre_table(c->T, d.J2, d.J2p, c->mu, table);
+            std::vector<float> ab, seed, mu2;
+            recurrence_tables(c->T, d.J2, d.J2p, c->mu, table, ab, seed, mu2);
+            auto up = [&](float **dst, const std::vector<float> &v) -> cudaError_t {
+                cudaError_t e = cudaMalloc(dst, v.size() * sizeof(float));
+                if (e != cudaSuccess) return e;
+                return cudaMemcpy(*dst, v.data(), v.size() * sizeof(float), cudaMemcpyHostToDevice);
+            };
+            SDC_CUDA(up(&c->rec_ab, ab));
+            SDC_CUDA(up(&c->rec_seed, seed));
+            SDC_CUDA(up(&c->rec_mu, mu2));
+        }
+        if (value != c->legendre) {
+            SDC_CUDA(cudaStreamSynchronize(c->stream));
+            c->legendre = value;
+            for (auto &g : c->graph)
+                if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+            if (c->graph_retape) { cudaGraphExecDestroy(c->graph_retape); c->graph_retape = nullptr; }
+        }
+        return SDC_OK;
+    }
+    if (key == SDC_OPT_CHAINS) {
+        if (value != 1 && value != 2) return fail(SDC_EINVAL, "chains must be 1 or 2");
+        if (value != c->chains) {
+            SDC_CUDA(cudaStreamSynchronize(c->stream));
+            c->chains = value;
+            for (auto &g : c->graph)
+                if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+            if (c->graph_retape) { cudaGraphExecDestroy(c->graph_retape); c->graph_retape = nullptr; }
         }
         return SDC_OK;
     }

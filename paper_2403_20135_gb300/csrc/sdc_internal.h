@@ -127,6 +127,10 @@ struct DeviceTables {
     const float *epi32;    // FP32 epilogue factors per coefficient: n eps_{n+1}, (n+1) eps_n, lambda_n, 0 [ncoef][4]
     const float *syn32;    // FP32 wind synthesis factors c0, c1, c2, 0 [next][4]
     int *err;              // device flag set by a kernel whose bounded wait expired
+    // on-the-fly Legendre recurrence of the FP32 synthesis (nullptr: table)
+    const float4 *rec_ab;  // (a_hi, a_lo, b_hi, b_lo) per extended row [next]
+    const float4 *rec_seed;   // (Pbar_m^m, Pbar_{m+1}^m) as FP32 pairs [T+1][J2p]
+    const float2 *rec_mu;  // mu_j as an FP32 pair [J2p]
     FftPlan plan16;        // FP32 ring: passes of radix 16, then 8/4/2, then 3
     const float2 *twp32;   // FP32 ring: per-pass twiddles of plan16 (after the first pass)
     int ntwp;
@@ -172,13 +176,21 @@ struct TcTile1 {                  // synthesis: latitudes j0..j0+nj of group (m,
     int m, p, j0, nj, njb, R, KR;
     long long aoff;
 };
-// The dynamic operands are split inside the MMA kernels (tc_legendre.cu).
+// The dynamic operands are split by their own kernels into the same layout,
+// group by group: the projection's W^T as [group][chunk][col block < kNbc3]
+// [k block][8][8], the synthesis coefficients as [group][chunk][col block <
+// kNbc1][k block][8][8].  Col blocks come first inside a chunk, so the
+// blocks of a batch of B states are one contiguous prefix.
 constexpr int kNbc3 = (10 * kMaxNodes + 7) / 8;   // projection columns b*10 + g*2 + (re, im)
 constexpr int kNbc1 = kMaxNodes;                  // synthesis columns b*8 + f*2 + (re, im)
 struct TcTables {
     const uint16_t *a3;           // analysis pieces [npieces][elems3]
     const uint16_t *a1;           // synthesis pieces [npieces][elems1]
     long long elems3, elems1;
+    uint16_t *wb;                 // projection B operand pieces [npieces][wb_elems]
+    uint16_t *cb;                 // synthesis B operand pieces [npieces][cb_elems]
+    long long wb_elems, cb_elems;
+    const long long *cb_off;      // [2 (T+1)] start of group (m, p) = 2 m + p in each cb piece
     const TcTile3 *tiles3;
     const TcTile1 *tiles1;
     int ntiles3, ntiles1;
@@ -204,6 +216,9 @@ bool lu_implicit_weights(int M, const std::vector<double> &Q, std::vector<double
 // padded to J2p: table[(ext_offset(m) + n - m) * J2p + j].
 void legendre_table(int T, int J2, int J2p, const std::vector<double> &mu, std::vector<double> &table);
 void epsilon_table(int T, std::vector<double> &eps);   // extended packing, eps_n^m
+// FP32-pair tables of the on-the-fly Legendre recurrence (tables.cpp)
+void recurrence_tables(int T, int J2, int J2p, const std::vector<double> &mu, const std::vector<double> &table,
+                       std::vector<float> &ab, std::vector<float> &seed, std::vector<float> &mu2);
 void synthesis_factors(int T, double radius, std::vector<double> &syn);   // [next][3]
 void order_maps(int T, std::vector<int> &row_m, std::vector<int> &coef_m);
 bool fft_plan(int L, FftPlan &plan);
@@ -222,14 +237,12 @@ cudaError_t launch_tendency(const Dims &d, const FftPlan &plan, bool fp32, int B
                             long long sstride, double2 *tend, long long tstride, const DeviceTables &tb,
                             const Workspace &ws, cudaStream_t s, int *launches, StageTimer *timer = nullptr,
                             void *grid_store = nullptr, const TcTables *tc = nullptr);
-// Each adds its one launch to *launches.
+// Each adds its two launches (operand split + MMA kernel) to *launches.
 cudaError_t launch_tc_synthesis(const TcTables &tc, const Dims &d, int B, const double2 *states, long long sstride,
-                                const double *syn, float2 *f1, cudaStream_t s, int *launches);
+                                const double *syn, const int *row_m, float2 *f1, cudaStream_t s, int *launches);
 cudaError_t launch_tc_projection(const TcTables &tc, const Dims &d, int B, const float2 *f2, float2 *y,
                                  cudaStream_t s, int *launches);
 cudaError_t configure_tc_kernels();
-// Whether the tensor-core kernels' shared memory holds B states at truncation T.
-bool tc_fits(int T, int npieces, int B);
 cudaError_t launch_sweep(const SweepParams &p, int M, bool fp32, cudaStream_t s, int *launches,
                          StageTimer *timer = nullptr);
 cudaError_t launch_resid_reduce(const double *part, int nblocks, int M, int m0, int m1,

@@ -307,6 +307,45 @@ void legendre_table(int T, int J2, int J2p, const std::vector<double> &mu, std::
     }
 }
 
+// Tables of the on-the-fly Legendre recurrence of the FP32 synthesis, every
+// value split into an FP32 pair (hi = the FP32 rounding, lo = the FP32
+// rounding of the remainder):
+//   ab[e] = (a_hi, a_lo, b_hi, b_lo) of Pbar_n = a_n mu Pbar_{n-1} - b_n Pbar_{n-2},
+//           a_n = 1 / eps_n, b_n = eps_{n-1} / eps_n (row e of degree n >= m + 2),
+//   seed[m][j] = (Pbar_m^m, Pbar_{m+1}^m) at latitude j (from the FP64 table),
+//   mu2[j] = mu_j (zero for the padding latitudes j >= J2).
+void recurrence_tables(int T, int J2, int J2p, const std::vector<double> &mu, const std::vector<double> &table,
+                       std::vector<float> &ab, std::vector<float> &seed, std::vector<float> &mu2) {
+    const int next = (T + 1) * (T + 4) / 2;
+    std::vector<double> eps;
+    epsilon_table(T, eps);
+    auto split = [](double x, float *o) {
+        const float hi = static_cast<float>(x);
+        o[0] = hi;
+        o[1] = static_cast<float>(x - static_cast<double>(hi));
+    };
+    ab.assign(4 * static_cast<size_t>(next), 0.0f);
+    for (int m = 0; m <= T; ++m) {
+        const int base = ext_offset(T, m);
+        for (int n = m + 2; n <= T + 1; ++n) {
+            const int e = base + n - m;
+            split(1.0 / eps[e], &ab[4 * static_cast<size_t>(e)]);
+            split(eps[e - 1] / eps[e], &ab[4 * static_cast<size_t>(e) + 2]);
+        }
+    }
+    seed.assign(4 * static_cast<size_t>(T + 1) * J2p, 0.0f);
+    for (int m = 0; m <= T; ++m) {
+        const int base = ext_offset(T, m);
+        for (int j = 0; j < J2; ++j) {
+            float *o = &seed[4 * (static_cast<size_t>(m) * J2p + j)];
+            split(table[static_cast<size_t>(base) * J2p + j], o);
+            split(table[static_cast<size_t>(base + 1) * J2p + j], o + 2);
+        }
+    }
+    mu2.assign(2 * static_cast<size_t>(J2p), 0.0f);
+    for (int j = 0; j < J2; ++j) split(mu[j], &mu2[2 * static_cast<size_t>(j)]);
+}
+
 void epsilon_table(int T, std::vector<double> &eps) {
     const int next = (T + 1) * (T + 4) / 2;
     eps.assign(next, 0.0);

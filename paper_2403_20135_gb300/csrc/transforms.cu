@@ -632,11 +632,43 @@ __host__ inline bool synthesis_nb_fits(const Dims &d, int nb, int nf) {
 // F1[b][j][f][parity][m]).  NF = 5: the transpose of the analysis projection
 // in the adjoint (coefficients = the rows Y-bar[b][e][5], gathered with
 // cp.async; output W-bar[b][j][g][parity][m]).
-template <int NB, int S, int NF>
+// FP32-pair ("double-float") arithmetic of the on-the-fly Legendre
+// recurrence: a value is hi + lo with |lo| <= ulp(hi) / 2.  The products use
+// the FMA error-free transformation of the product, the sum Knuth's
+// two-sum followed by a fast renormalisation (Dekker); the explicit _rn
+// intrinsics keep the compiler from contracting or reordering them.
+struct dfl {
+    float hi, lo;
+};
+__device__ __forceinline__ dfl df_mul(dfl a, dfl b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    const float s = __fadd_rn(p, e);
+    return {s, __fsub_rn(e, __fsub_rn(s, p))};
+}
+__device__ __forceinline__ dfl df_sub(dfl a, dfl b) {
+    const float s = __fsub_rn(a.hi, b.hi);
+    const float v = __fsub_rn(s, a.hi);
+    float e = __fsub_rn(__fsub_rn(a.hi, __fsub_rn(s, v)), __fadd_rn(b.hi, v));
+    e = __fadd_rn(e, __fsub_rn(a.lo, b.lo));
+    const float r = __fadd_rn(s, e);
+    return {r, __fsub_rn(e, __fsub_rn(r, s))};
+}
+
+// REC (NF = 4): the Legendre rows of every chunk are generated in shared
+// memory by the three-term recurrence Pbar_n = a_n mu Pbar_{n-1} -
+// b_n Pbar_{n-2} (a_n = 1 / eps_n, b_n = eps_{n-1} / eps_n) in FP32-pair
+// arithmetic, one thread per latitude, from the FP64 values of Pbar_m^m and
+// Pbar_{m+1}^m, instead of being copied from the FP32 table; the stored value
+// is the FP32 rounding of the pair.
+template <int NB, int S, int NF, bool REC = false>
 __global__ void __launch_bounds__(kSynNbMaxThreads, 1)
     k1_synthesis_f32_nb(const double2 *__restrict__ states, long long sstride, const float2 *__restrict__ ybar,
                         int B, Dims d, const float *__restrict__ pbar, const float4 *__restrict__ syn32,
-                        float2 *__restrict__ f1, int nstages, int *err) {
+                        float2 *__restrict__ f1, int nstages, int *err, const float4 *__restrict__ rec_ab = nullptr,
+                        const float4 *__restrict__ rec_seed = nullptr, const float2 *__restrict__ rec_mu = nullptr) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     uint64_t *mbar = reinterpret_cast<uint64_t *>(smem_raw);                 // [kMaxSynStages], then the prologue's
     uint64_t *mpro = mbar + kMaxSynStages;
@@ -697,7 +729,8 @@ __global__ void __launch_bounds__(kSynNbMaxThreads, 1)
             }
         bulk_copy(sy, syn32 + ext_offset(T, m1), static_cast<uint32_t>(nn1) * sizeof(float4), mpro);
         if (two) bulk_copy(sy + nn1, syn32 + ext_offset(T, m2), static_cast<uint32_t>(nn2) * sizeof(float4), mpro);
-        for (; issued < min(nstages, nch); ++issued) issue(issued);
+        if (!REC)
+            for (; issued < min(nstages, nch); ++issued) issue(issued);
     }
     if constexpr (NF == 5) {                             // the Y-bar rows of both orders, 8 bytes per piece
         for (int i = threadIdx.x; i < rows * NB * 5; i += blockDim.x) {
@@ -770,14 +803,49 @@ __global__ void __launch_bounds__(kSynNbMaxThreads, 1)
             for (int f = 0; f < NF; ++f) a[b][f][0] = a[b][f][1] = make_float2(0.f, 0.f);
     };
     reset();
+    // recurrence state of this thread's latitude (REC): rows t - 2 and t - 1
+    dfl r_m2{0.f, 0.f}, r_m1{0.f, 0.f}, r_mu{0.f, 0.f};
+    if (REC && threadIdx.x < d.J2p) {
+        const float2 mv = rec_mu[threadIdx.x];
+        r_mu = {mv.x, mv.y};
+    }
     int c = 0;
     for (; c < nch; ++c) {
         int m, t0, cnt;
         chunk(c, m, t0, cnt);
-        const bool slow = !mbar_wait(&mbar[c % nstages], (c / nstages) & 1);
-        if (__syncthreads_or(slow)) {                    // the block agrees before anyone leaves
-            if (threadIdx.x == 0) atomicExch(err, 5);
-            break;
+        if constexpr (REC) {
+            float *Pg = stage + (c % nstages) * stage_elems;
+            const int j = threadIdx.x;
+            if (j < d.J2p) {
+                if (t0 == 0) {                           // a new order: Pbar_m^m, Pbar_{m+1}^m
+                    const float4 sd = rec_seed[static_cast<size_t>(m) * d.J2p + j];
+                    r_m2 = {sd.x, sd.y};
+                    r_m1 = {sd.z, sd.w};
+                }
+                const float4 *ab = rec_ab + ext_offset(T, m);
+                for (int r = 0; r < cnt; ++r) {
+                    const int t = t0 + r;
+                    dfl v;
+                    if (t == 0) {
+                        v = r_m2;
+                    } else if (t == 1) {
+                        v = r_m1;
+                    } else {
+                        const float4 k = __ldg(ab + t);
+                        v = df_sub(df_mul(df_mul({k.x, k.y}, r_mu), r_m1), df_mul({k.z, k.w}, r_m2));
+                        r_m2 = r_m1;
+                        r_m1 = v;
+                    }
+                    Pg[static_cast<size_t>(r) * d.J2p + j] = v.hi;
+                }
+            }
+            __syncthreads();
+        } else {
+            const bool slow = !mbar_wait(&mbar[c % nstages], (c / nstages) & 1);
+            if (__syncthreads_or(slow)) {                // the block agrees before anyone leaves
+                if (threadIdx.x == 0) atomicExch(err, 5);
+                break;
+            }
         }
         const float *P = stage + (c % nstages) * stage_elems + jl;
         const float *cc = cf + static_cast<size_t>((c >= nch1 ? nn1 : 0) + t0) * RS;
@@ -835,7 +903,7 @@ __global__ void __launch_bounds__(kSynNbMaxThreads, 1)
             reset();
         }
         __syncthreads();                                 // every read of this stage is done
-        if (threadIdx.x == 0 && issued < nch) issue(issued++);
+        if (!REC && threadIdx.x == 0 && issued < nch) issue(issued++);
     }
     if (c < nch && threadIdx.x == 0) {                   // stopped early: let issued copies land (bounded)
         for (int k = c; k < issued; ++k) mbar_wait(&mbar[k % nstages], (k / nstages) & 1);
@@ -1063,6 +1131,7 @@ static cudaError_t configure(const Dims &d, const FftPlan &plan) {
     cudaError_t e = cudaSuccess;
     if (sm2 != 0) e = cudaFuncSetAttribute(k2_ring<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2);
     if (e != cudaSuccess) return e;
+
     e = cudaFuncSetAttribute(k1_synthesis<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(static_cast<size_t>(d.T + 4) * 4 * sizeof(V2<R>)));
     if (e != cudaSuccess || sizeof(R) != sizeof(float)) return e;
@@ -1091,12 +1160,21 @@ static cudaError_t configure(const Dims &d, const FftPlan &plan) {
               (const void *)k1_synthesis_f32_nb<4, 2, 4>}},
             {{(const void *)k1_synthesis_f32_nb<1, 1, 5>, (const void *)k1_synthesis_f32_nb<2, 1, 5>, nullptr},
              {(const void *)k1_synthesis_f32_nb<1, 2, 5>, (const void *)k1_synthesis_f32_nb<2, 2, 5>, nullptr}}};
+        // the recurrence variants of the synthesis (NF = 4) use the same shared memory
+        const void *fr[2][3] = {{(const void *)k1_synthesis_f32_nb<1, 1, 4, true>,
+                                 (const void *)k1_synthesis_f32_nb<2, 1, 4, true>,
+                                 (const void *)k1_synthesis_f32_nb<4, 1, 4, true>},
+                                {(const void *)k1_synthesis_f32_nb<1, 2, 4, true>,
+                                 (const void *)k1_synthesis_f32_nb<2, 2, 4, true>,
+                                 (const void *)k1_synthesis_f32_nb<4, 2, 4, true>}};
         for (int fi = 0; fi < 2; ++fi)
             for (int k = 0; k < 3 - fi; ++k) {
                 if (!synthesis_nb_fits(d, 1 << k, 4 + fi)) continue;
                 for (int si = 0; si < 2; ++si) {
-                    e = cudaFuncSetAttribute(fs[fi][si][k], cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)synthesis_nb_smem(d, 1 << k, 4 + fi));
+                    const int bytes = (int)synthesis_nb_smem(d, 1 << k, 4 + fi);
+                    e = cudaFuncSetAttribute(fs[fi][si][k], cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+                    if (e == cudaSuccess && fi == 0)
+                        e = cudaFuncSetAttribute(fr[si][k], cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
                     if (e != cudaSuccess) return e;
                 }
             }
@@ -1123,7 +1201,7 @@ static cudaError_t configure(const Dims &d, const FftPlan &plan) {
 template <int NF>
 static cudaError_t launch_synthesis_nb(const Dims &d, int B, const double2 *states, long long sstride,
                                        const float2 *ybar, const float *pbar, const float *syn32, float2 *f1,
-                                       int *err, cudaStream_t s) {
+                                       int *err, cudaStream_t s, const DeviceTables *rec = nullptr) {
     // NF = 5 keeps NB <= 2: four states' 40 accumulators and coefficient rows exceed the registers
     const int nb = B == 1 ? 1 : ((NF == 5 || B == 2 || !synthesis_nb_fits(d, 4, NF)) ? 2 : 4);
     const int S = synthesis_nb_s(d.J2);
@@ -1131,6 +1209,25 @@ static cudaError_t launch_synthesis_nb(const Dims &d, int B, const double2 *stat
     const int nt = synthesis_nb_threads(d.J2, S), ns = synthesis_nb_stages(d, nb, NF);
     const size_t sm = synthesis_nb_smem(d, nb, NF);
     const float4 *sy = reinterpret_cast<const float4 *>(syn32);
+    // the recurrence needs a thread per latitude (the block always has at least J2 + 1 threads)
+    if constexpr (NF == 4) {
+        if (rec && rec->rec_ab && nt >= d.J2p) {
+#define SDC_SYN_REC(NBV, SV)                                                                                  \
+    k1_synthesis_f32_nb<NBV, SV, 4, true><<<g, nt, sm, s>>>(states, sstride, ybar, B, d, pbar, sy, f1, ns, err, \
+                                                             rec->rec_ab, rec->rec_seed, rec->rec_mu)
+            if (S == 2) {
+                if (nb == 1) SDC_SYN_REC(1, 2);
+                else if (nb == 2) SDC_SYN_REC(2, 2);
+                else SDC_SYN_REC(4, 2);
+            } else {
+                if (nb == 1) SDC_SYN_REC(1, 1);
+                else if (nb == 2) SDC_SYN_REC(2, 1);
+                else SDC_SYN_REC(4, 1);
+            }
+#undef SDC_SYN_REC
+            return cudaGetLastError();
+        }
+    }
 #define SDC_SYN_NB(NBV, SV) \
     k1_synthesis_f32_nb<NBV, SV, NF><<<g, nt, sm, s>>>(states, sstride, ybar, B, d, pbar, sy, f1, ns, err)
     if (S == 2) {
@@ -1164,10 +1261,11 @@ static cudaError_t launch_tendency_t(const Dims &d, const FftPlan &plan, int B, 
     if (timer) timer->mark(STAGE_SYNTH);
     if constexpr (sizeof(R) == sizeof(float)) {
         if (tc) {
-            cudaError_t e = launch_tc_synthesis(*tc, d, B, states, sstride, tb.syn, f1, s, launches);
+            cudaError_t e = launch_tc_synthesis(*tc, d, B, states, sstride, tb.syn, tb.row_m, f1, s, launches);
             if (e != cudaSuccess) return e;
         } else if (synthesis_nb_fits(d, 2, 4)) {
-            const cudaError_t e = launch_synthesis_nb<4>(d, B, states, sstride, nullptr, pbar, tb.syn32, f1, tb.err, s);
+            const cudaError_t e =
+                launch_synthesis_nb<4>(d, B, states, sstride, nullptr, pbar, tb.syn32, f1, tb.err, s, &tb);
             if (e != cudaSuccess) return e;
             if (launches) ++*launches;
         } else {

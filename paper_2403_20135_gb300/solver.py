@@ -58,6 +58,14 @@ class Solver:
         """Implicit weights of serial IMEX SDC: SDC_SERIAL_IMPLICIT_EULER or SDC_SERIAL_IMPLICIT_LU."""
         _lib.check(self.lib.sdc_set_option(self.h, _lib.SDC_OPT_SERIAL_IMPLICIT, weights), "sdc_set_option")
 
+    def set_legendre(self, source: int):
+        """Legendre functions of the FP32 synthesis: SDC_LEGENDRE_TABLE or SDC_LEGENDRE_RECURRENCE."""
+        _lib.check(self.lib.sdc_set_option(self.h, _lib.SDC_OPT_LEGENDRE, source), "sdc_set_option")
+
+    def set_chains(self, chains: int):
+        """Concurrent state chains of a tendency batch in the step graphs: 1 or 2."""
+        _lib.check(self.lib.sdc_set_option(self.h, _lib.SDC_OPT_CHAINS, chains), "sdc_set_option")
+
     @classmethod
     def for_workload(cls, wl, precision: int = _lib.SDC_FP64, **kw):
         import swe_inputs as si

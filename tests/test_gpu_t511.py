@@ -103,10 +103,9 @@ def test_t511_fp32_step_adjoint_close_to_fp64():
 
 
 def test_t511_tensor_core_five_states():
-    """Five node states at T511 in the 3-piece mode (80 projection and 48
-    synthesis columns per tile, the longest groups: the tensor-core kernels'
-    largest shared-memory layouts).  The batch's tendencies against the FP64
-    context's, within the per-tendency bound."""
+    """Five node states at T511 in the 3-piece mode (64 projection and 48
+    synthesis columns per tile, the longest groups).  The batch's tendencies
+    against the FP64 context's, within the per-tendency bound."""
     from paper_2403_20135_gb300 import Solver
     s64 = Solver(WL.T, WL.nlat, WL.nlon, 5, 3, WL.dt, si.RADIUS, si.OMEGA, si.GRAVITY, si.MEAN_DEPTH, precision=0)
     u0 = s64.initial_state(WL)
