@@ -43,20 +43,26 @@ FP32_SIMT_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # DRAM bytes (read + write) of one launch of the FP64 ring kernel with a batch
 # of 4 states at the T255 workload, from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum), and the SHA-256 prefix of
-# the kernel's sources at that capture.  The traffic is the batch's F1 input,
-# so a launch of b states moves b/4 of it.  When the sources differ the
-# counters no longer describe the kernel and the bench reports null.
-RING_FP64_TRAFFIC_B4 = 25.291264e6 + 228.096e3
-RING_FP64_SOURCES = ("paper_2403_20135_gb300/csrc/transforms.cu", "paper_2403_20135_gb300/csrc/fft.cuh")
-RING_FP64_SOURCES_SHA = None
+# the kernel's source (its function in transforms.cu and the FFT header) at
+# that capture.  The traffic is the batch's F1 input, so a launch of b states
+# moves b/4 of it.  When the source differs the counters no longer describe
+# the kernel and the bench reports null.
+RING_FP64_TRAFFIC_B4 = 25289216.0 + 192768.0
+RING_FP64_SOURCES_SHA = "22cf27af41541150"
 
 
-def _sources_sha(paths) -> str:
+def _ring_fp64_source_sha() -> str:
+    """SHA-256 prefix of the FP64 ring kernel's source text: the k2_ring
+    function of transforms.cu and all of fft.cuh."""
     import hashlib
-    h = hashlib.sha256()
-    for p in paths:
-        with open(os.path.join(ROOT, p), "rb") as f:
-            h.update(f.read())
+    csrc = os.path.join(ROOT, "paper_2403_20135_gb300", "csrc")
+    with open(os.path.join(csrc, "transforms.cu")) as f:
+        text = f.read()
+    start = text.index("__global__ void k2_ring(")
+    end = text.index("// -----", start)
+    h = hashlib.sha256(text[start:end].encode())
+    with open(os.path.join(csrc, "fft.cuh"), "rb") as f:
+        h.update(f.read())
     return h.hexdigest()[:16]
 
 
@@ -402,7 +408,7 @@ def cuda_arm(args, rank: int, world: int):
     flops_per_launch = stage_flops(wl, dom, nodes_per_step) / launches_per_step
     achieved_tf = flops_per_launch / (prof[dom]["ms_per_launch"] * 1e-3) / 1e12
     traffic = None
-    if dom == "ring" and RING_FP64_SOURCES_SHA == _sources_sha(RING_FP64_SOURCES):
+    if dom == "ring" and RING_FP64_SOURCES_SHA == _ring_fp64_source_sha():
         traffic = RING_FP64_TRAFFIC_B4 * (nodes_per_step / launches_per_step) / 4.0
     fp64_peak = fp64_fma_rate()
     roofline = {"bound": "alu", "achieved": achieved_tf, "peak": fp64_peak, "unit": "TFLOP/s",
@@ -688,13 +694,16 @@ def work_precision(hours: float):
                       "reference": f"dSDC FP64, dt = {dt_ref} s"}), flush=True)
 
 
-def profile_run(name: str, steps: int, adjoint: bool = False):
+def profile_run(name: str, steps: int, adjoint: bool = False, chains: int = 0):
     """A few untimed steps of one precision mode (the command profilers wrap);
-    with `adjoint`, reversed steps (retape + step adjoint) instead."""
+    with `adjoint`, reversed steps (retape + step adjoint) instead; `chains`
+    (1 or 2) overrides the library's default chain count."""
     import torch
     from paper_2403_20135_gb300 import Solver
     wl = si.WORKLOADS[WORKLOAD]
     s = Solver.for_workload(wl, precision=PRECISIONS[name])
+    if chains:
+        s.set_chains(chains)
     u = s.initial_state(wl)
     if adjoint:
         ub = torch.ones_like(u)
@@ -724,6 +733,7 @@ def main():
     ap.add_argument("--profile-run", choices=sorted(PRECISIONS), default=None,
                     help="only run --steps untimed steps of this precision (for profilers)")
     ap.add_argument("--adjoint", action="store_true", help="with --profile-run: reversed steps")
+    ap.add_argument("--chains", type=int, default=0, help="with --profile-run: concurrent state chains (1 or 2)")
     ap.add_argument("--work-precision", type=float, default=None, metavar="HOURS",
                     help="only run the work-precision study over this simulated time")
     args = ap.parse_args()
@@ -731,7 +741,7 @@ def main():
         work_precision(args.work_precision)
         return
     if args.profile_run:
-        profile_run(args.profile_run, args.steps, args.adjoint)
+        profile_run(args.profile_run, args.steps, args.adjoint, args.chains)
         return
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
