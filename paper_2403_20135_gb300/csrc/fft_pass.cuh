@@ -197,6 +197,38 @@ __device__ __forceinline__ void fft_pass_ct(const float2 *src, float2 *dst, cons
     }
 }
 
+// Ns and twiddle offset (in the [r - 1][k] pass-by-pass table) of pass p.
+__host__ __device__ constexpr int plan16_ns(int L, int p) {
+    int ns = 1;
+    for (int q = 0; q < p; ++q) ns *= plan16_radix(L, q);
+    return ns;
+}
+__host__ __device__ constexpr int plan16_toff(int L, int p) {
+    int t = 0, ns = 1;
+    for (int q = 0; q < p; ++q) {
+        const int r = plan16_radix(L, q);
+        if (ns > 1) t += (r - 1) * ns;
+        ns *= r;
+    }
+    return t;
+}
+
+// Passes P .. PEND - 1 only (the caller does the rest); returns the buffer
+// holding the result.
+template <int L, int NB, int PEND, int P = 0, int Ns = 1, int TOFF = 0>
+__device__ __forceinline__ float2 *fft_passes_ct_until(float2 *src, float2 *dst, const float2 *__restrict__ twp,
+                                                       bool inv) {
+    if constexpr (P == PEND) {
+        return src;
+    } else {
+        constexpr int R = plan16_radix(L, P);
+        fft_pass_ct<R, L, Ns, NB>(src, dst, twp + TOFF, inv);
+        __syncthreads();
+        return fft_passes_ct_until<L, NB, PEND, P + 1, Ns * R, (Ns > 1 ? TOFF + (R - 1) * Ns : TOFF)>(dst, src, twp,
+                                                                                                        inv);
+    }
+}
+
 template <int L, int NB, int P = 0, int Ns = 1, int TOFF = 0>
 __device__ __forceinline__ float2 *fft_passes_ct(float2 *src, float2 *dst, const float2 *__restrict__ twp,
                                                  bool inv) {

@@ -300,7 +300,7 @@ __global__ void __launch_bounds__(kTcThreads) k3_tc(TcTables tc, Dims d, int B, 
 // Synthesis: one block per tile (m, p, latitudes j0..j0+nj), all B states.
 // Columns col = b*8 + f*2 + (re, im) of the prepared coefficients C[q][col]
 // (fields zeta, Phi', U, V as in the FP64/FP32 synthesis), pre-split by
-// k1_prep_split.  Output F1[b][j][f][p][m] (float2).
+// k1_prep_split.  Output F1[b][j][m][p][f] (float2).
 // ---------------------------------------------------------------------------
 template <int NP>
 __global__ void __launch_bounds__(kTcThreads) k1_tc(TcTables tc, Dims d, int B, float2 *__restrict__ f1) {
@@ -326,9 +326,10 @@ __global__ void __launch_bounds__(kTcThreads) k1_tc(TcTables tc, Dims d, int B, 
 #pragma unroll
             for (int cb = 0; cb < kNbc1; ++cb) {
                 if (cb < B) {
-                    float2 *o = f1 + (static_cast<size_t>(cb) * d.J2 + j) * 8 * (T + 1) + t.p * (T + 1) + m;
-#pragma unroll
-                    for (int f = 0; f < 4; ++f) o[f * 2 * (T + 1)] = make_float2(acc[cb][2 * f], acc[cb][2 * f + 1]);
+                    float4 *o = reinterpret_cast<float4 *>(f1 + (static_cast<size_t>(cb) * d.J2 + j) * 8 * (T + 1) +
+                                                           (2 * m + t.p) * 4);
+                    o[0] = make_float4(acc[cb][0], acc[cb][1], acc[cb][2], acc[cb][3]);
+                    o[1] = make_float4(acc[cb][4], acc[cb][5], acc[cb][6], acc[cb][7]);
                 }
             }
         }

@@ -33,7 +33,10 @@ namespace sdc {
 // ---------------------------------------------------------------------------
 // K1: synthesis.  grid ((T+2)/2 order pairs, B states, latitude chunks): a
 // block serves orders m and T - m (equal work for every block).  Output
-// F1[b][j][field][parity][m], fields (zeta, Phi', U, V).  The wind
+// F1[b][j][field][parity][m] in FP64, F1[b][j][m][parity][field] in FP32
+// (the four fields of one (j, m, parity) fill one 32-byte sector, so the
+// transposing stores of the FP32 kernels are whole sectors), fields
+// (zeta, Phi', U, V).  The wind
 // coefficients on degrees n' = m..T+1 come from host-computed factors
 // (c0, c1, c2) = syn[e]:
 //   U_n' = i c0 div_n' - c1 zeta_{n'-1} - c2 zeta_{n'+1}
@@ -244,6 +247,27 @@ __global__ void k2_ring(const V2<R> *__restrict__ f1, V2<R> *__restrict__ f2, Di
 // always written to X, the forward result again lands by parity.
 // ---------------------------------------------------------------------------
 
+// Unpack of the forward transforms of the north (real part) and south
+// (imaginary part) rings, weighting and store of F2[b][m][g][parity][j2].
+__device__ __forceinline__ void ring_f32_output(const float2 *Y, float2 *__restrict__ f2, const Dims &d, int b, int j2,
+                                                int Lp, int L, const float *__restrict__ rw) {
+    const int T = d.T;
+    const float wt = rw[4 * j2 + 2], wp = rw[4 * j2 + 3];
+    const float half_invL = 0.5f / float(L);
+    for (int i = threadIdx.x; i < 5 * (T + 1); i += blockDim.x) {
+        const int g = i / (T + 1), m = i - g * (T + 1);
+        const float2 y = Y[g * Lp + fpad(m)];
+        float2 yc = Y[g * Lp + fpad(m == 0 ? 0 : L - m)];
+        yc.y = -yc.y;
+        const float2 gn = cscale<float>(cadd<float>(y, yc), half_invL);
+        const float2 gsx = cscale<float>(mul_mi<float>(csub<float>(y, yc)), half_invL);
+        const float wg = (g == P_E) ? wp : wt;
+        float2 *o = f2 + ((static_cast<size_t>(b) * (T + 1) + m) * 5 + g) * 2 * d.J2 + j2;
+        o[0] = cscale<float>(cadd<float>(gn, gsx), wg);
+        o[d.J2] = cscale<float>(csub<float>(gn, gsx), wg);
+    }
+}
+
 // LC > 0: ring length fixed at compile time (LC == plan.L); 0: any length.
 template <int LC>
 __global__ void __launch_bounds__(256) k2_ring_f32(const float2 *__restrict__ f1, float2 *__restrict__ f2, Dims d,
@@ -276,20 +300,66 @@ __global__ void __launch_bounds__(256) k2_ring_f32(const float2 *__restrict__ f1
     cp_async_wait<0>();
     __syncthreads();
     for (int i = threadIdx.x; i < 4 * (T + 1); i += blockDim.x) {
-        const int f = i / (T + 1), m = i - f * (T + 1);
-        float2 e = raw[(f * 2 + 0) * (T + 1) + m], o = raw[(f * 2 + 1) * (T + 1) + m];
+        const int m = i >> 2, f = i & 3;                 // raw = F1[b][j2][m][parity][f]
+        float2 e = raw[m * 8 + f], o = raw[m * 8 + 4 + f];
         if (m == 0) { e.y = 0.f; o.y = 0.f; }
         const float2 n = cadd<float>(e, o), sv = csub<float>(e, o);
         X[f * Lp + fpad(m)] = make_float2(n.x - sv.y, n.y + sv.x);                // n + i s
         if (m > 0) X[f * Lp + fpad(L - m)] = make_float2(n.x + sv.y, -n.y + sv.x);   // conj(n) + i conj(s)
     }
     __syncthreads();
+    const float fN = rw[4 * j2], inv2c = rw[4 * j2 + 1];
+    float2 *gs = gstore ? gstore + (static_cast<size_t>(b) * d.J2 + j2) * 4 * L : nullptr;
+    constexpr int NPASS = LC > 0 ? plan16_npasses(LC) : 0;
+    if constexpr (LC > 0 && plan16_radix(LC, NPASS - 1) == 3) {
+        // The last inverse pass (radix 3, Ns = L/3) fused with the grid
+        // products: a thread finishes the butterflies of all four fields at
+        // the grid points j, j + L/3, j + 2L/3 and writes the five products
+        // there, so the four transformed fields never go back to shared memory.
+        constexpr int Lr = LC / 3, TL = plan16_toff(LC, NPASS - 1);
+        static_assert(plan16_ns(LC, NPASS - 1) == Lr, "the last pass spans the ring in three strides");
+        float2 *A = fft_passes_ct_until<LC, 4, NPASS - 1>(X, S, TW, true);
+        float2 *P2 = (A == X) ? S : X;
+        for (int j = threadIdx.x; j < Lr; j += blockDim.x) {
+            float2 w1 = TW[TL + j], w2 = TW[TL + Lr + j];
+            w1.y = -w1.y;                                // inverse transform: conjugate twiddles
+            w2.y = -w2.y;
+            float2 v[4][3];
+#pragma unroll
+            for (int f = 0; f < 4; ++f) {
+                v[f][0] = A[f * Lp + fpad(j)];
+                v[f][1] = cmul<float>(A[f * Lp + fpad(j + Lr)], w1);
+                v[f][2] = cmul<float>(A[f * Lp + fpad(j + 2 * Lr)], w2);
+                dft<3>(v[f], true);
+            }
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                const int k = j + r * Lr, kp = fpad(k);
+                const float2 zz = v[G_ZETA][r], pp = v[G_PHI][r], uu = v[G_U][r], vv = v[G_V][r];
+                if (gs) {
+                    gs[G_ZETA * L + k] = zz;
+                    gs[G_PHI * L + k] = pp;
+                    gs[G_U * L + k] = uu;
+                    gs[G_V * L + k] = vv;
+                }
+                const float etaN = zz.x + fN, etaS = zz.y - fN;
+                P2[P_A * Lp + kp] = make_float2(etaN * uu.x, etaS * uu.y);
+                P2[P_B * Lp + kp] = make_float2(etaN * vv.x, etaS * vv.y);
+                P2[P_C * Lp + kp] = make_float2(pp.x * uu.x, pp.y * uu.y);
+                P2[P_D * Lp + kp] = make_float2(pp.x * vv.x, pp.y * vv.y);
+                P2[P_E * Lp + kp] =
+                    make_float2((uu.x * uu.x + vv.x * vv.x) * inv2c, (uu.y * uu.y + vv.y * vv.y) * inv2c);
+            }
+        }
+        __syncthreads();
+        const float2 *Y = fft_passes_ct<LC, 5>(P2, A, TW, false);
+        ring_f32_output(Y, f2, d, b, j2, Lp, L, rw);
+        return;
+    }
     const float2 *G;
     if constexpr (LC > 0) G = fft_passes_ct<LC, 4>(X, S, TW, true);
     else G = fft_passes(X, S, 4, Lp, plan, TW, true);
 
-    const float fN = rw[4 * j2], inv2c = rw[4 * j2 + 1];
-    float2 *gs = gstore ? gstore + (static_cast<size_t>(b) * d.J2 + j2) * 4 * L : nullptr;
     for (int k = threadIdx.x; k < L; k += blockDim.x) {
         const int kp = fpad(k);
         const float2 zz = G[G_ZETA * Lp + kp], pp = G[G_PHI * Lp + kp];
@@ -312,20 +382,7 @@ __global__ void __launch_bounds__(256) k2_ring_f32(const float2 *__restrict__ f1
     if constexpr (LC > 0) Y = fft_passes_ct<LC, 5>(X, S, TW, false);
     else Y = fft_passes(X, S, 5, Lp, plan, TW, false);
 
-    const float wt = rw[4 * j2 + 2], wp = rw[4 * j2 + 3];
-    const float half_invL = 0.5f / float(L);
-    for (int i = threadIdx.x; i < 5 * (T + 1); i += blockDim.x) {
-        const int g = i / (T + 1), m = i - g * (T + 1);
-        const float2 y = Y[g * Lp + fpad(m)];
-        float2 yc = Y[g * Lp + fpad(m == 0 ? 0 : L - m)];
-        yc.y = -yc.y;
-        const float2 gn = cscale<float>(cadd<float>(y, yc), half_invL);
-        const float2 gsx = cscale<float>(mul_mi<float>(csub<float>(y, yc)), half_invL);
-        const float wg = (g == P_E) ? wp : wt;
-        float2 *o = f2 + ((static_cast<size_t>(b) * (T + 1) + m) * 5 + g) * 2 * d.J2 + j2;
-        o[0] = cscale<float>(cadd<float>(gn, gsx), wg);
-        o[d.J2] = cscale<float>(csub<float>(gn, gsx), wg);
-    }
+    ring_f32_output(Y, f2, d, b, j2, Lp, L, rw);
 }
 
 // ---------------------------------------------------------------------------
@@ -405,7 +462,7 @@ __host__ inline size_t synthesis_f32_smem(const Dims &d, int nstages, int nf = 4
 }
 
 // NF = 4: the synthesis (coefficients prepared from the FP64 states, output
-// F1[b][j][f][parity][m]).  NF = 5: the transpose of the analysis projection
+// F1[b][j][m][parity][f]).  NF = 5: the transpose of the analysis projection
 // in the adjoint (coefficients = the rows Y-bar[b][e][5], output
 // W-bar[b][j][g][parity][m], the layout the FP32 ring transpose reads).
 template <int S, int NF>
@@ -545,12 +602,12 @@ __global__ void __launch_bounds__(256) k1_synthesis_f32(const double2 *__restric
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
                         if (j0 + k >= d.J2) break;
-                        float2 *o = f1 + (static_cast<size_t>(b) * d.J2 + j0 + k) * (4 * 2 * (T + 1)) + m;
-#pragma unroll
-                        for (int f = 0; f < 4; ++f) {
-                            o[(f * 2 + 0) * (T + 1)] = ae[f][k];
-                            o[(f * 2 + 1) * (T + 1)] = ao[f][k];
-                        }
+                        float4 *o = reinterpret_cast<float4 *>(
+                            f1 + (static_cast<size_t>(b) * d.J2 + j0 + k) * (4 * 2 * (T + 1)) + 8 * m);
+                        o[0] = make_float4(ae[0][k].x, ae[0][k].y, ae[1][k].x, ae[1][k].y);
+                        o[1] = make_float4(ae[2][k].x, ae[2][k].y, ae[3][k].x, ae[3][k].y);
+                        o[2] = make_float4(ao[0][k].x, ao[0][k].y, ao[1][k].x, ao[1][k].y);
+                        o[3] = make_float4(ao[2][k].x, ao[2][k].y, ao[3][k].x, ao[3][k].y);
                     }
                 } else {
 #pragma unroll
@@ -629,7 +686,7 @@ __host__ inline bool synthesis_nb_fits(const Dims &d, int nb, int nf) {
 }
 
 // NF = 4: the synthesis (coefficients prepared from the FP64 states, output
-// F1[b][j][f][parity][m]).  NF = 5: the transpose of the analysis projection
+// F1[b][j][m][parity][f]).  NF = 5: the transpose of the analysis projection
 // in the adjoint (coefficients = the rows Y-bar[b][e][5], gathered with
 // cp.async; output W-bar[b][j][g][parity][m]).
 // FP32-pair ("double-float") arithmetic of the on-the-fly Legendre
@@ -893,10 +950,17 @@ __global__ void __launch_bounds__(kSynNbMaxThreads, 1)
 #pragma unroll
                     for (int b = 0; b < NB; ++b) {
                         if (b >= nbv) break;
-                        float2 *o = f1 + (static_cast<size_t>(b0 + b) * d.J2 + j0 + k) * (NF * 2 * (T + 1)) +
-                                    par * (T + 1) + m;
+                        if constexpr (NF == 4) {         // F1[b][j][m][parity][f]: one 32-byte sector per store pair
+                            float4 *o = reinterpret_cast<float4 *>(
+                                f1 + (static_cast<size_t>(b0 + b) * d.J2 + j0 + k) * (8 * (T + 1)) + (2 * m + par) * 4);
+                            o[0] = make_float4(a[b][0][k].x, a[b][0][k].y, a[b][1][k].x, a[b][1][k].y);
+                            o[1] = make_float4(a[b][2][k].x, a[b][2][k].y, a[b][3][k].x, a[b][3][k].y);
+                        } else {
+                            float2 *o = f1 + (static_cast<size_t>(b0 + b) * d.J2 + j0 + k) * (NF * 2 * (T + 1)) +
+                                        par * (T + 1) + m;
 #pragma unroll
-                        for (int f = 0; f < NF; ++f) o[f * 2 * (T + 1)] = a[b][f][k];
+                            for (int f = 0; f < NF; ++f) o[f * 2 * (T + 1)] = a[b][f][k];
+                        }
                     }
                 }
             }

@@ -225,7 +225,11 @@ def test_zero_steps_and_counters():
     e1, s1, l1 = s.counters()
     assert e1 - e0 == 3 * (1 + (K - 1) * M)          # Table 1
     assert s1 - s0 == 3 * ((K - 1) * M + 1)
-    assert s.launches_per_step() == 4 * K             # K tendency batches x 3 kernels + K sweeps (epilogue inside)
+    # E0 (one state, 3 kernels), K - 1 batches of M states split into two
+    # concurrent chains of 3 kernels each, and K sweeps (epilogue inside)
+    assert s.launches_per_step() == 3 + 6 * (K - 1) + K
+    s.set_chains(1)
+    assert s.launches_per_step() == 4 * K             # K tendency batches x 3 kernels + K sweeps
 
 
 def test_invalid_shapes_raise():
