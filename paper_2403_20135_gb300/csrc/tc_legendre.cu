@@ -362,9 +362,10 @@ __global__ void k2_split_w(TcTables tc, Dims d, int B, int nbc, const float2 *__
         const int b = c / 10;
         live[cp] = b < B;
         const int bb = live[cp] ? b : 0, gg = live[cp] ? (c - 10 * b) / 2 : 0;
-        const float2 *src = f2 + ((static_cast<size_t>(bb) * (T + 1) + m) * 5 + gg) * 2 * J2 + p * J2;
+        // F2[b][m][j][g][parity]: latitude stride of ten values
+        const float2 *src = f2 + (static_cast<size_t>(bb) * (T + 1) + m) * J2 * 10 + gg * 2 + p;
 #pragma unroll
-        for (int kr = 0; kr < 8; ++kr) w[cp][kr] = src[min(kb * 8 + kr, J2 - 1)];
+        for (int kr = 0; kr < 8; ++kr) w[cp][kr] = src[static_cast<size_t>(min(kb * 8 + kr, J2 - 1)) * 10];
     }
     float v[8][8];                              // [column in block][latitude in k block]
 #pragma unroll

@@ -248,12 +248,18 @@ __global__ void k2_ring(const V2<R> *__restrict__ f1, V2<R> *__restrict__ f2, Di
 // ---------------------------------------------------------------------------
 
 // Unpack of the forward transforms of the north (real part) and south
-// (imaginary part) rings, weighting and store of F2[b][m][g][parity][j2].
-__device__ __forceinline__ void ring_f32_output(const float2 *Y, float2 *__restrict__ f2, const Dims &d, int b, int j2,
-                                                int Lp, int L, const float *__restrict__ rw) {
+// (imaginary part) rings, weighting and store of F2[b][m][j2][g][parity]
+// (FP32 layout: the ten values of one (m, j2) are 80 contiguous bytes).  The
+// values are staged as [m][g][parity] in the free scratch array Z, then
+// written out by consecutive lanes, so that a warp's store covers whole
+// sectors instead of one 8-byte piece per sector.
+__device__ __forceinline__ void ring_f32_output(const float2 *Y, float2 *Z, float2 *__restrict__ f2, const Dims &d,
+                                                int b, int j2, int Lp, int L, const float *__restrict__ rw) {
     const int T = d.T;
     const float wt = rw[4 * j2 + 2], wp = rw[4 * j2 + 3];
     const float half_invL = 0.5f / float(L);
+    float4 *z4 = reinterpret_cast<float4 *>(Z);
+    const bool al16 = (reinterpret_cast<uintptr_t>(Z) & 15) == 0;   // odd padded lengths: Z on an 8-byte boundary
     for (int i = threadIdx.x; i < 5 * (T + 1); i += blockDim.x) {
         const int g = i / (T + 1), m = i - g * (T + 1);
         const float2 y = Y[g * Lp + fpad(m)];
@@ -262,9 +268,19 @@ __device__ __forceinline__ void ring_f32_output(const float2 *Y, float2 *__restr
         const float2 gn = cscale<float>(cadd<float>(y, yc), half_invL);
         const float2 gsx = cscale<float>(mul_mi<float>(csub<float>(y, yc)), half_invL);
         const float wg = (g == P_E) ? wp : wt;
-        float2 *o = f2 + ((static_cast<size_t>(b) * (T + 1) + m) * 5 + g) * 2 * d.J2 + j2;
-        o[0] = cscale<float>(cadd<float>(gn, gsx), wg);
-        o[d.J2] = cscale<float>(csub<float>(gn, gsx), wg);
+        const float2 ev = cscale<float>(cadd<float>(gn, gsx), wg), od = cscale<float>(csub<float>(gn, gsx), wg);
+        if (al16) {
+            z4[m * 5 + g] = make_float4(ev.x, ev.y, od.x, od.y);
+        } else {
+            Z[(m * 5 + g) * 2] = ev;
+            Z[(m * 5 + g) * 2 + 1] = od;
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 5 * (T + 1); i += blockDim.x) {
+        const int m = i / 5, g = i - m * 5;
+        const float4 v = al16 ? z4[i] : make_float4(Z[2 * i].x, Z[2 * i].y, Z[2 * i + 1].x, Z[2 * i + 1].y);
+        reinterpret_cast<float4 *>(f2 + ((static_cast<size_t>(b) * (T + 1) + m) * d.J2 + j2) * 10)[g] = v;
     }
 }
 
@@ -353,7 +369,7 @@ __global__ void __launch_bounds__(256) k2_ring_f32(const float2 *__restrict__ f1
         }
         __syncthreads();
         const float2 *Y = fft_passes_ct<LC, 5>(P2, A, TW, false);
-        ring_f32_output(Y, f2, d, b, j2, Lp, L, rw);
+        ring_f32_output(Y, Y == P2 ? A : P2, f2, d, b, j2, Lp, L, rw);
         return;
     }
     const float2 *G;
@@ -382,7 +398,7 @@ __global__ void __launch_bounds__(256) k2_ring_f32(const float2 *__restrict__ f1
     if constexpr (LC > 0) Y = fft_passes_ct<LC, 5>(X, S, TW, false);
     else Y = fft_passes(X, S, 5, Lp, plan, TW, false);
 
-    ring_f32_output(Y, f2, d, b, j2, Lp, L, rw);
+    ring_f32_output(Y, Y == X ? S : X, f2, d, b, j2, Lp, L, rw);
 }
 
 // ---------------------------------------------------------------------------
@@ -995,38 +1011,40 @@ constexpr int kPrjMaxThreads = 288;   // two blocks per SM fit the register file
 // order), Y[b][e][g].  NF = 4: the transpose of the synthesis in the adjoint,
 // W = F1-bar[b][j][f][parity][m] gathered per order into the same
 // [f][parity][j] arrangement, Z-bar[b][e][f].
+// W rows in shared memory: J2 latitudes padded by 2 (J2 even: rows stay on
+// 16-byte boundaries, and the transposing stage of the FP32 F2 layout writes
+// ten neighbouring values of one latitude to ten different bank groups).
+__host__ __device__ inline int project_f32_wstride(int J2) { return J2 % 2 == 0 ? J2 + 2 : J2; }
+
 template <bool VEC, bool ASYNC, int NF>
 __global__ void __launch_bounds__(kPrjMaxThreads, 2) k3_project_f32(const float2 *__restrict__ src, Dims d,
                                                       const float *__restrict__ pbar, float2 *__restrict__ y) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float2 *ws = reinterpret_cast<float2 *>(smem_raw);   // [2][2 NF][J2]
-    float4 *pst = reinterpret_cast<float4 *>(ws + 2 * 2 * NF * d.J2);   // [kPrjDepth][4 rows][blockDim] (ASYNC)
-    const int T = d.T, J2 = d.J2;
+    const int T = d.T, J2 = d.J2, JW = project_f32_wstride(d.J2);
+    float2 *ws = reinterpret_cast<float2 *>(smem_raw);   // [2][2 NF][JW]
+    float4 *pst = reinterpret_cast<float4 *>(ws + 2 * 2 * NF * JW);   // [kPrjDepth][4 rows][blockDim] (ASYNC)
     const int b = blockIdx.x;
     const int m1 = blockIdx.y, m2 = T - blockIdx.y;
     const int norders = (m2 > m1) ? 2 : 1;
     for (int h = 0; h < norders; ++h) {
-        float2 *dst = ws + h * 2 * NF * J2;
+        float2 *dst = ws + h * 2 * NF * JW;
         const int mh = h ? m2 : m1;
-        if constexpr (NF == 5) {
+        if constexpr (NF == 5) {                          // F2[b][m][j][g][parity] -> [g][parity][j]
             const float2 *w = src + (static_cast<size_t>(b) * (T + 1) + mh) * 10 * J2;
-            if (VEC) {                                    // 10 J2 float2 = 5 J2 16-byte pieces, asynchronous
-                for (int i = threadIdx.x; i < 5 * J2; i += blockDim.x) cp_async16(dst + 2 * i, w + 2 * i);
-            } else {
-                for (int i = threadIdx.x; i < 10 * J2; i += blockDim.x) dst[i] = w[i];
+            for (int i = threadIdx.x; i < 10 * J2; i += blockDim.x) {
+                const int j = i / 10, gp = i - j * 10;
+                cp_async8(dst + gp * JW + j, w + i);
             }
         } else {                                          // gather (f, parity) columns of order mh, 8 bytes each
             const float2 *w = src + static_cast<size_t>(b) * J2 * 8 * (T + 1) + mh;
             for (int i = threadIdx.x; i < 8 * J2; i += blockDim.x) {
                 const int fp = i / J2, j = i - fp * J2;
-                cp_async8(dst + i, w + (static_cast<size_t>(j) * 8 + fp) * (T + 1));
+                cp_async8(dst + fp * JW + j, w + (static_cast<size_t>(j) * 8 + fp) * (T + 1));
             }
         }
     }
-    if (VEC || NF != 5) {
-        cp_async_commit();
-        cp_async_wait<0>();
-    }
+    cp_async_commit();
+    cp_async_wait<0>();
     __syncthreads();
     // quads of (m1, p=0), (m1, p=1), (m2, p=0), (m2, p=1)
     auto quads_of = [&](int m, int p) { return ((T + 3 - m - p) / 2 + 3) / 4; };
@@ -1048,7 +1066,7 @@ __global__ void __launch_bounds__(kPrjMaxThreads, 2) k3_project_f32(const float2
         const float *pr[4];
 #pragma unroll
         for (int r = 0; r < 4; ++r) pr[r] = pbar + static_cast<size_t>(e0 + 2 * min(r, nr - 1)) * d.J2p;
-        const float2 *W = ws + h * 2 * NF * J2 + p * J2;
+        const float2 *W = ws + h * 2 * NF * JW + p * JW;
         float2 acc[4][NF];
 #pragma unroll
         for (int r = 0; r < 4; ++r)
@@ -1084,8 +1102,8 @@ __global__ void __launch_bounds__(kPrjMaxThreads, 2) k3_project_f32(const float2
                 }
 #pragma unroll
                 for (int g = 0; g < NF; ++g) {
-                    const float4 wa = *reinterpret_cast<const float4 *>(W + g * 2 * J2 + j);
-                    const float4 wb = *reinterpret_cast<const float4 *>(W + g * 2 * J2 + j + 2);
+                    const float4 wa = *reinterpret_cast<const float4 *>(W + g * 2 * JW + j);
+                    const float4 wb = *reinterpret_cast<const float4 *>(W + g * 2 * JW + j + 2);
 #pragma unroll
                     for (int r = 0; r < 4; ++r) {
                         acc[r][g] = caxpy(pv[r][0], make_float2(wa.x, wa.y), acc[r][g]);
@@ -1102,7 +1120,7 @@ __global__ void __launch_bounds__(kPrjMaxThreads, 2) k3_project_f32(const float2
             for (int r = 0; r < 4; ++r) pv[r] = pr[r][j];
 #pragma unroll
             for (int g = 0; g < NF; ++g) {
-                const float2 w = W[g * 2 * J2 + j];
+                const float2 w = W[g * 2 * JW + j];
 #pragma unroll
                 for (int r = 0; r < 4; ++r) {
                     acc[r][g].x = fmaf(pv[r], w.x, acc[r][g].x);
@@ -1134,7 +1152,7 @@ __global__ void __launch_bounds__(kPrjMaxThreads, 2) k3_project_f32(const float2
 // shared memory of a K3a (FP32) block; the per-lane cp.async stages are
 // used when the W rows leave room for them (and J2 is even)
 static bool project_f32_async(const Dims &d, int nthreads, size_t *bytes, int nf = 5) {
-    const size_t w = 2 * 2 * static_cast<size_t>(nf) * d.J2 * sizeof(float2);
+    const size_t w = 2 * 2 * static_cast<size_t>(nf) * project_f32_wstride(d.J2) * sizeof(float2);
     const size_t st = static_cast<size_t>(kPrjDepth) * 4 * nthreads * sizeof(float4);
     const bool async = d.J2 % 2 == 0 && w + st <= 200 * 1024;
     *bytes = async ? w + st : w;
