@@ -135,7 +135,17 @@ typedef enum {
      * the results are the same.  The tensor-core modes stay on one chain.
      * Any other value returns SDC_EINVAL; changing it drops the captured
      * graphs. */
-    SDC_OPT_CHAINS = 5
+    SDC_OPT_CHAINS = 5,
+    /* Programmatic dependent launch inside the captured step and retape
+     * graphs: 1 (default) launches the sweep and the FP32 synthesis, ring and
+     * projection kernels as programmatic dependents of their predecessors, so
+     * that their launch overlaps the predecessor's last blocks; a kernel does
+     * only the work that needs none of its predecessors' results (table and
+     * twiddle prefetch, barrier set-up) before it waits for their completion,
+     * so the results are the same.  0 launches every kernel after its
+     * predecessor has completed.  Any other value returns SDC_EINVAL; changing
+     * it drops the captured graphs. */
+    SDC_OPT_PDL = 6
 } sdc_option;
 enum {
     SDC_LEGENDRE_TABLE = 0,

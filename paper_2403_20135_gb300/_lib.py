@@ -22,6 +22,7 @@ SDC_QDELTA_CLAMPED, SDC_QDELTA_LITERAL, SDC_QDELTA_MIN_SR_NS, SDC_QDELTA_IMPLICI
 SDC_METHOD_DSDC, SDC_METHOD_SERIAL_SDC, SDC_METHOD_IMEX2 = 0, 1, 2
 SDC_OPT_LEGENDRE = 4
 SDC_OPT_CHAINS = 5
+SDC_OPT_PDL = 6
 SDC_LEGENDRE_TABLE, SDC_LEGENDRE_RECURRENCE = 0, 1
 
 

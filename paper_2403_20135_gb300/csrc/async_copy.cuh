@@ -71,4 +71,14 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
+// Programmatic dependent launch (griddepcontrol): a kernel launched with the
+// programmatic-serialisation attribute is scheduled as its predecessor in the
+// stream retires; pdl_wait() returns once every prerequisite grid has
+// completed and its memory is visible (at once when there is none).  No
+// kernel here signals its dependents early (launch_dependents): dependents
+// that start early hold shared memory and registers while they wait, which
+// measured slower on these kernels than letting them start as the
+// predecessor's blocks exit.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 }  // namespace sdc

@@ -58,6 +58,7 @@ struct sdc_ctx {
     cudaStream_t cap2 = nullptr;         // second capture stream: the other chain of a split batch
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int chains = 2;                      // SDC_OPT_CHAINS
+    int pdl = 1;                         // SDC_OPT_PDL
     std::vector<double> mu, w, tau, Q;
     std::vector<double> qd_min_sr_s;     // MIN-SR-S diagonal, computed when that rule is selected
 
@@ -197,7 +198,8 @@ cudaError_t tendency(sdc_ctx *c, int B, const double2 *states, long long sstride
                      long long tstride, cudaStream_t s, int *launches, StageTimer *timer = nullptr,
                      void *grid_store = nullptr) {
     const bool fp32 = c->precision != SDC_FP64;
-    const DeviceTables tb = tables(c);
+    DeviceTables tb = tables(c);
+    tb.pdl = c->pdl != 0 && s == c->cap && !timer;        // inside a captured step or retape graph
     Workspace ws{c->f1, c->f2, c->f3};
     const bool use_tc = c->precision == SDC_MIXED_BF16X3 || c->precision == SDC_MIXED_BF16X6;
     // Two chains (SDC_OPT_CHAINS): while a graph is captured, the states of
@@ -342,6 +344,7 @@ cudaError_t enqueue_step(sdc_ctx *c, cudaStream_t s, bool with_resid, int *launc
     for (int m = 0; m < M; ++m)
         for (int j = 0; j < M; ++j) p.Q[m][j] = c->dt * c->Q[m * M + j];
     p.resid_part = with_resid ? c->resid_part : nullptr;
+    p.pdl = (c->pdl != 0 && s == c->cap && !timer) ? 1 : 0;
 
     for (int k = 0; k < K; ++k) {             // sweep k+1
         const bool first = (k == 0), last = (k == K - 1);
@@ -906,6 +909,17 @@ int sdc_set_option(sdc_ctx *c, int key, int value) {
         if (value != c->chains) {
             SDC_CUDA(cudaStreamSynchronize(c->stream));
             c->chains = value;
+            for (auto &g : c->graph)
+                if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+            if (c->graph_retape) { cudaGraphExecDestroy(c->graph_retape); c->graph_retape = nullptr; }
+        }
+        return SDC_OK;
+    }
+    if (key == SDC_OPT_PDL) {
+        if (value != 0 && value != 1) return fail(SDC_EINVAL, "pdl must be 0 or 1");
+        if (value != c->pdl) {
+            SDC_CUDA(cudaStreamSynchronize(c->stream));
+            c->pdl = value;
             for (auto &g : c->graph)
                 if (g) { cudaGraphExecDestroy(g); g = nullptr; }
             if (c->graph_retape) { cudaGraphExecDestroy(c->graph_retape); c->graph_retape = nullptr; }

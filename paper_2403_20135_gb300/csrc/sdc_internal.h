@@ -72,6 +72,7 @@ struct SweepParams {
     double phibar;
     double Q[kMaxNodes][kMaxNodes];   // dt * q_{m,j}
     double alpha[kMaxNodes];      // dt * q^Delta_{m,m}
+    int pdl;                      // launched as a programmatic dependent
 };
 
 // One node update of serial IMEX SDC (Algorithm 1, Eq. (6)).
@@ -134,10 +135,37 @@ struct DeviceTables {
     FftPlan plan16;        // FP32 ring: passes of radix 16, then 8/4/2, then 3
     const float2 *twp32;   // FP32 ring: per-pass twiddles of plan16 (after the first pass)
     int ntwp;
+    bool pdl;              // launch the FP32 synthesis, ring and projection as programmatic dependents
 };
 
 // Transform workspaces (elements of the transform precision):
-// f1 [B][J2][4][2][T+1], f2 [B][T+1][5][2][J2], f3 [B][next][5] complex.
+// f1 [B][J2][4][2][T+1] (FP32: [B][J2][T+1][2][4]), f2 [B][T+1][5][2][J2]
+// (FP32: [B][T+1][J2][5][2]), f3 [B][next][5] complex.
+#ifdef __CUDACC__
+// Launch of kernel k, as a programmatic dependent of the preceding kernel in
+// the stream when pdl is set (the kernel must call pdl_wait() before it
+// touches anything its predecessors write).
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_k(bool pdl, void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                            Args... args) {
+    if (!pdl) {
+        k<<<grid, block, smem, s>>>(args...);
+        return cudaSuccess;
+    }
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k, static_cast<KArgs>(args)...);
+}
+#endif
+
 struct Workspace {
     void *f1, *f2, *f3;
 };

@@ -21,6 +21,7 @@
 // times the warps of a thread-per-mode layout to hide its latency.
 #include <cuda_runtime.h>
 
+#include "async_copy.cuh"
 #include "epilogue.cuh"
 #include "sdc_internal.h"
 
@@ -40,6 +41,7 @@ __device__ __forceinline__ double2 shfl2(double2 v, int src) {
 
 template <int M, bool RESID, typename R>
 __global__ void __launch_bounds__(kSweepThreads) k4_sweep(SweepParams p) {
+    pdl_wait();                                           // everything below reads the preceding kernels' results
     constexpr int G = sweep_lanes(M);
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int nc = p.ncoef;
@@ -153,10 +155,11 @@ __global__ void k5_resid_reduce(const double *__restrict__ part, int nblocks, in
 template <typename R>
 static cudaError_t launch_sweep_t(const SweepParams &p, int M, cudaStream_t s) {
     const int nb = sweep_blocks(p.ncoef, M);
-#define SDC_SWEEP_CASE(MM)                                                           \
-    case MM:                                                                         \
-        if (p.resid_part) k4_sweep<MM, true, R><<<nb, kSweepThreads, 0, s>>>(p);     \
-        else k4_sweep<MM, false, R><<<nb, kSweepThreads, 0, s>>>(p);                 \
+    cudaError_t e = cudaSuccess;
+#define SDC_SWEEP_CASE(MM)                                                                               \
+    case MM:                                                                                             \
+        if (p.resid_part) e = launch_k(p.pdl != 0, k4_sweep<MM, true, R>, dim3(nb), dim3(kSweepThreads), 0, s, p); \
+        else e = launch_k(p.pdl != 0, k4_sweep<MM, false, R>, dim3(nb), dim3(kSweepThreads), 0, s, p);             \
         break;
     switch (M) {
         SDC_SWEEP_CASE(1) SDC_SWEEP_CASE(2) SDC_SWEEP_CASE(3) SDC_SWEEP_CASE(4)
@@ -164,6 +167,7 @@ static cudaError_t launch_sweep_t(const SweepParams &p, int M, cudaStream_t s) {
         default: return cudaErrorInvalidValue;
     }
 #undef SDC_SWEEP_CASE
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 

@@ -301,18 +301,20 @@ __global__ void __launch_bounds__(256) k2_ring_f32(const float2 *__restrict__ f1
     // S and the pass twiddles into TW, all copies in flight at once
     const float2 *in = f1 + (static_cast<size_t>(b) * d.J2 + j2) * (4 * 2 * (T + 1));
     float2 *raw = S;                                     // 8 (T + 1) <= 5 Lp elements
-    if ((Lp & 1) == 0) {                                 // S starts on a 16-byte boundary
-        for (int q = threadIdx.x; q < 4 * (T + 1); q += blockDim.x) cp_async16(raw + 2 * q, in + 2 * q);
-    } else {
-        for (int q = threadIdx.x; q < 8 * (T + 1); q += blockDim.x) cp_async8(raw + q, in + q);
-    }
+    // twiddles and the zero band first: they need nothing of the synthesis
     for (int k = threadIdx.x; k < ntw; k += blockDim.x) cp_async8(TW + k, twp + k);
-    cp_async_commit();
     const int gap = L - 2 * T - 1;
     for (int i = threadIdx.x; i < 4 * gap; i += blockDim.x) {
         const int f = i / gap, k = T + 1 + (i - f * gap);
         X[f * Lp + fpad(k)] = make_float2(0.f, 0.f);
     }
+    pdl_wait();
+    if ((Lp & 1) == 0) {                                 // S starts on a 16-byte boundary
+        for (int q = threadIdx.x; q < 4 * (T + 1); q += blockDim.x) cp_async16(raw + 2 * q, in + 2 * q);
+    } else {
+        for (int q = threadIdx.x; q < 8 * (T + 1); q += blockDim.x) cp_async8(raw + q, in + q);
+    }
+    cp_async_commit();
     cp_async_wait<0>();
     __syncthreads();
     for (int i = threadIdx.x; i < 4 * (T + 1); i += blockDim.x) {
@@ -789,6 +791,11 @@ __global__ void __launch_bounds__(kSynNbMaxThreads, 1)
     if (NF == 4 && threadIdx.x == 0) {
         for (int k = 0; k <= kMaxSynStages; ++k) mbar_init(&mbar[k], 1);
         mbar_init_fence();
+        // the table stages need nothing of the preceding kernels: in flight
+        // before the wait for the states (programmatic dependent launch)
+        if (!REC)
+            for (; issued < min(nstages, nch); ++issued) issue(issued);
+        pdl_wait();
         const uint32_t n1b = static_cast<uint32_t>(nc1) * sizeof(double2);
         const uint32_t n2b = static_cast<uint32_t>(ncs - nc1) * sizeof(double2);
         expect_tx(mpro, static_cast<uint32_t>(nbv) * 3 * (n1b + n2b) +
@@ -802,8 +809,6 @@ __global__ void __launch_bounds__(kSynNbMaxThreads, 1)
             }
         bulk_copy(sy, syn32 + ext_offset(T, m1), static_cast<uint32_t>(nn1) * sizeof(float4), mpro);
         if (two) bulk_copy(sy + nn1, syn32 + ext_offset(T, m2), static_cast<uint32_t>(nn2) * sizeof(float4), mpro);
-        if (!REC)
-            for (; issued < min(nstages, nch); ++issued) issue(issued);
     }
     if constexpr (NF == 5) {                             // the Y-bar rows of both orders, 8 bytes per piece
         for (int i = threadIdx.x; i < rows * NB * 5; i += blockDim.x) {
@@ -1026,6 +1031,9 @@ __global__ void __launch_bounds__(kPrjMaxThreads, 2) k3_project_f32(const float2
     const int b = blockIdx.x;
     const int m1 = blockIdx.y, m2 = T - blockIdx.y;
     const int norders = (m2 > m1) ? 2 : 1;
+    if constexpr (NF == 5) {
+        pdl_wait();
+    }
     for (int h = 0; h < norders; ++h) {
         float2 *dst = ws + h * 2 * NF * JW;
         const int mh = h ? m2 : m1;
@@ -1284,6 +1292,7 @@ template <int NF>
 static cudaError_t launch_synthesis_nb(const Dims &d, int B, const double2 *states, long long sstride,
                                        const float2 *ybar, const float *pbar, const float *syn32, float2 *f1,
                                        int *err, cudaStream_t s, const DeviceTables *rec = nullptr) {
+    const bool pdl = NF == 4 && rec && rec->pdl;          // the adjoint's transpose (NF = 5) waits for nothing
     // NF = 5 keeps NB <= 2: four states' 40 accumulators and coefficient rows exceed the registers
     const int nb = B == 1 ? 1 : ((NF == 5 || B == 2 || !synthesis_nb_fits(d, 4, NF)) ? 2 : 4);
     const int S = synthesis_nb_s(d.J2);
@@ -1292,11 +1301,12 @@ static cudaError_t launch_synthesis_nb(const Dims &d, int B, const double2 *stat
     const size_t sm = synthesis_nb_smem(d, nb, NF);
     const float4 *sy = reinterpret_cast<const float4 *>(syn32);
     // the recurrence needs a thread per latitude (the block always has at least J2 + 1 threads)
+    cudaError_t e = cudaSuccess;
     if constexpr (NF == 4) {
         if (rec && rec->rec_ab && nt >= d.J2p) {
-#define SDC_SYN_REC(NBV, SV)                                                                                  \
-    k1_synthesis_f32_nb<NBV, SV, 4, true><<<g, nt, sm, s>>>(states, sstride, ybar, B, d, pbar, sy, f1, ns, err, \
-                                                             rec->rec_ab, rec->rec_seed, rec->rec_mu)
+#define SDC_SYN_REC(NBV, SV)                                                                              \
+    e = launch_k(pdl, k1_synthesis_f32_nb<NBV, SV, 4, true>, g, dim3(nt), sm, s, states, sstride, ybar, B, d, \
+                 pbar, sy, f1, ns, err, rec->rec_ab, rec->rec_seed, rec->rec_mu)
             if (S == 2) {
                 if (nb == 1) SDC_SYN_REC(1, 2);
                 else if (nb == 2) SDC_SYN_REC(2, 2);
@@ -1307,11 +1317,14 @@ static cudaError_t launch_synthesis_nb(const Dims &d, int B, const double2 *stat
                 else SDC_SYN_REC(4, 1);
             }
 #undef SDC_SYN_REC
+            if (e != cudaSuccess) return e;
             return cudaGetLastError();
         }
     }
-#define SDC_SYN_NB(NBV, SV) \
-    k1_synthesis_f32_nb<NBV, SV, NF><<<g, nt, sm, s>>>(states, sstride, ybar, B, d, pbar, sy, f1, ns, err)
+#define SDC_SYN_NB(NBV, SV)                                                                                   \
+    e = launch_k(pdl, k1_synthesis_f32_nb<NBV, SV, NF, false>, g, dim3(nt), sm, s, states, sstride, ybar, B, d, pbar, \
+                 sy, f1, ns, err, static_cast<const float4 *>(nullptr), static_cast<const float4 *>(nullptr),       \
+                 static_cast<const float2 *>(nullptr))
     if (S == 2) {
         if (nb == 1) SDC_SYN_NB(1, 2);
         else if (nb == 2) SDC_SYN_NB(2, 2);
@@ -1322,6 +1335,7 @@ static cudaError_t launch_synthesis_nb(const Dims &d, int B, const double2 *stat
         else if constexpr (NF == 4) SDC_SYN_NB(4, 1);
     }
 #undef SDC_SYN_NB
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
@@ -1372,8 +1386,10 @@ static cudaError_t launch_tendency_t(const Dims &d, const FftPlan &plan, int B, 
         const dim3 g2(d.J2, B);
         const size_t sm = ring_f32_smem_bytes(d.L, tb.ntwp);
         float2 *gsr = static_cast<float2 *>(grid_store);
-#define SDC_RING_F32(LC) \
-    k2_ring_f32<LC><<<g2, kK2Threads, sm, s>>>(f1, f2, d, tb.plan16, tb.twp32, tb.ntwp, tb.ring32, gsr)
+        cudaError_t e = cudaSuccess;
+#define SDC_RING_F32(LC)                                                                                            \
+    e = launch_k(tb.pdl, k2_ring_f32<LC>, g2, dim3(kK2Threads), sm, s, static_cast<const float2 *>(f1), f2, d, tb.plan16, \
+                 tb.twp32, tb.ntwp, tb.ring32, gsr)
         switch (d.L) {
             case 96: SDC_RING_F32(96); break;
             case 192: SDC_RING_F32(192); break;
@@ -1383,6 +1399,7 @@ static cudaError_t launch_tendency_t(const Dims &d, const FftPlan &plan, int B, 
             default: SDC_RING_F32(0); break;
         }
 #undef SDC_RING_F32
+        if (e != cudaSuccess) return e;
     } else {
         k2_ring<R><<<dim3(d.J2, B), kK2Threads, sm2, s>>>(f1, f2, d, plan, tw, tb.ring64, nscratch,
                                                          static_cast<V2<R> *>(grid_store));
@@ -1397,9 +1414,12 @@ static cudaError_t launch_tendency_t(const Dims &d, const FftPlan &plan, int B, 
             const int nt = project_f32_threads(d.T);
             size_t smp = 0;
             const bool async = project_f32_async(d, nt, &smp);
-            if (d.J2 % 2 != 0) k3_project_f32<false, false, 5><<<g3, nt, smp, s>>>(f2, d, pbar, f3);
-            else if (async) k3_project_f32<true, true, 5><<<g3, nt, smp, s>>>(f2, d, pbar, f3);
-            else k3_project_f32<true, false, 5><<<g3, nt, smp, s>>>(f2, d, pbar, f3);
+            const float2 *f2c = f2;
+            cudaError_t e;
+            if (d.J2 % 2 != 0) e = launch_k(tb.pdl, k3_project_f32<false, false, 5>, g3, dim3(nt), smp, s, f2c, d, pbar, f3);
+            else if (async) e = launch_k(tb.pdl, k3_project_f32<true, true, 5>, g3, dim3(nt), smp, s, f2c, d, pbar, f3);
+            else e = launch_k(tb.pdl, k3_project_f32<true, false, 5>, g3, dim3(nt), smp, s, f2c, d, pbar, f3);
+            if (e != cudaSuccess) return e;
             if (launches) ++*launches;
         }
     } else {

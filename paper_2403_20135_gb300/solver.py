@@ -66,6 +66,10 @@ class Solver:
         """Concurrent state chains of a tendency batch in the step graphs: 1 or 2."""
         _lib.check(self.lib.sdc_set_option(self.h, _lib.SDC_OPT_CHAINS, chains), "sdc_set_option")
 
+    def set_pdl(self, on: int):
+        """Programmatic dependent launch in the step graphs: 1 (default) or 0."""
+        _lib.check(self.lib.sdc_set_option(self.h, _lib.SDC_OPT_PDL, on), "sdc_set_option")
+
     @classmethod
     def for_workload(cls, wl, precision: int = _lib.SDC_FP64, **kw):
         import swe_inputs as si

@@ -16,6 +16,7 @@ def test_two_chains_equal_one_chain(precision):
     from paper_2403_20135_gb300 import Solver
     wl = si.Workload("c", 2, 63, 100, 192, 4, 4, 300.0, 1, 1, (100.0, 100.0))
     s1 = Solver.for_workload(wl, precision=precision)
+    s1.set_chains(1)
     s2 = Solver.for_workload(wl, precision=precision)
     s2.set_chains(2)
     u0 = s1.initial_state(wl)
@@ -27,6 +28,7 @@ def test_two_chains_equal_one_chain(precision):
     # an odd node count splits the batch unevenly
     wl3 = si.Workload("c", 2, 31, 48, 96, 3, 3, 600.0, 1, 1, (100.0, 100.0))
     t1 = Solver.for_workload(wl3, precision=precision)
+    t1.set_chains(1)
     t2 = Solver.for_workload(wl3, precision=precision)
     t2.set_chains(2)
     v0 = t1.initial_state(wl3)
