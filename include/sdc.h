@@ -129,12 +129,12 @@ typedef enum {
     SDC_OPT_LEGENDRE = 4,
     /* Concurrent state chains of a tendency batch in the captured step and
      * retape graphs: 1 runs the transforms of the batch's states as one
-     * launch per stage; 2 (default) splits the states into two halves whose
-     * transforms run on two streams inside the graph, so that one half's
-     * kernels fill the SMs the other half's leave idle.  The arithmetic and
-     * the results are the same.  The tensor-core modes stay on one chain.
-     * Any other value returns SDC_EINVAL; changing it drops the captured
-     * graphs. */
+     * launch per stage; 2 (default) to 4 split the states into that many
+     * parts (at most one per state) whose transforms run on as many streams
+     * inside the graph, so that one part's kernels fill the SMs the others'
+     * leave idle.  The arithmetic and the results are the same.  The
+     * tensor-core modes stay on one chain.  Any other value returns
+     * SDC_EINVAL; changing it drops the captured graphs. */
     SDC_OPT_CHAINS = 5,
     /* Programmatic dependent launch inside the captured step and retape
      * graphs: 1 (default) launches the sweep and the FP32 synthesis, ring and

@@ -55,8 +55,8 @@ struct sdc_ctx {
     FftPlan plan{};
     cudaStream_t stream = nullptr;       // caller's stream
     cudaStream_t cap = nullptr;          // private stream used for graph capture
-    cudaStream_t cap2 = nullptr;         // second capture stream: the other chain of a split batch
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaStream_t capx[kMaxChains - 1] = {};   // extra capture streams: the other chains of a split batch
+    cudaEvent_t ev_fork = nullptr, ev_join[kMaxChains - 1] = {};
     int chains = 2;                      // SDC_OPT_CHAINS
     int pdl = 1;                         // SDC_OPT_PDL
     std::vector<double> mu, w, tau, Q;
@@ -125,9 +125,11 @@ void free_ctx(sdc_ctx *c) {
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->cap) cudaStreamDestroy(c->cap);
-    if (c->cap2) cudaStreamDestroy(c->cap2);
+    for (auto &x : c->capx)
+        if (x) cudaStreamDestroy(x);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
-    if (c->ev_join) cudaEventDestroy(c->ev_join);
+    for (auto &x : c->ev_join)
+        if (x) cudaEventDestroy(x);
     delete c;
 }
 
@@ -202,34 +204,38 @@ cudaError_t tendency(sdc_ctx *c, int B, const double2 *states, long long sstride
     tb.pdl = c->pdl != 0 && s == c->cap && !timer;        // inside a captured step or retape graph
     Workspace ws{c->f1, c->f2, c->f3};
     const bool use_tc = c->precision == SDC_MIXED_BF16X3 || c->precision == SDC_MIXED_BF16X6;
-    // Two chains (SDC_OPT_CHAINS): while a graph is captured, the states of
-    // the batch are split into two halves whose transforms run on two
-    // streams, so that the kernels of one half fill the SMs the other half's
-    // kernels leave idle (tails, order-pair grids smaller than the GPU).  Every
-    // kernel indexes its workspaces by the state, so the second half runs on
-    // the same buffers offset by its first state.  The tensor-core modes
-    // share their split operands across the batch and stay on one chain.
-    if (c->chains == 2 && B >= 2 && s == c->cap && !timer && !use_tc) {
+    // Chains (SDC_OPT_CHAINS): while a graph is captured, the states of the
+    // batch are split into up to `chains` parts whose transforms run on as
+    // many streams, so that the kernels of one part fill the SMs the others'
+    // kernels leave idle (tails, order-pair grids smaller than the GPU).
+    // Every kernel indexes its workspaces by the state, so part k runs on the
+    // same buffers offset by its first state.  The tensor-core modes share
+    // their split operands across the batch and stay on one chain.
+    if (c->chains >= 2 && B >= 2 && s == c->cap && !timer && !use_tc) {
         const Dims &d = c->d;
-        const int B1 = B / 2, B2 = B - B1;
+        const int nch = c->chains < B ? c->chains : B;
         const size_t elem = fp32 ? sizeof(float2) : sizeof(double2);
         const size_t f1s = static_cast<size_t>(d.J2) * 8 * (d.T + 1) * elem;
         const size_t f2s = static_cast<size_t>(d.T + 1) * 10 * d.J2 * elem;
         const size_t f3s = static_cast<size_t>(d.next) * 5 * elem;
         const size_t gss = static_cast<size_t>(d.J2) * 4 * d.L * elem;
-        Workspace ws2{static_cast<char *>(c->f1) + B1 * f1s, static_cast<char *>(c->f2) + B1 * f2s,
-                      static_cast<char *>(c->f3) + B1 * f3s};
         cudaError_t e = cudaEventRecord(c->ev_fork, s);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(c->cap2, c->ev_fork, 0);
-        if (e == cudaSuccess)
-            e = launch_tendency(d, c->plan, fp32, B1, states, sstride, tend, tstride, tb, ws, s, launches, nullptr,
-                                grid_store, nullptr);
-        if (e == cudaSuccess)
-            e = launch_tendency(d, c->plan, fp32, B2, states + B1 * sstride, sstride,
-                                tend ? tend + B1 * tstride : nullptr, tstride, tb, ws2, c->cap2, launches, nullptr,
-                                grid_store ? static_cast<char *>(grid_store) + B1 * gss : nullptr, nullptr);
-        if (e == cudaSuccess) e = cudaEventRecord(c->ev_join, c->cap2);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, c->ev_join, 0);
+        for (int k = 1; k < nch && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(c->capx[k - 1], c->ev_fork, 0);
+        int b0 = 0;
+        for (int k = 0; k < nch && e == cudaSuccess; ++k) {
+            const int bk = B / nch + (k < B % nch ? 1 : 0);   // the larger parts first
+            const Workspace wk{static_cast<char *>(c->f1) + b0 * f1s, static_cast<char *>(c->f2) + b0 * f2s,
+                               static_cast<char *>(c->f3) + b0 * f3s};
+            e = launch_tendency(d, c->plan, fp32, bk, states + b0 * sstride, sstride,
+                                tend ? tend + b0 * tstride : nullptr, tstride, tb, wk, k ? c->capx[k - 1] : s,
+                                launches, nullptr, grid_store ? static_cast<char *>(grid_store) + b0 * gss : nullptr,
+                                nullptr);
+            b0 += bk;
+        }
+        for (int k = 1; k < nch && e == cudaSuccess; ++k) {
+            e = cudaEventRecord(c->ev_join[k - 1], c->capx[k - 1]);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(s, c->ev_join[k - 1], 0);
+        }
         return e;
     }
     return launch_tendency(c->d, c->plan, fp32, B, states, sstride, tend, tstride, tb, ws, s, launches, timer,
@@ -690,9 +696,9 @@ int sdc_create(sdc_ctx **out, int T, int J, int L, int M, int K, double dt, cons
     } while (0)
 
     SDC_TRY(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
-    SDC_TRY(cudaStreamCreateWithFlags(&c->cap2, cudaStreamNonBlocking));
+    for (auto &x : c->capx) SDC_TRY(cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking));
     SDC_TRY(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
-    SDC_TRY(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
+    for (auto &x : c->ev_join) SDC_TRY(cudaEventCreateWithFlags(&x, cudaEventDisableTiming));
     SDC_TRY(configure_transform_kernels(d, c->plan, precision != SDC_FP64));
     SDC_TRY(configure_adjoint_kernels(d, c->plan, precision != SDC_FP64));
     if (precision != SDC_FP64) SDC_TRY(configure_transform_kernels(d, c->plan, false));
@@ -905,7 +911,7 @@ int sdc_set_option(sdc_ctx *c, int key, int value) {
         return SDC_OK;
     }
     if (key == SDC_OPT_CHAINS) {
-        if (value != 1 && value != 2) return fail(SDC_EINVAL, "chains must be 1 or 2");
+        if (value < 1 || value > kMaxChains) return fail(SDC_EINVAL, "chains must be 1 to 4");
         if (value != c->chains) {
             SDC_CUDA(cudaStreamSynchronize(c->stream));
             c->chains = value;

@@ -35,6 +35,8 @@ struct FftPlan {
 };
 
 // Sizes handed to every transform kernel.
+constexpr int kMaxChains = 4;   // concurrent state chains of a split tendency batch (SDC_OPT_CHAINS)
+
 struct Dims {
     int T;        // truncation
     int J;        // latitudes

@@ -63,7 +63,7 @@ class Solver:
         _lib.check(self.lib.sdc_set_option(self.h, _lib.SDC_OPT_LEGENDRE, source), "sdc_set_option")
 
     def set_chains(self, chains: int):
-        """Concurrent state chains of a tendency batch in the step graphs: 1 or 2."""
+        """Concurrent state chains of a tendency batch in the step graphs: 1 to 4."""
         _lib.check(self.lib.sdc_set_option(self.h, _lib.SDC_OPT_CHAINS, chains), "sdc_set_option")
 
     def set_pdl(self, on: int):
