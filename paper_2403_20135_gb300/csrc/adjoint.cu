@@ -225,7 +225,11 @@ __global__ void k2t_ring(const V2<R> *__restrict__ wbar, const V2<R> *__restrict
 
 // K2^T in FP32 on the padded radix-16 passes of fft_pass.cuh (as the FP32
 // forward ring): LC > 0 fixes the ring length at compile time.  W-bar comes
-// in the layout [b][j2][g][parity][m] (m fastest: the fill loads coalesce).
+// in the layout [b][j2][m][parity][g] (contiguous per ring pair: one bulk
+// round of 16-byte copies; the synthesis transpose that writes it stores 40
+// contiguous bytes per (j2, m, parity)); F1-bar leaves as [b][m][j2][f][parity]
+// (64 contiguous bytes per (m, j2), read per order by the projection-shaped
+// synthesis transpose).
 template <int LC>
 __global__ void __launch_bounds__(256) k2t_ring_f32(const float2 *__restrict__ wbar, const float2 *__restrict__ gbase,
                                                     float2 *__restrict__ f1bar, Dims d, FftPlan plan,
@@ -261,9 +265,8 @@ __global__ void __launch_bounds__(256) k2t_ring_f32(const float2 *__restrict__ w
         bool conj = false;
         if (k <= T) m = k;
         else if (k >= L - T) { m = L - k; conj = true; }
-        if (m >= 0) {
-            const float2 *src = raw + g * 2 * (T + 1) + m;
-            const float2 ws = src[0], wa = src[T + 1];
+        if (m >= 0) {                                    // raw = W-bar[b][j2][m][parity][g]
+            const float2 ws = raw[m * 10 + g], wa = raw[m * 10 + 5 + g];
             const float wg = (g == P_E) ? wp : wt;
             const float sc = wg * ((m == 0) ? invL : 0.5f * invL);
             float2 gn = cscale<float>(cadd<float>(ws, wa), sc), gsth = cscale<float>(csub<float>(ws, wa), sc);
@@ -298,7 +301,11 @@ __global__ void __launch_bounds__(256) k2t_ring_f32(const float2 *__restrict__ w
     if constexpr (LC > 0) Y = fft_passes_ct<LC, 4>(X, S, TW, false);
     else Y = fft_passes(X, S, 4, Lp, plan, TW, false);
 
-    float2 *o = f1bar + (static_cast<size_t>(b) * J2 + j2) * 8 * (T + 1);
+    // F1-bar[b][m][j2][f][parity]: the values are staged as [m][f][parity] in
+    // the free scratch array, then 64 contiguous bytes per (m, j2) are written
+    // by neighbouring lanes (whole sectors instead of 8-byte pieces)
+    float2 *Z = const_cast<float2 *>(Y == X ? S : X);
+    const bool al16 = (reinterpret_cast<uintptr_t>(Z) & 15) == 0;   // odd padded lengths: Z on an 8-byte boundary
     for (int i = threadIdx.x; i < 4 * (T + 1); i += blockDim.x) {
         const int f = i / (T + 1), m = i - f * (T + 1);
         const float2 y = Y[f * Lp + fpad(m)];
@@ -309,8 +316,19 @@ __global__ void __launch_bounds__(256) k2t_ring_f32(const float2 *__restrict__ w
         const float2 fs = cscale<float>(mul_mi<float>(csub<float>(y, yc)), wm);
         float2 se = cadd<float>(fn, fs), so = csub<float>(fn, fs);
         if (m == 0) { se.y = 0.f; so.y = 0.f; }
-        o[(f * 2 + 0) * (T + 1) + m] = se;
-        o[(f * 2 + 1) * (T + 1) + m] = so;
+        if (al16) {
+            reinterpret_cast<float4 *>(Z)[m * 4 + f] = make_float4(se.x, se.y, so.x, so.y);
+        } else {
+            Z[(m * 4 + f) * 2] = se;
+            Z[(m * 4 + f) * 2 + 1] = so;
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 4 * (T + 1); i += blockDim.x) {
+        const int m = i >> 2, f = i & 3;
+        const float4 v = al16 ? reinterpret_cast<const float4 *>(Z)[i]
+                              : make_float4(Z[2 * i].x, Z[2 * i].y, Z[2 * i + 1].x, Z[2 * i + 1].y);
+        reinterpret_cast<float4 *>(f1bar + ((static_cast<size_t>(b) * (T + 1) + m) * J2 + j2) * 8)[f] = v;
     }
 }
 

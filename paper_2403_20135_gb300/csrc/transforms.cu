@@ -482,7 +482,7 @@ __host__ inline size_t synthesis_f32_smem(const Dims &d, int nstages, int nf = 4
 // NF = 4: the synthesis (coefficients prepared from the FP64 states, output
 // F1[b][j][m][parity][f]).  NF = 5: the transpose of the analysis projection
 // in the adjoint (coefficients = the rows Y-bar[b][e][5], output
-// W-bar[b][j][g][parity][m], the layout the FP32 ring transpose reads).
+// W-bar[b][j][m][parity][g], the layout the FP32 ring transpose reads).
 template <int S, int NF>
 __global__ void __launch_bounds__(256) k1_synthesis_f32(const double2 *__restrict__ states, long long sstride,
                                                         const float2 *__restrict__ ybar, Dims d,
@@ -631,11 +631,11 @@ __global__ void __launch_bounds__(256) k1_synthesis_f32(const double2 *__restric
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
                         if (j0 + k >= d.J2) break;
-                        float2 *o = f1 + (static_cast<size_t>(b) * d.J2 + j0 + k) * (5 * 2 * (T + 1)) + m;
+                        float2 *o = f1 + (static_cast<size_t>(b) * d.J2 + j0 + k) * (5 * 2 * (T + 1)) + 10 * m;
 #pragma unroll
                         for (int f = 0; f < 5; ++f) {
-                            o[(f * 2 + 0) * (T + 1)] = ae[f][k];
-                            o[(f * 2 + 1) * (T + 1)] = ao[f][k];
+                            o[f] = ae[f][k];
+                            o[5 + f] = ao[f][k];
                         }
                     }
                 }
@@ -706,7 +706,7 @@ __host__ inline bool synthesis_nb_fits(const Dims &d, int nb, int nf) {
 // NF = 4: the synthesis (coefficients prepared from the FP64 states, output
 // F1[b][j][m][parity][f]).  NF = 5: the transpose of the analysis projection
 // in the adjoint (coefficients = the rows Y-bar[b][e][5], gathered with
-// cp.async; output W-bar[b][j][g][parity][m]).
+// cp.async; output W-bar[b][j][m][parity][g]: one store run of 40 bytes per (j, m, parity)).
 // FP32-pair ("double-float") arithmetic of the on-the-fly Legendre
 // recurrence: a value is hi + lo with |lo| <= ulp(hi) / 2.  The products use
 // the FMA error-free transformation of the product, the sum Knuth's
@@ -976,11 +976,11 @@ __global__ void __launch_bounds__(kSynNbMaxThreads, 1)
                                 f1 + (static_cast<size_t>(b0 + b) * d.J2 + j0 + k) * (8 * (T + 1)) + (2 * m + par) * 4);
                             o[0] = make_float4(a[b][0][k].x, a[b][0][k].y, a[b][1][k].x, a[b][1][k].y);
                             o[1] = make_float4(a[b][2][k].x, a[b][2][k].y, a[b][3][k].x, a[b][3][k].y);
-                        } else {
+                        } else {                         // W-bar[b][j][m][parity][g]: 40 contiguous bytes
                             float2 *o = f1 + (static_cast<size_t>(b0 + b) * d.J2 + j0 + k) * (NF * 2 * (T + 1)) +
-                                        par * (T + 1) + m;
+                                        (2 * m + par) * NF;
 #pragma unroll
-                            for (int f = 0; f < NF; ++f) o[f * 2 * (T + 1)] = a[b][f][k];
+                            for (int f = 0; f < NF; ++f) o[f] = a[b][f][k];
                         }
                     }
                 }
@@ -1014,7 +1014,7 @@ constexpr int kPrjMaxThreads = 288;   // two blocks per SM fit the register file
 // involved because a lane only reads what it copied.
 // NF = 5: the analysis projection, W = F2[b][m][g][parity][j] (contiguous per
 // order), Y[b][e][g].  NF = 4: the transpose of the synthesis in the adjoint,
-// W = F1-bar[b][j][f][parity][m] gathered per order into the same
+// W = F1-bar[b][m][j][f][parity] (contiguous per order) staged into the same
 // [f][parity][j] arrangement, Z-bar[b][e][f].
 // W rows in shared memory: J2 latitudes padded by 2 (J2 even: rows stay on
 // 16-byte boundaries, and the transposing stage of the FP32 F2 layout writes
@@ -1043,11 +1043,11 @@ __global__ void __launch_bounds__(kPrjMaxThreads, 2) k3_project_f32(const float2
                 const int j = i / 10, gp = i - j * 10;
                 cp_async8(dst + gp * JW + j, w + i);
             }
-        } else {                                          // gather (f, parity) columns of order mh, 8 bytes each
-            const float2 *w = src + static_cast<size_t>(b) * J2 * 8 * (T + 1) + mh;
+        } else {                                          // F1-bar[b][m][j][f][parity] -> [f][parity][j]
+            const float2 *w = src + (static_cast<size_t>(b) * (T + 1) + mh) * 8 * J2;
             for (int i = threadIdx.x; i < 8 * J2; i += blockDim.x) {
-                const int fp = i / J2, j = i - fp * J2;
-                cp_async8(dst + fp * JW + j, w + (static_cast<size_t>(j) * 8 + fp) * (T + 1));
+                const int j = i >> 3, fp = i & 7;
+                cp_async8(dst + fp * JW + j, w + i);
             }
         }
     }
