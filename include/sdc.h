@@ -139,7 +139,8 @@ typedef enum {
     /* Programmatic dependent launch inside the captured step and retape
      * graphs: 1 (default) launches the sweep and the FP32 synthesis, ring and
      * projection kernels as programmatic dependents of their predecessors, so
-     * that their launch overlaps the predecessor's last blocks; a kernel does
+     * that their launch overlaps the predecessor's last blocks (the sweep lets
+     * its successor start as soon as all its own blocks run); a kernel does
      * only the work that needs none of its predecessors' results (table and
      * twiddle prefetch, barrier set-up) before it waits for their completion,
      * so the results are the same.  0 launches every kernel after its

@@ -73,12 +73,15 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 
 // Programmatic dependent launch (griddepcontrol): a kernel launched with the
 // programmatic-serialisation attribute is scheduled as its predecessor in the
-// stream retires; pdl_wait() returns once every prerequisite grid has
-// completed and its memory is visible (at once when there is none).  No
-// kernel here signals its dependents early (launch_dependents): dependents
-// that start early hold shared memory and registers while they wait, which
-// measured slower on these kernels than letting them start as the
-// predecessor's blocks exit.
+// stream retires, or earlier once every block of the predecessor has issued
+// pdl_release(); pdl_wait() returns once every prerequisite grid has
+// completed and its memory is visible (at once when there is none).  Only
+// the sweep releases its dependents early: dependents that start early hold
+// shared memory and registers while they wait, which measured slower for
+// the transform kernels (whose successors compete with the other state
+// chain's kernels) and faster for the sweep (whose one-wave grid leaves the
+// next synthesis room to prefetch its table while the sweep drains).
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 }  // namespace sdc

@@ -41,6 +41,10 @@ __device__ __forceinline__ double2 shfl2(double2 v, int src) {
 
 template <int M, bool RESID, typename R>
 __global__ void __launch_bounds__(kSweepThreads) k4_sweep(SweepParams p) {
+    // the sweep's successors (the next batch's synthesis) may be scheduled as
+    // soon as every sweep block runs: they prefetch constant tables while
+    // the sweep drains, and wait for its completion before reading its output
+    pdl_release();
     pdl_wait();                                           // everything below reads the preceding kernels' results
     constexpr int G = sweep_lanes(M);
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
