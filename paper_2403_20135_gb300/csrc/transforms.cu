@@ -664,7 +664,8 @@ __global__ void __launch_bounds__(256) k1_synthesis_f32(const double2 *__restric
 // shuffle at the end of each order); a thread keeps two latitudes x NB states
 // x 4 fields (64 accumulators at NB = 4).
 constexpr int kSynNbMaxThreads = 384;
-constexpr int kSynNbRows = 56;             // table rows per bulk copy (even: chunks start on even t)
+constexpr int kSynNbRowsMin = 56;          // table rows per chunk at least (even: chunks start on even t)
+constexpr int kSynNbRowsMax = 128;         // and at most
 static_assert(8 * (kMaxSynStages + 1) <= static_cast<int>(kSynCtrlBytes), "stage and prologue barriers fit");
 constexpr size_t kSmemLimit = 227 * 1024;
 
@@ -688,15 +689,24 @@ __host__ inline size_t synthesis_nb_fixed(const Dims &d, int nb, int nf) {
              static_cast<size_t>(d.T + 4) * sizeof(float4);
     return b;
 }
+// Rows per chunk: the largest even count (kSynNbRowsMin..kSynNbRowsMax) for
+// which two stages fit beside the fixed part -- fewer, larger chunks mean
+// fewer block barriers per order pair.
+__host__ inline int synthesis_nb_rows(const Dims &d, int nb, int nf) {
+    const size_t fixed = synthesis_nb_fixed(d, nb, nf);
+    for (int r = kSynNbRowsMax; r > kSynNbRowsMin; r -= 2)
+        if (fixed + 2 * static_cast<size_t>(r) * d.J2p * sizeof(float) <= kSmemLimit) return r;
+    return kSynNbRowsMin;
+}
 __host__ inline int synthesis_nb_stages(const Dims &d, int nb, int nf) {
-    const size_t per = static_cast<size_t>(kSynNbRows) * d.J2p * sizeof(float);
+    const size_t per = static_cast<size_t>(synthesis_nb_rows(d, nb, nf)) * d.J2p * sizeof(float);
     const size_t fixed = synthesis_nb_fixed(d, nb, nf);
     const int ns = fixed < kSmemLimit ? static_cast<int>((kSmemLimit - fixed) / per) : 0;
     return ns > kMaxSynStages ? kMaxSynStages : ns;
 }
 __host__ inline size_t synthesis_nb_smem(const Dims &d, int nb, int nf) {
-    return synthesis_nb_fixed(d, nb, nf) +
-           static_cast<size_t>(synthesis_nb_stages(d, nb, nf)) * kSynNbRows * d.J2p * sizeof(float);
+    return synthesis_nb_fixed(d, nb, nf) + static_cast<size_t>(synthesis_nb_stages(d, nb, nf)) *
+                                               synthesis_nb_rows(d, nb, nf) * d.J2p * sizeof(float);
 }
 // whether the batched kernel serves these sizes (threads, at least two stages)
 __host__ inline bool synthesis_nb_fits(const Dims &d, int nb, int nf) {
@@ -742,7 +752,8 @@ template <int NB, int S, int NF, bool REC = false>
 __global__ void __launch_bounds__(kSynNbMaxThreads, 1)
     k1_synthesis_f32_nb(const double2 *__restrict__ states, long long sstride, const float2 *__restrict__ ybar,
                         int B, Dims d, const float *__restrict__ pbar, const float4 *__restrict__ syn32,
-                        float2 *__restrict__ f1, int nstages, int *err, const float4 *__restrict__ rec_ab = nullptr,
+                        float2 *__restrict__ f1, int nstages, int crows, int *err,
+                        const float4 *__restrict__ rec_ab = nullptr,
                         const float4 *__restrict__ rec_seed = nullptr, const float2 *__restrict__ rec_mu = nullptr) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     uint64_t *mbar = reinterpret_cast<uint64_t *>(smem_raw);                 // [kMaxSynStages], then the prologue's
@@ -753,9 +764,9 @@ __global__ void __launch_bounds__(kSynNbMaxThreads, 1)
     double2 *raw = reinterpret_cast<double2 *>(cf + static_cast<size_t>(T + 4) * RS);   // [NB][3][T + 2] (NF = 4)
     float2 *s32 = reinterpret_cast<float2 *>(raw + static_cast<size_t>(NB) * 3 * (T + 2));   // [NB][3][T + 2]
     float4 *sy = reinterpret_cast<float4 *>(s32 + synthesis_nb_s32_elems(T, NB));             // [T + 4]
-    float *stage = NF == 4 ? reinterpret_cast<float *>(sy + (T + 4))        // [nstages][kSynNbRows][J2p]
+    float *stage = NF == 4 ? reinterpret_cast<float *>(sy + (T + 4))        // [nstages][crows][J2p]
                            : reinterpret_cast<float *>(raw);
-    const size_t stage_elems = static_cast<size_t>(kSynNbRows) * d.J2p;
+    const size_t stage_elems = static_cast<size_t>(crows) * d.J2p;
     const int m1 = blockIdx.x, m2 = T - blockIdx.x;
     const int b0 = blockIdx.y * NB;
     const int nbv = min(NB, B - b0);
@@ -764,13 +775,13 @@ __global__ void __launch_bounds__(kSynNbMaxThreads, 1)
     const int nn2 = two ? T + 2 - m2 : 0;
     const int rows = nn1 + nn2;
     const int nc1 = T + 1 - m1, ncs = nc1 + (two ? T + 1 - m2 : 0);         // state coefficients per field
-    const int nch1 = (nn1 + kSynNbRows - 1) / kSynNbRows;
-    const int nch = nch1 + (nn2 + kSynNbRows - 1) / kSynNbRows;
+    const int nch1 = (nn1 + crows - 1) / crows;
+    const int nch = nch1 + (nn2 + crows - 1) / crows;
     auto chunk = [&](int c, int &m, int &t0, int &cnt) {
         const bool second = c >= nch1;
         m = second ? m2 : m1;
-        t0 = (second ? c - nch1 : c) * kSynNbRows;
-        cnt = min(kSynNbRows, (second ? nn2 : nn1) - t0);
+        t0 = (second ? c - nch1 : c) * crows;
+        cnt = min(crows, (second ? nn2 : nn1) - t0);
     };
     auto issue = [&](int c) {
         int m, t0, cnt;
@@ -1297,7 +1308,7 @@ static cudaError_t launch_synthesis_nb(const Dims &d, int B, const double2 *stat
     const int nb = B == 1 ? 1 : ((NF == 5 || B == 2 || !synthesis_nb_fits(d, 4, NF)) ? 2 : 4);
     const int S = synthesis_nb_s(d.J2);
     const dim3 g((d.T + 2) / 2, (B + nb - 1) / nb);
-    const int nt = synthesis_nb_threads(d.J2, S), ns = synthesis_nb_stages(d, nb, NF);
+    const int nt = synthesis_nb_threads(d.J2, S), ns = synthesis_nb_stages(d, nb, NF), cr = synthesis_nb_rows(d, nb, NF);
     const size_t sm = synthesis_nb_smem(d, nb, NF);
     const float4 *sy = reinterpret_cast<const float4 *>(syn32);
     // the recurrence needs a thread per latitude (the block always has at least J2 + 1 threads)
@@ -1306,7 +1317,7 @@ static cudaError_t launch_synthesis_nb(const Dims &d, int B, const double2 *stat
         if (rec && rec->rec_ab && nt >= d.J2p) {
 #define SDC_SYN_REC(NBV, SV)                                                                              \
     e = launch_k(pdl, k1_synthesis_f32_nb<NBV, SV, 4, true>, g, dim3(nt), sm, s, states, sstride, ybar, B, d, \
-                 pbar, sy, f1, ns, err, rec->rec_ab, rec->rec_seed, rec->rec_mu)
+                 pbar, sy, f1, ns, cr, err, rec->rec_ab, rec->rec_seed, rec->rec_mu)
             if (S == 2) {
                 if (nb == 1) SDC_SYN_REC(1, 2);
                 else if (nb == 2) SDC_SYN_REC(2, 2);
@@ -1323,7 +1334,7 @@ static cudaError_t launch_synthesis_nb(const Dims &d, int B, const double2 *stat
     }
 #define SDC_SYN_NB(NBV, SV)                                                                                   \
     e = launch_k(pdl, k1_synthesis_f32_nb<NBV, SV, NF, false>, g, dim3(nt), sm, s, states, sstride, ybar, B, d, pbar, \
-                 sy, f1, ns, err, static_cast<const float4 *>(nullptr), static_cast<const float4 *>(nullptr),       \
+                 sy, f1, ns, cr, err, static_cast<const float4 *>(nullptr), static_cast<const float4 *>(nullptr),   \
                  static_cast<const float2 *>(nullptr))
     if (S == 2) {
         if (nb == 1) SDC_SYN_NB(1, 2);
