@@ -387,6 +387,61 @@ __global__ void k2_split_w(TcTables tc, Dims d, int B, int nbc, const float2 *__
     }
 }
 
+// The same split with one block per order m: the ring's output of this order
+// for every state (F2[b][m][j][g][parity], contiguous per state) is staged in
+// shared memory with 16-byte copies, then a thread builds the 8 columns x 8
+// latitudes of one (parity, column block, k block) item from there.  Items
+// run parity-fastest, then column block, so the lanes of a warp read
+// neighbouring values of the same latitude records instead of records eight
+// latitudes apart.  Used while the B states' records fit kSplitStageMax.
+constexpr size_t kSplitStageMax = 100 * 1024;   // two blocks per SM (T511 with four states measured slower staged)
+
+template <int NP>
+__global__ void __launch_bounds__(256) k2_split_w_staged(TcTables tc, Dims d, int B, int nbc,
+                                                         const float2 *__restrict__ f2) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2 *wm = reinterpret_cast<float2 *>(smem_raw);   // [B][J2][10]
+    const int m = blockIdx.x;
+    const int T = d.T, J2 = d.J2;
+    const int kjb = tc.kj / 8;
+    for (int b = 0; b < B; ++b) {                        // 10 J2 float2 = 5 J2 16-byte pieces per state
+        const float4 *src = reinterpret_cast<const float4 *>(f2 + (static_cast<size_t>(b) * (T + 1) + m) * J2 * 10);
+        float4 *dst = reinterpret_cast<float4 *>(wm + static_cast<size_t>(b) * J2 * 10);
+        for (int i = threadIdx.x; i < 5 * J2; i += blockDim.x) dst[i] = src[i];
+    }
+    __syncthreads();
+    const int items = 2 * nbc * kjb;
+    for (int it = threadIdx.x; it < items; it += blockDim.x) {
+        const int p = it & 1, rest = it >> 1;
+        const int cb = rest % nbc, kb = rest / nbc;
+        float v[8][8];                                   // [column in block][latitude in k block]
+#pragma unroll
+        for (int cp = 0; cp < 4; ++cp) {
+            const int c = cb * 8 + 2 * cp;               // even: (re, im) of one (b, g) pair
+            const int b = c / 10, gg = (c - 10 * b) / 2;
+#pragma unroll
+            for (int kr = 0; kr < 8; ++kr) {
+                const int lat = kb * 8 + kr;
+                float2 w = make_float2(0.f, 0.f);
+                if (b < B && lat < J2) w = wm[(static_cast<size_t>(b) * J2 + lat) * 10 + gg * 2 + p];
+                v[2 * cp][kr] = w.x;
+                v[2 * cp + 1][kr] = w.y;
+            }
+        }
+        const int g = 2 * m + p;
+        const int c0 = kb / kTcChunkKB * kTcChunkKB, kbc = min(kTcChunkKB, kjb - c0);
+        uint16_t *dst = tc.wb + static_cast<long long>(g) * kNbc3 * kjb * 64 + static_cast<long long>(c0) * kNbc3 * 64 +
+                        (cb * kbc + kb - c0) * 64;
+#pragma unroll
+        for (int cr = 0; cr < 8; ++cr) {
+            uint4 out[NP];
+            split8<NP>(v[cr], out);
+#pragma unroll
+            for (int i = 0; i < NP; ++i) *reinterpret_cast<uint4 *>(dst + i * tc.wb_elems + cr * 8) = out[i];
+        }
+    }
+}
+
 // Synthesis coefficients, one thread per (extended row e, state b): the
 // FP32 values (zeta, Phi', U, V) of degree n' (the wind factors as in the
 // FP64/FP32 synthesis), split into NP pieces at row q of column block b.
@@ -450,6 +505,8 @@ cudaError_t configure_tc_kernels() {
     set(reinterpret_cast<const void *>(k3_tc<3>), (int)tc_smem_bytes(3, kNbc3));
     set(reinterpret_cast<const void *>(k1_tc<2>), (int)tc_smem_bytes(2, kNbc1));
     set(reinterpret_cast<const void *>(k1_tc<3>), (int)tc_smem_bytes(3, kNbc1));
+    set(reinterpret_cast<const void *>(k2_split_w_staged<2>), (int)kSplitStageMax);
+    set(reinterpret_cast<const void *>(k2_split_w_staged<3>), (int)kSplitStageMax);
     return e;
 }
 
@@ -475,11 +532,15 @@ cudaError_t launch_tc_projection(const TcTables &tc, const Dims &d, int B, const
     const int nbc = (10 * B + 15) / 16 * 2;
     const long long nsplit = 2LL * (d.T + 1) * nbc * (tc.kj / 8);
     const unsigned gs = static_cast<unsigned>((nsplit + 127) / 128);
+    const size_t stage = static_cast<size_t>(B) * d.J2 * 10 * sizeof(float2);
+    const bool staged = stage <= kSplitStageMax;
     if (tc.npieces == 2) {
-        k2_split_w<2><<<gs, 128, 0, s>>>(tc, d, B, nbc, f2);
+        if (staged) k2_split_w_staged<2><<<d.T + 1, 256, stage, s>>>(tc, d, B, nbc, f2);
+        else k2_split_w<2><<<gs, 128, 0, s>>>(tc, d, B, nbc, f2);
         k3_tc<2><<<tc.ntiles3, kTcThreads, tc_smem_bytes(2, nbc), s>>>(tc, d, B, y);
     } else {
-        k2_split_w<3><<<gs, 128, 0, s>>>(tc, d, B, nbc, f2);
+        if (staged) k2_split_w_staged<3><<<d.T + 1, 256, stage, s>>>(tc, d, B, nbc, f2);
+        else k2_split_w<3><<<gs, 128, 0, s>>>(tc, d, B, nbc, f2);
         k3_tc<3><<<tc.ntiles3, kTcThreads, tc_smem_bytes(3, nbc), s>>>(tc, d, B, y);
     }
     if (launches) *launches += 2;
