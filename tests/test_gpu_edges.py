@@ -90,3 +90,29 @@ def test_most_sweeps():
     ref = osdc.swe_run(o, u, osdc.Collocation(M), K, 600.0, 1)
     got = to_numpy(_solver(T, J, L, M, K).run(_cuda(u), 1))
     assert np.all(rel_l2(got, ref) <= 1e-11), rel_l2(got, ref)
+
+
+@pytest.mark.parametrize("T,J,L", [(15, 24, 48), (47, 72, 144)])
+def test_odd_padded_ring_lengths(T, J, L):
+    """Ring lengths whose padded length (one spare element per 16) is odd: 48
+    and 144 longitudes give 51 and 153, so the FP32 ring kernels' second
+    scratch array starts on an 8-byte boundary and their input copies and
+    output staging take the 8-byte branches (generic pass plans; 48 = 16 x 3,
+    144 = 16 x 9).  FP32 tendency and run against the oracle within the mixed
+    bound, the FP32-mode adjoint against the FP64 one."""
+    o, u = _state(T, J, L, M=4, K=4)
+    ref = o.explicit(u)
+    s32 = _solver(T, J, L, M=4, K=4, dt=300.0, precision=1)
+    err = rel_l2(to_numpy(s32.tendency(_cuda(np.stack([u, 0.5 * u])))[0]), ref)
+    assert np.all(err <= bound(1, T, J, L)), err
+    s64 = _solver(T, J, L, M=4, K=4, dt=300.0)
+    a = to_numpy(s64.run(_cuda(u), 3))
+    b = to_numpy(s32.run(_cuda(u), 3))
+    assert np.all(rel_l2(b, a) <= 30 * bound(1, T, J, L)), rel_l2(b, a)
+    rng = np.random.default_rng(11)
+    target = torch.from_numpy(o.height_grid(u) + rng.standard_normal((J, L))).to("cuda")
+    ref_loss, ref_g = s64.adjoint_run(_cuda(u), 2, target, nsnapshots=2)
+    loss, g = s32.adjoint_run(_cuda(u), 2, target, nsnapshots=2)
+    s32.sync()
+    assert abs(loss - ref_loss) <= 1e-5 * abs(ref_loss), (loss, ref_loss)
+    assert np.all(rel_l2(to_numpy(g), to_numpy(ref_g)) <= 1e-5), rel_l2(to_numpy(g), to_numpy(ref_g))
