@@ -78,7 +78,7 @@ __global__ void k3t_epilogue(const double2 *__restrict__ abar, long long astride
 // ---------------------------------------------------------------------------
 // K3a^T: W-bar_g[parity][j] = sum over rows e of order m with that parity of
 // Pbar_e(mu_j) Y-bar_g[e]; blocks serve orders m and T - m.  Output in the
-// forward's F2 layout [b][m][g][parity][j2].
+// FP64 forward's F2 layout [b][m][g][parity][j2].
 // ---------------------------------------------------------------------------
 template <typename R>
 __global__ void __launch_bounds__(64) k3t_synth(const V2<R> *__restrict__ ybar, Dims d, const R *__restrict__ pbar,

@@ -256,8 +256,9 @@ __device__ __forceinline__ void tc_epilogue_free(TcSmem &sm, uint32_t ncols) {
 
 // ---------------------------------------------------------------------------
 // Analysis projection: one block per tile (m, p, rows q0..q0+nrows), all B
-// states.  Columns col = b*10 + g*2 + (re, im) of W = F2[b][m][g][p][j],
-// pre-split by k2_split_w.  Output Y[b][e][g] (float2), e = ext_offset(m) + p + 2q.
+// states.  Columns col = b*10 + g*2 + (re, im) of W = F2[b][m][j][g][p],
+// pre-split by k2_split_w_staged or k2_split_w.  Output Y[b][e][g] (float2),
+// e = ext_offset(m) + p + 2q.
 // ---------------------------------------------------------------------------
 template <int NP>
 __global__ void __launch_bounds__(kTcThreads) k3_tc(TcTables tc, Dims d, int B, float2 *__restrict__ y) {
@@ -339,7 +340,9 @@ __global__ void __launch_bounds__(kTcThreads) k1_tc(TcTables tc, Dims d, int B, 
 
 // W^T pieces of the projection, one thread per (group, col block, k block):
 // 8 columns x 8 latitudes of F2 (zero beyond B states and J2 latitudes),
-// split and written as NP core matrices.
+// split and written as NP core matrices.  Reads the FP32 F2 layout
+// [b][m][j][g][parity] straight from global memory (used where the staged
+// variant below does not fit its shared memory).
 template <int NP>
 __global__ void k2_split_w(TcTables tc, Dims d, int B, int nbc, const float2 *__restrict__ f2) {
     const int kjb = tc.kj / 8;

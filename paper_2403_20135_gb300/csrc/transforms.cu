@@ -147,7 +147,8 @@ size_t ring_smem_bytes(int L, int elem_bytes, int *scratch_arrays) {
 // K2: one block per (latitude pair j2, state b).  The north ring (mu_j > 0)
 // and its mirror (mu = -mu_j) travel together as the real and imaginary
 // parts of one complex sequence.
-// Input  F1[b][j2][4][2][T+1]; output F2[b][m][5][2][J2] =
+// FP64 (the FP32 layouts are at k2_ring_f32 and ring_f32_output):
+// input  F1[b][j2][4][2][T+1]; output F2[b][m][5][2][J2] =
 //   w~_j (G_north + G_south) (parity 0), w~_j (G_north - G_south) (parity 1)
 // for G in (A, B, C, D) = (eta U, eta V, Phi' U, Phi' V), weight w~ = w/(1-mu^2);
 // G = E = (U^2 + V^2) / (2 (1 - mu^2)) uses the plain Gauss weight w.
@@ -242,9 +243,13 @@ __global__ void k2_ring(const V2<R> *__restrict__ f1, V2<R> *__restrict__ f2, Di
 // ---------------------------------------------------------------------------
 // K2 (FP32): the ring kernel of k2_ring with the padded radix-16 passes of
 // fft_pass.cuh (shared-memory bound in FP32: fewer passes, no bank
-// conflicts, no copy-back).  X[5] and S[5] are both resident; the grid
-// fields land in X or S by the parity of the pass count, the products are
-// always written to X, the forward result again lands by parity.
+// conflicts, no copy-back).  Input F1[b][j2][m][parity][field] (the block's
+// slice is contiguous).  X[5] and S[5] are both resident; for the lengths
+// fixed at compile time whose last pass is radix 3 that pass runs fused with
+// the grid products, which land in the array the pass did not read; for the
+// other lengths the grid fields land in X or S by the parity of the pass
+// count and the products are written to X; the forward result again lands by
+// parity and the other array stages the output.
 // ---------------------------------------------------------------------------
 
 // Unpack of the forward transforms of the north (real part) and south
