@@ -42,6 +42,8 @@ bool is_2a3b(int L) {
 
 }  // namespace
 
+constexpr int kStepsPerGraph = 4;   // steps per graph of a long run (sdc_run)
+
 struct sdc_ctx {
     int T = 0, J = 0, L = 0, M = 0, K = 0;
     int precision = SDC_FP64;
@@ -99,8 +101,9 @@ struct sdc_ctx {
     TcTile1 *tc_t1 = nullptr;
     int *tc_err = nullptr;
 
-    cudaGraphExec_t graph[2] = {nullptr, nullptr};   // [with residuals]
-    int graph_launches[2] = {0, 0};
+    // [0] one step, [1] one step with residuals, [2] kStepsPerGraph steps
+    cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};
+    int graph_launches[3] = {0, 0, 0};
     double2 *alt = nullptr;              // reference integrators: extra node iterates
     cudaGraphExec_t graph_retape = nullptr, graph_adjoint = nullptr;
     int retape_launches = 0, adjoint_launches = 0;
@@ -403,13 +406,19 @@ cudaError_t upload_denominators(sdc_ctx *c) {
     return cudaMemcpy(c->den, den.data(), den.size() * sizeof(double), cudaMemcpyHostToDevice);
 }
 
-int ensure_graph(sdc_ctx *c, bool with_resid) {
-    const int v = with_resid ? 1 : 0;
+// Graph v: 0 one step, 1 one step with residuals, 2 kStepsPerGraph steps in
+// one graph (sdc_run's long runs: one graph launch per kStepsPerGraph steps,
+// and each step's first kernel launched as a programmatic dependent of the
+// previous step's last sweep).
+int ensure_graph(sdc_ctx *c, bool with_resid, int v = -1) {
+    if (v < 0) v = with_resid ? 1 : 0;
     if (c->graph[v]) return SDC_OK;
     cudaGraph_t g = nullptr;
     SDC_CUDA(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
     int launches = 0;
-    cudaError_t e = enqueue_step(c, c->cap, with_resid, &launches);
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < (v == 2 ? kStepsPerGraph : 1) && e == cudaSuccess; ++k)
+        e = enqueue_step(c, c->cap, with_resid, &launches);
     cudaError_t e2 = cudaStreamEndCapture(c->cap, &g);
     if (e != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
@@ -598,7 +607,13 @@ int Reverser::advance(int n) {
 int run_steps(sdc_ctx *c, int nsteps, bool with_resid) {
     int st = ensure_graph(c, with_resid);
     if (st != SDC_OK) return st;
-    for (int i = 0; i < nsteps; ++i) SDC_CUDA(cudaGraphLaunch(c->graph[with_resid ? 1 : 0], c->stream));
+    int i = 0;
+    if (!with_resid && nsteps >= kStepsPerGraph) {
+        st = ensure_graph(c, false, 2);
+        if (st != SDC_OK) return st;
+        for (; i + kStepsPerGraph <= nsteps; i += kStepsPerGraph) SDC_CUDA(cudaGraphLaunch(c->graph[2], c->stream));
+    }
+    for (; i < nsteps; ++i) SDC_CUDA(cudaGraphLaunch(c->graph[with_resid ? 1 : 0], c->stream));
     c->n_explicit += static_cast<long long>(nsteps) * evals_per_step(c);
     c->n_solve += static_cast<long long>(nsteps) * solves_per_step(c);
     c->n_launch += static_cast<long long>(nsteps) * c->graph_launches[with_resid ? 1 : 0];

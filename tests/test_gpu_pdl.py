@@ -56,3 +56,19 @@ def test_pdl_option_errors():
         with pytest.raises(SdcError) as e:
             s.set_pdl(bad)
         assert e.value.status == 1
+
+
+@pytest.mark.parametrize("precision", [0, 1, 2])
+def test_multi_step_graph_equals_single_steps(precision):
+    """sdc_run captures four steps per graph for long runs (the remainder runs
+    on the one-step graph): nine steps in one call equal nine one-step calls
+    bit for bit."""
+    from paper_2403_20135_gb300 import Solver
+    wl = si.Workload("p", 2, 31, 48, 96, 3, 3, 600.0, 1, 1, (100.0, 100.0))
+    s = Solver.for_workload(wl, precision=precision)
+    u0 = s.initial_state(wl)
+    a = to_numpy(s.run(u0.clone(), 9))
+    x = u0.clone()
+    for _ in range(9):
+        s.run(x, 1)
+    np.testing.assert_array_equal(a, to_numpy(x))
