@@ -118,3 +118,17 @@ def test_t511_tensor_core_five_states():
     for b in range(5):
         err = rel_l2(got[b], ref[b])
         assert np.all(err <= bound(3, WL.T, WL.nlat, WL.nlon)), (b, err)
+
+
+def test_t511_fp32_chains_equal_one_chain():
+    """Two state chains at the largest size, where the FP32 Legendre table
+    (202 MB) streams from HBM: steps and reversed steps equal the one-chain
+    results bit for bit."""
+    a = _solver(1)
+    b = _solver(1)
+    a.set_chains(1)
+    b.set_chains(2)
+    u0 = a.initial_state(WL)
+    np.testing.assert_array_equal(to_numpy(a.run(u0.clone(), 2)), to_numpy(b.run(u0.clone(), 2)))
+    ub = torch.ones_like(u0)
+    np.testing.assert_array_equal(to_numpy(a.step_adjoint(u0, ub)), to_numpy(b.step_adjoint(u0, ub)))
